@@ -1,0 +1,127 @@
+"""Oracle PM force step: deposit -> solve -> interpolate -> kick-drift -> recompress.
+
+Follows the per-step flow of Sec. 2.1-2.3 (Fig. 2: link list, density
+interpolation, Fourier transforms, inverse force interpolation; PP is not
+part of this step) with the two-level split of Sec. 2.1:
+
+  * single level (coarse_ratio == 1): one periodic fine mesh, full Green's
+    function of Eq. 2, acceleration interpolated from it;
+  * two level: long-range acceleration on the coarse mesh (n_fine /
+    coarse_ratio per side, Gaussian long-range Green's function) plus the
+    short-range acceleration of the particle's home tile; each tile of
+    interior t carries a buffer b (edge T = t + 2b), receives the particles
+    whose CIC stencil lies inside it, and is solved by its own FFT
+    convolution with the truncated short-range kernel (radius R <= b - 2).
+
+Kick-drift (the paper does not spell it out): v' = v + c_kick a, then
+x' = (x + c_drift v') wrapped into [0, n_fine).
+
+Config keys: n_fine, coarse_ratio, tile, buffer, cmp_ratio, vel_bits, G,
+mass (per species), r_split, r_cut.
+"""
+from __future__ import annotations
+
+from typing import Dict, List, Sequence
+
+import numpy as np
+
+from . import codec, mesh, solve
+
+
+def tile_origins(n_fine: int, t: int):
+    nt = n_fine // t
+    for iz in range(nt):
+        for iy in range(nt):
+            for ix in range(nt):
+                yield (ix, iy, iz), np.array([ix * t, iy * t, iz * t], dtype=np.float64)
+
+
+def density_fine(xs: Sequence[np.ndarray], cfg: Dict) -> np.ndarray:
+    """Periodic CIC mass per fine cell, both species."""
+    n = cfg["n_fine"]
+    return sum(mesh.cic_deposit(x, m, n) for x, m in zip(xs, cfg["mass"]))
+
+
+def density_coarse(xs: Sequence[np.ndarray], cfg: Dict) -> np.ndarray:
+    """Periodic CIC mass per coarse cell (positions divided by coarse_ratio)."""
+    rc = cfg["coarse_ratio"]
+    nc = cfg["n_fine"] // rc
+    return sum(mesh.cic_deposit(np.asarray(x, np.float64) / rc, m, nc) for x, m in zip(xs, cfg["mass"]))
+
+
+def accel_single_level(xs: Sequence[np.ndarray], cfg: Dict) -> List[np.ndarray]:
+    n = cfg["n_fine"]
+    a_mesh = solve.accel_periodic(density_fine(xs, cfg), 1.0, cfg["G"])
+    return [mesh.cic_interp(a_mesh, x, n) for x in xs]
+
+
+def coarse_accel_mesh(xs, cfg) -> np.ndarray:
+    rc = cfg["coarse_ratio"]
+    return solve.accel_periodic(density_coarse(xs, cfg), float(rc), cfg["G"], cfg["r_split"])
+
+
+def fine_accel(xs: Sequence[np.ndarray], cfg: Dict) -> List[np.ndarray]:
+    """Short-range acceleration of every particle from its home tile."""
+    n, t, b = cfg["n_fine"], cfg["tile"], cfg["buffer"]
+    T = t + 2 * b
+    if cfg["r_cut"] > b - 2:
+        raise ValueError("kernel radius must satisfy R <= buffer - 2")
+    K = solve.fine_kernel(T, cfg["G"], cfg["r_split"], cfg["r_cut"])
+    xs64 = [np.asarray(x, np.float64).reshape(-1, 3) for x in xs]
+    home = [np.floor(x / t).astype(np.int64) for x in xs64]
+    out = [np.zeros_like(x) for x in xs64]
+    for idx, o in tile_origins(n, t):
+        origin = o - b
+        rho = sum(mesh.tile_deposit(x, m, origin, T, n) for x, m in zip(xs64, cfg["mass"]))
+        a_t = solve.accel_tile(rho, K)
+        for s, x in enumerate(xs64):
+            sel = np.all(home[s] == np.array(idx), axis=1)
+            if np.any(sel):
+                u = np.mod(x[sel] - origin, n)
+                out[s][sel] = mesh.tile_interp(a_t, u)
+    return out
+
+
+def accel(xs: Sequence[np.ndarray], cfg: Dict) -> List[np.ndarray]:
+    """Per-particle acceleration of each species (fine-cell units)."""
+    if cfg["coarse_ratio"] == 1:
+        return accel_single_level(xs, cfg)
+    rc = cfg["coarse_ratio"]
+    nc = cfg["n_fine"] // rc
+    a_c = coarse_accel_mesh(xs, cfg)
+    coarse = [mesh.cic_interp(a_c, np.asarray(x, np.float64) / rc, nc) for x in xs]
+    fine = fine_accel(xs, cfg)
+    return [c + f for c, f in zip(coarse, fine)]
+
+
+def kick_drift(x, v, a, c_kick: float, c_drift: float, n_fine: int):
+    v1 = np.asarray(v, np.float64) + c_kick * np.asarray(a, np.float64)
+    x1 = np.mod(np.asarray(x, np.float64) + c_drift * v1, float(n_fine))
+    return x1, v1
+
+
+def to_f32_positions(x, n_fine: int) -> np.ndarray:
+    """float32 cast of wrapped positions, keeping them inside [0, n_fine)."""
+    x32 = np.asarray(x, np.float64).astype(np.float32)
+    x32[x32 >= np.float32(n_fine)] = np.float32(0.0)
+    return x32
+
+
+def step(codes: Sequence[codec.Codes], cfg: Dict, c_kick: float, c_drift: float,
+         order: str = "stable"):
+    """One full PM step from compressed state to compressed state.
+
+    Returns (new codes per species, float64 x', v' per species in input order).
+    """
+    n = cfg["n_fine"]
+    n_cmp = n // cfg["cmp_ratio"]
+    xv = [codec.decompress(c, n) for c in codes]
+    xs = [p[0] for p in xv]
+    a = accel(xs, cfg)
+    new_codes, states = [], []
+    for (x, v), acc in zip(xv, a):
+        x1, v1 = kick_drift(x, v, acc, c_kick, c_drift, n)
+        new_codes.append(codec.compress(to_f32_positions(x1, n), v1.astype(np.float32), n, n_cmp,
+                                        cfg["vel_bits"], order=order))
+        states.append((x1, v1))
+    return new_codes, states
