@@ -1,0 +1,376 @@
+"""Benchmark of the fused two-species PM step (particle-steps per second).
+
+Workload (default): two-level PM, 256^3 fine mesh, coarse ratio 4 (64^3
+coarse mesh), 64 fine tiles of 64^3 interior + 16-cell buffer (96^3 FFTs),
+128^3 Zel'dovich CDM + 256^3 Fermi-Dirac neutrinos (18.9M particles),
+compressed state with 8-bit offsets and 8-bit velocities, float32 math.
+One step = decompress + deposit, coarse and tile solves, interpolate + kick
++ drift + recompress of both species (pm_step), codes -> codes.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+Under torchrun each rank runs an independent replica of the workload (the
+path shards by independent problems; no data-path collective): value is the
+particle-steps of all ranks divided by the slowest rank's time.
+--impl reference times the oracle (plain float64 numpy restatement of the
+method) on a bounded sample of the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "particle-steps/s (CDM+nu) per PM step"
+UNIT = "particle-steps/s"
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        if self.thread is not None:
+            self.thread.join(timeout=5)
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in self.rows:
+            for i, nm in enumerate(names):
+                if r[5 + i].lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(self.rows)}
+
+
+def algorithmic_bytes(cfg, counts, vel_bits):
+    """Algorithmic bytes per launch of each kernel kind (see the design notes)."""
+    nf, t, b = cfg["n_fine"], cfg["tile"], cfg["buffer"]
+    T = t + 2 * b
+    NH = T // 2 + 1
+    vb = 2 if vel_bits == 16 else 1
+    N = sum(counts)
+    batch = cfg.get("tile_batch", 8) or 8
+    nc = nf // cfg["coarse_ratio"]
+    ncell = (nf // cfg["cmp_ratio"]) ** 3
+    per_tile_a = T ** 3 * 4 + T * T * NH * 8
+    per_tile_b = T * T * NH * 8 + 3 * t * T * NH * 8
+    per_tile_c = 3 * t * T * NH * 8 + 3 * t ** 3 * 4
+    return {
+        "fft_a_tiles": batch * per_tile_a,
+        "fft_b_tiles": batch * per_tile_b,
+        "fft_c_tiles": batch * per_tile_c,
+        # positions + count bytes read, fine + coarse density written once
+        "deposit": N * 3 + 2 * ncell + nf ** 3 * 4 + nc ** 3 * 4,
+        # codes read, fine + coarse force read once
+        "ikd_count": N * 3 * (1 + vb) + 12 * (nf ** 3 + nc ** 3),
+        "ikd_scatter": N * 3 * (1 + vb) * 2 + 12 * (nf ** 3 + nc ** 3),
+    }
+
+
+def build_state(pm, w, torch):
+    import torch as _t  # noqa: F401
+    codes = []
+    for s in range(2):
+        x = torch.from_numpy(w.x[s]).cuda()
+        v = torch.from_numpy(w.v[s]).cuda()
+        cap = max(64, w.x[s].shape[0] // 255 + 1)
+        out = pm.empty_codes(w.x[s].shape[0], esc_cap=cap)
+        pm.compress(s, x, v, out=out)
+        codes.append(out)
+        del x, v
+    pm.check()
+    spare = [pm.empty_codes(c.n, esc_cap=c.esc.shape[0]) for c in codes]
+    return codes, spare
+
+
+def codes_bytes(c, vel_bits):
+    vb = 2 if vel_bits == 16 else 1
+    return c.cnt.numel() + c.esc.numel() * 4 + 4 + c.n * 3 * (1 + vb) + 4
+
+
+def run_gb300(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1611_01545_gb300 import PM, _lib
+    from synth import make_workload
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    w = make_workload(args.workload, seed=None)
+    cfg = w.config()
+    cfg["tile_batch"] = args.tile_batch
+    pm = PM(cfg)
+    codes, spare = build_state(pm, w, torch)
+    counts = w.counts
+    n_total = sum(counts)
+    lib = _lib.load()
+    stream = torch.cuda.current_stream()
+    a, b = codes, spare
+
+    def one_step():
+        nonlocal a, b
+        pm.step(a, b, 1.0, 1.0)
+        a, b = b, a
+
+    for _ in range(args.warmup):
+        one_step()
+    pm.check()
+    # timed region: per-kernel CUDA events live, device time by events around the loop
+    pm.set_timing(True)
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches0 = lib.pm_launch_count()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        one_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    launches = lib.pm_launch_count() - launches0
+    sampler.stop()
+    ms = e0.elapsed_time(e1)
+    pm.check()
+    stages = pm.stage_times()
+    pm.set_timing(False)
+    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = n_total * args.steps * world / (ms_max / 1e3)
+
+    # end-to-end through the C ABI with host buffers (pinned), copies in the timed region
+    hin = [c.to("cpu", pin=True) for c in a]
+    hout = [c.to("cpu", pin=True) for c in b]
+    pm.step_host(hin, hout, 1.0, 1.0)     # first call allocates the library's staging buffers
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    k_e2e = max(1, min(args.steps, 10))
+    t0 = time.perf_counter()
+    for _ in range(k_e2e):
+        pm.step_host(hin, hout, 1.0, 1.0)
+        hin, hout = hout, hin
+    e2e_s = time.perf_counter() - t0
+    te = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e_value = n_total * k_e2e * world / float(te.item())
+    h2d = sum(codes_bytes(c, w.vel_bits) for c in a)
+    d2h = h2d
+
+    alg = algorithmic_bytes(cfg, counts, w.vel_bits)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    hbm = peaks.get("hbm_gbs")
+    peak_src = "measured" if hbm else "fallback"
+    hbm = hbm or 6800.0
+    # dominant kernel: largest total time among kinds with an algorithmic byte model
+    dom = None
+    for k, (avg, cnt) in stages.items():
+        if k in alg and (dom is None or avg * cnt > stages[dom][0] * stages[dom][1]):
+            dom = k
+    roofline = None
+    if dom:
+        avg_ms = stages[dom][0]
+        achieved = alg[dom] / (avg_ms / 1e3) / 1e9
+        roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": hbm,
+                    "peak_source": peak_src, "unit": "GB/s", "frac": round(achieved / hbm, 4), "traffic": None,
+                    "alg_bytes_per_launch": alg[dom], "avg_launch_ms": round(avg_ms, 5)}
+    step_ms = ms_max / args.steps
+    result = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": args.workload, "n_fine": w.n_fine, "coarse_ratio": w.coarse_ratio,
+                   "tile": w.tile, "buffer": w.buffer, "tile_batch": args.tile_batch,
+                   "particles": {"cdm": counts[0], "nu": counts[1]}, "vel_bits": w.vel_bits,
+                   "global_batch": n_total * world, "parallelism": f"replicas{world}",
+                   "l2": "working set > L2 (126 MB): codes 113 MB + meshes > 400 MB per step"},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "steps": k_e2e},
+        "gpu_launches": int(launches),
+        "roofline": roofline,
+        "stages_ms": {k: round(v[0], 5) for k, v in stages.items()},
+        "stage_launches": {k: v[1] for k, v in stages.items()},
+        "clocks": sampler.summary(),
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        result["cpu_baseline"] = cpu_baseline(w, 1.0 / 64)
+    if world > 1:
+        dist.destroy_process_group()
+    pm.close()
+    return result if rank == 0 else None
+
+
+def cpu_baseline(workload, frac: float = 1.0 / 64):
+    """Times the oracle, as it stands, on a bounded sample of the workload.
+
+    Sample: the oracle's particle stages (CIC deposit onto the coarse and the
+    fine mesh, interpolation, kick-drift, codec) on a random subset of both
+    species, one buffered fine-tile solve and the full coarse-mesh solve;
+    the full-step time is extrapolated per particle and per tile.
+    """
+    from oracle import codec, mesh, solve, step
+    from synth import make_workload
+
+    w = make_workload(workload) if isinstance(workload, str) else workload
+    nf, t, b = w.n_fine, w.tile, w.buffer
+    T = t + 2 * b
+    n_tiles = (nf // t) ** 3 if w.coarse_ratio > 1 else 0
+    rng = np.random.default_rng(5)
+    sub = []
+    for s in range(2):
+        n = w.x[s].shape[0]
+        idx = rng.choice(n, max(1, int(n * frac)), replace=False)
+        sub.append((w.x[s][idx], w.v[s][idx]))
+    t0 = time.perf_counter()
+    nc = nf // 4
+    xs = []
+    for s, (x, v) in enumerate(sub):
+        c = codec.compress(x, v, nf, nc, w.vel_bits)
+        xd, vd = codec.decompress(c, nf)
+        xs.append((xd, vd))
+    rho_f = sum(mesh.cic_deposit(x, m, nf) for (x, _), m in zip(xs, w.mass))
+    if w.coarse_ratio > 1:
+        rho_c = sum(mesh.cic_deposit(x.astype(np.float64) / w.coarse_ratio, m, nf // w.coarse_ratio)
+                    for (x, _), m in zip(xs, w.mass))
+    zero3 = np.zeros((3,) + rho_f.shape)
+    for (x, v) in xs:
+        a = mesh.cic_interp(zero3, x, nf)
+        x1, v1 = step.kick_drift(x, v, a, 1.0, 1.0, nf)
+        codec.compress(step.to_f32_positions(x1, nf), v1.astype(np.float32), nf, nc, w.vel_bits)
+    t_particles = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    if w.coarse_ratio > 1:
+        solve.accel_periodic(rho_c, float(w.coarse_ratio), w.G, w.r_split)
+    else:
+        solve.accel_periodic(rho_f, 1.0, w.G)
+    t_coarse = time.perf_counter() - t0
+    t_tile = 0.0
+    if n_tiles:
+        K = solve.fine_kernel(T, w.G, w.r_split, w.r_cut)
+        t0 = time.perf_counter()
+        solve.accel_tile(rho_f[:T, :T, :T], K)
+        t_tile = time.perf_counter() - t0
+    n_total = sum(w.counts)
+    est = t_particles / frac + t_coarse + t_tile * n_tiles
+    return {"value": n_total / est, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": (f"oracle particle stages on {frac:.4f} of both species ({sum(len(x) for x, _ in sub)} "
+                       f"particles, {t_particles:.1f} s), 1 of {n_tiles} tile solves ({t_tile:.1f} s), full coarse "
+                       f"solve ({t_coarse:.1f} s); full step extrapolated to {est:.0f} s"),
+            "seconds_measured": round(t_particles + t_coarse + t_tile, 2), "n_total": n_total}
+
+
+def run_reference(args):
+    """Reference arm: the oracle timed on the host cores, one bounded sample per step."""
+    from synth import make_workload
+
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return None
+    w = make_workload(args.workload)
+    frac = 1.0 / 256
+    samples = []
+    t0 = time.perf_counter()
+    for _ in range(args.warmup):
+        cpu_baseline(w, frac)
+    for _ in range(args.steps):
+        samples.append(cpu_baseline(w, frac))
+    wall = time.perf_counter() - t0
+    value = statistics.median(s["value"] for s in samples)
+    cb = dict(samples[-1])
+    cb["value"] = value
+    return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": cb["n_total"] / value * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": args.workload}, "cpu_baseline": cb,
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "wall_s": round(wall, 1)}
+
+
+def main():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    p.add_argument("--workload", default="two_level256")
+    p.add_argument("--tile-batch", type=int, default=8)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    args = p.parse_args()
+    res = run_reference(args) if args.impl == "reference" else run_gb300(args)
+    if res is not None:
+        print(json.dumps(res))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,253 @@
+/*
+ * pm.h -- C ABI of libpm: the two-species (CDM + neutrino) particle-mesh
+ * force step of Emberson et al., "Cosmological neutrino simulations at
+ * extreme scale" (CUBEP3M / TianNu), on one NVIDIA GB300 (sm_103a).
+ *
+ * The step, per the paper:
+ *   decompress  the cell-ordered phase-space codes of Sec. 2.4;
+ *   deposit     CIC density of both species, each with its own mass, on the
+ *               coarse mesh and the buffered fine tiles (Sec. 2.1 footnote,
+ *               Sec. 2.3 "density_interpolation", Fig. 1);
+ *   solve       forward FFT, Green's-function multiply, three inverse FFTs
+ *               (Eqs. 1-3), long range on the coarse mesh and short range
+ *               per fine tile (Sec. 2.1);
+ *   interpolate CIC force readback (Sec. 2.3 "inverse_force_interpolation");
+ *   kick-drift  v' = v + c_kick a, x' = x + c_drift v' (periodic);
+ *   recompress  back to the Sec. 2.4 codes with a fresh v_max.
+ *
+ * Conventions (every entry point):
+ *   - positions are float32 in fine-cell units on [0, n_fine), periodic;
+ *     velocities float32 in fine cells per unit time; particle arrays are
+ *     [n][3] (x, y, z interleaved);
+ *   - meshes are dense float32 (or int64 fixed point) arrays indexed
+ *     [z][y][x], x fastest; acceleration meshes are [3][z][y][x];
+ *   - every pointer argument marked "device" is CUDA device memory owned by
+ *     the caller (e.g. a torch tensor's data_ptr()); the library never frees
+ *     it.  The library owns its handle, plans, precomputed kernels and
+ *     workspace;
+ *   - calls are asynchronous and ordered on the given CUDA stream
+ *     (cudaStream_t passed as void*; NULL = legacy default stream).  Errors
+ *     found while launching are returned; errors found on the device (a
+ *     corrupt stream, a capacity overflow) set a sticky status word that
+ *     pm_check() returns;
+ *   - sizes and indices are 64-bit.
+ * Return value of every int function: PM_OK or one PM_ERR_* code; the text
+ * of the last error is available from pm_last_error().
+ */
+#ifndef PM_H
+#define PM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PM_OK 0
+#define PM_ERR_ARG 1      /* null pointer, bad species index, size mismatch */
+#define PM_ERR_CONFIG 2   /* unsupported configuration in pm_init */
+#define PM_ERR_CUDA 3     /* a CUDA runtime call failed */
+#define PM_ERR_CORRUPT 4  /* compressed stream fails validation */
+#define PM_ERR_OVERFLOW 5 /* a caller-sized capacity (escape list) was exceeded */
+#define PM_ERR_RANGE 6    /* position outside [0, n_fine) handed to the codec */
+#define PM_ERR_TIMEOUT 7  /* a bounded device wait gave up */
+
+typedef struct pm_handle pm_handle_t;
+
+/* Problem statement (Sec. 2.1): meshes, tiles, species and the split.
+ *  n_fine        fine-mesh cells per side; positions live on [0, n_fine).
+ *  coarse_ratio  fine cells per coarse cell (the paper uses 4: the short-
+ *                range mesh is 4x finer than the long-range one).  1 selects
+ *                a single periodic mesh solved with the full Green's
+ *                function of Eq. 2 (no tiles, no split).
+ *  tile, buffer  fine-tile interior edge t and buffer width b (Fig. 1);
+ *                tile edge T = t + 2b must be one of 16, 32, 48, 64, 96,
+ *                128; t must divide n_fine; T <= n_fine.
+ *  cmp_ratio     fine cells per compression ("linked-list") cell (Sec. 2.4
+ *                bins on the coarse mesh: 4); a power of two.  In two-level
+ *                mode it must equal coarse_ratio.
+ *  vel_bits      16 (the paper's 2-byte velocities) or 8 (reduced precision).
+ *  deposit_mode  0: float32 CIC with atomics; 1: int64 fixed point (mass in
+ *                units of 2^-32, conservative integer split) -- bit-exact and
+ *                independent of particle order.
+ *  G             gravitational constant in these units.
+ *  mass, count   per species (0 = CDM, 1 = neutrinos).
+ *  r_split       Gaussian split scale r_s in fine cells (two-level).
+ *  r_cut         short-range kernel radius R in fine cells, R <= b - 2.
+ *  tile_batch    fine tiles solved per batch (0 = library default). */
+typedef struct pm_config {
+  int32_t n_fine;
+  int32_t coarse_ratio;
+  int32_t tile;
+  int32_t buffer;
+  int32_t cmp_ratio;
+  int32_t vel_bits;
+  int32_t deposit_mode;
+  int32_t tile_batch;
+  double G;
+  double mass[2];
+  int64_t count[2];
+  double r_split;
+  double r_cut;
+} pm_config_t;
+
+/* One species' compressed state (Sec. 2.4) in device memory, SoA layout:
+ *  n        particle count (host value; particles are conserved by a step).
+ *  cnt      [n_cmp^3] count byte per compression cell, cells ordered
+ *           c = ix + n_cmp (iy + n_cmp iz); 255 = "see escape list".
+ *  esc      [esc_cap][2] uint32 pairs (cell, count) for cells holding >= 255
+ *           particles, ascending by cell (the paper's 4-byte count).
+ *  esc_cap  capacity of esc in pairs (written by compress, read by decompress).
+ *  n_esc    device uint32: number of valid pairs in esc.
+ *  pos      [n][3] uint8 in-cell offsets: floor(256 * offset / cell width).
+ *  vel      [n][3] uint16 (vel_bits 16) or uint8 (vel_bits 8):
+ *           floor(v 2^(b-1) / v_max + 2^(b-1)) clamped to [0, 2^b - 1].
+ *  vmax     device float32: v_max of this species, max over particles and
+ *           components of |v_d| (the paper's per-species header value).
+ * Particles are stored cell by cell in cell order; within a cell the order
+ * is unspecified (the paper leaves it open). */
+typedef struct pm_codes {
+  int64_t n;
+  uint8_t* cnt;
+  uint32_t* esc;
+  int64_t esc_cap;
+  uint32_t* n_esc;
+  uint8_t* pos;
+  void* vel;
+  float* vmax;
+} pm_codes_t;
+
+/* Host-memory twin of pm_codes_t for pm_step_host and the serializer: same
+ * fields and layouts, every pointer is host memory (pinned for speed). */
+typedef pm_codes_t pm_host_codes_t;
+
+/* Validates cfg, allocates the workspace and precomputes, in float64 on the
+ * host then rounded to float32, the coarse Green's function (Eq. 2 with the
+ * Gaussian long-range factor, or the full Eq. 2 for a single mesh) and the
+ * DFT of the short-range tile kernel.  Uses the current CUDA device; blocks
+ * until the tables are uploaded.  *out receives the handle.
+ * Errors: PM_ERR_ARG (null), PM_ERR_CONFIG (see pm_config_t), PM_ERR_CUDA. */
+int pm_init(const pm_config_t* cfg, pm_handle_t** out);
+
+/* Frees the handle and its workspace (synchronises its device first). */
+int pm_destroy(pm_handle_t* h);
+
+/* Sizes derived from the config (host values): compression cells per side,
+ * coarse cells per side (0 for a single mesh), fine tiles, tile edge T. */
+int pm_geometry(const pm_handle_t* h, int64_t* n_cmp, int64_t* n_coarse, int64_t* n_tiles,
+                int64_t* tile_edge);
+
+/* Decompress one species (Sec. 2.4): x, v device [n][3] float32, in stream
+ * (cell) order.  Positions decode at bin centres:
+ *   x_d = (c_d + (q_d + 1/2) / 256) * cmp_ratio,
+ *   v_d = ((q_d - 2^(b-1)) + 1/2) * v_max / 2^(b-1).
+ * Validation (count bytes vs escape list vs in->n, v_max finite >= 0)
+ * reports PM_ERR_CORRUPT through pm_check(). */
+int pm_decompress(pm_handle_t* h, int species, const pm_codes_t* in, float* x, float* v, void* stream);
+
+/* Compress one species (Sec. 2.4) from device float32 x, v [in->n][3] (x in
+ * [0, n_fine)).  v_max is the exact max |v_d| unless vmax_in (device float)
+ * is given.  out->cnt/esc/n_esc/pos/vel/vmax are written; out->n must equal
+ * the particle count.  Escape-list overflow -> PM_ERR_OVERFLOW (pm_check);
+ * a position outside [0, n_fine) -> PM_ERR_RANGE (pm_check). */
+int pm_compress(pm_handle_t* h, int species, const float* x, const float* v, const float* vmax_in,
+                pm_codes_t* out, void* stream);
+
+/* CIC deposit (Sec. 2.3) of n particles of one species, mass cfg.mass[s],
+ * ADDED into the caller's meshes (zero them first): rho_fine [n_fine^3],
+ * rho_coarse [n_coarse^3] (two-level only, else NULL).  Fine tiles are
+ * periodic windows of rho_fine: tile (i,j,k) covers fine cells
+ * (i t - b .. i t + t + b - 1, ...) mod n_fine (see pm_tile_density). */
+int pm_deposit(pm_handle_t* h, int species, const float* x, int64_t n, float* rho_coarse,
+               float* rho_fine, void* stream);
+
+/* Same, int64 fixed point: each particle's mass llrint(m 2^32) is split
+ * exactly over its 8 CIC corners, one dimension at a time, with weights
+ * floor(f 2^20) (f = x - floor(x) in float32).  Bit-exact, order-free. */
+int pm_deposit_fixed(pm_handle_t* h, int species, const float* x, int64_t n, int64_t* rho_coarse,
+                     int64_t* rho_fine, void* stream);
+
+/* The fused deposit that pm_step runs: decodes both species' positions from
+ * their codes and deposits them (masses cfg.mass) into the caller's meshes,
+ * binned in shared memory per block of compression cells.  Meshes are
+ * float32, or int64 when cfg.deposit_mode == 1; they are ADDED to.
+ * Validation of the codes as in pm_decompress. */
+int pm_deposit_codes(pm_handle_t* h, const pm_codes_t in[2], void* rho_coarse, void* rho_fine, void* stream);
+
+/* Copies fine tile `tile` (index ix + nt (iy + nt iz)) of the periodic fine
+ * density into out [T^3]: the window the tile solve transforms.  On cells
+ * 1..T-2 it equals a CIC deposit of exactly the particles whose stencil lies
+ * inside the tile. */
+int pm_tile_density(pm_handle_t* h, const float* rho_fine, int64_t tile, float* out, void* stream);
+
+/* Solve (Eqs. 1-3, Sec. 2.1).  Single mesh: acc_fine [3][n_fine^3] =
+ * acceleration at the fine mesh points, acc_coarse unused.  Two level:
+ * acc_coarse [3][n_coarse^3] long-range acceleration on the coarse mesh;
+ * acc_fine [3][n_fine^3] short-range acceleration, each tile contributing its
+ * interior t^3 cells.  rho_* as produced by pm_deposit (float32 mode). */
+int pm_solve(pm_handle_t* h, const float* rho_coarse, const float* rho_fine, float* acc_coarse,
+             float* acc_fine, void* stream);
+
+/* Same, reading int64 fixed-point densities (mass units 2^-32). */
+int pm_solve_fixed(pm_handle_t* h, const int64_t* rho_coarse, const int64_t* rho_fine, float* acc_coarse,
+                   float* acc_fine, void* stream);
+
+/* CIC force interpolation: a [n][3] = coarse CIC gather (positions /
+ * coarse_ratio) + fine CIC gather, at device positions x [n][3]. */
+int pm_interpolate(pm_handle_t* h, const float* x, int64_t n, const float* acc_coarse,
+                   const float* acc_fine, float* a, void* stream);
+
+/* Interpolate, then kick and drift in place: v' = v + c_kick a,
+ * x' = x + c_drift v' wrapped into [0, n_fine). */
+int pm_kick_drift(pm_handle_t* h, float* x, float* v, int64_t n, const float* acc_coarse,
+                  const float* acc_fine, double c_kick, double c_drift, void* stream);
+
+/* One fused PM step from compressed state to compressed state for both
+ * species: decompress + deposit, solve, interpolate + kick + drift +
+ * recompress, with the library's own meshes.  in[s] and out[s] must not
+ * alias; out[s].n must equal in[s].n.  v_max of the output is the exact
+ * per-species max |v'_d|. */
+int pm_step(pm_handle_t* h, const pm_codes_t in[2], pm_codes_t out[2], double c_kick, double c_drift,
+            void* stream);
+
+/* pm_step from HOST buffers: copies both species' codes host -> device,
+ * steps, copies the result codes device -> host, on `stream`, and
+ * synchronises it before returning.  Device staging buffers are owned by
+ * the handle (allocated on first use).  Returns the device status too. */
+int pm_step_host(pm_handle_t* h, const pm_host_codes_t in[2], pm_host_codes_t out[2], double c_kick,
+                 double c_drift, void* stream);
+
+/* Synchronises `stream`, returns and clears the sticky device status
+ * (PM_OK, PM_ERR_CORRUPT, PM_ERR_OVERFLOW, PM_ERR_RANGE, PM_ERR_TIMEOUT). */
+int pm_check(pm_handle_t* h, void* stream);
+
+/* Copies the last error message (NUL-terminated, truncated to n). */
+int pm_last_error(const pm_handle_t* h, char* buf, size_t n);
+
+/* Per-stage timing of pm_step with CUDA events on its stream: enable (1) or
+ * disable (0); pm_stage_times writes up to cap averages in ms over the
+ * steps since enabling, names into the ';'-separated buffer. */
+int pm_set_timing(pm_handle_t* h, int on);
+int pm_stage_times(pm_handle_t* h, float* ms, int cap, int* n_stages, char* names, size_t names_cap);
+
+/* Serializer for the Sec. 2.4 byte stream (host memory, not stream-ordered):
+ * header "PMNU", u32 version 1, u32 n_cmp, u32 vel_bits, u64 n, f32 v_max,
+ * u32 0; then per cell the count byte (255 + int32 count if >= 255) and the
+ * cell's records px py pz (u8) vx vy vz (u16 LE or u8).  `codes` points to
+ * host copies (cnt, esc, *n_esc, pos, vel, *vmax).  With buf == NULL only
+ * *len is computed. */
+int pm_serialize(const pm_host_codes_t* codes, int32_t n_cmp, int32_t vel_bits, uint8_t* buf, size_t cap,
+                 size_t* len);
+int pm_deserialize(const uint8_t* buf, size_t len, int32_t n_cmp, int32_t vel_bits, pm_host_codes_t* codes);
+
+const char* pm_error_string(int code);
+
+/* Number of CUDA kernels the library has launched in this process (all
+ * handles), for launch accounting in benchmarks. */
+int64_t pm_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PM_H */

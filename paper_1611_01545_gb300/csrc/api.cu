@@ -1,0 +1,814 @@
+// C ABI of libpm (include/pm.h): handle, workspace, precomputed Green's
+// functions, entry points and the host serializer of the Sec. 2.4 stream.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <atomic>
+#include <cmath>
+#include <string>
+#include <vector>
+
+#include "fft.cuh"
+#include "particles.cuh"
+#include "pm_common.cuh"
+
+using namespace pm;
+
+struct pm_handle {
+  pm_config_t cfg;
+  Geom gm;
+  Geo geo;
+  int device = 0;
+  std::string err;
+  // plans
+  SolvePlan plan_mesh;   // coarse mesh (two-level) or the single periodic mesh
+  SolvePlan plan_tiles;  // fine tiles (two-level)
+  // workspace
+  float* rho_f = nullptr;
+  float* rho_c = nullptr;
+  long long* rho_f_fix = nullptr;
+  long long* rho_c_fix = nullptr;
+  float* acc_f = nullptr;
+  float* acc_c = nullptr;
+  int64_t* off[2] = {nullptr, nullptr};
+  int64_t* newoff[2] = {nullptr, nullptr};
+  uint32_t* counts[2] = {nullptr, nullptr};
+  uint32_t* vmax_bits = nullptr;  // [2]
+  void* partial = nullptr;
+  int* status = nullptr;
+  Blk blk_dep{}, blk_ikd{};
+  std::vector<void*> allocs;
+  Timer timer;
+  // staging for pm_step_host
+  pm_codes_t stage_in[2]{}, stage_out[2]{};
+  bool staged = false;
+};
+
+namespace {
+
+int fail(pm_handle* h, int code, const std::string& msg) {
+  if (h) h->err = msg;
+  return code;
+}
+
+#define CK(h, expr)                                                                          \
+  do {                                                                                       \
+    cudaError_t e_ = (expr);                                                                 \
+    if (e_ != cudaSuccess)                                                                   \
+      return fail(h, PM_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(e_));      \
+  } while (0)
+
+template <class T>
+cudaError_t dalloc(pm_handle* h, T** p, size_t bytes) {
+  void* q = nullptr;
+  cudaError_t e = cudaMalloc(&q, bytes ? bytes : 16);
+  if (e != cudaSuccess) return e;
+  h->allocs.push_back(q);
+  *p = static_cast<T*>(q);
+  return cudaSuccess;
+}
+
+bool supported_fft(int n) { return n == 16 || n == 32 || n == 48 || n == 64 || n == 96 || n == 128; }
+bool pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
+
+int slot_of_rt(int N, int k) {
+  int N1 = 0, N2 = 0;
+  switch (N) {
+    case 16: N1 = 4; N2 = 4; break;
+    case 32: N1 = 4; N2 = 8; break;
+    case 48: N1 = 6; N2 = 8; break;
+    case 64: N1 = 8; N2 = 8; break;
+    case 96: N1 = 8; N2 = 12; break;
+    case 128: N1 = 8; N2 = 16; break;
+  }
+  return N2 * (k % N1) + k / N1;
+}
+
+int mode_number(int j, int n) { return j <= n / 2 ? j : j - n; }
+
+// Periodic-mesh multiplier of i: a_d(k) = i [4 pi G k_d g(k) / (k^2 V)] M(k), k = 2 pi m / (N h),
+// g = exp(-k^2 r_s^2) (long range) or 1; k_d -> 0 at the Nyquist index; 0 at k = 0.
+std::vector<float> periodic_kernel(int N, double h, double G, double r_s) {
+  const int NH = N / 2 + 1;
+  std::vector<float> out((size_t)3 * N * N * NH);
+  const double V = std::pow(N * h, 3);
+  const double two_pi = 2.0 * pmfft::kPi;
+  for (int kz = 0; kz < N; ++kz)
+    for (int ky = 0; ky < N; ++ky)
+      for (int kx = 0; kx < NH; ++kx) {
+        int m[3] = {mode_number(kx, N), mode_number(ky, N), mode_number(kz, N)};
+        double k[3], kg[3], k2 = 0;
+        for (int d = 0; d < 3; ++d) {
+          k[d] = two_pi * m[d] / (N * h);
+          kg[d] = (2 * std::abs(m[d]) == N) ? 0.0 : k[d];
+          k2 += k[d] * k[d];
+        }
+        double g = 0.0;
+        if (k2 > 0) {
+          g = 4.0 * pmfft::kPi * G / (k2 * V);
+          if (r_s > 0) g *= std::exp(-k2 * r_s * r_s);
+        }
+        size_t idx = ((size_t)slot_of_rt(N, kz) * N + slot_of_rt(N, ky)) * NH + kx;
+        for (int d = 0; d < 3; ++d) out[(size_t)d * N * N * NH + idx] = (float)(kg[d] * g);
+      }
+  return out;
+}
+
+// Fine tile multiplier of i: Im DFT_T[K_d] / T^3 with K_d(r) = -G r_d S(r) / r^3 (0 < r <= R),
+// S(r) = erfc(r / 2 r_s) + r / (r_s sqrt(pi)) exp(-r^2 / 4 r_s^2).  K_d is odd along d and even
+// along the other axes, so Im DFT = -sum K_d sin(2 pi n_d r_d / T) prod_{e != d} cos(2 pi n_e r_e / T),
+// evaluated separably over the (2R+1)^3 support.
+std::vector<float> tile_kernel(int T, double G, double r_s, double R) {
+  const int NH = T / 2 + 1;
+  const int Ri = (int)std::floor(R);
+  const int W = 2 * Ri + 1;
+  std::vector<float> out((size_t)3 * T * T * NH);
+  std::vector<double> cs((size_t)T * W), sn((size_t)T * W);
+  for (int n = 0; n < T; ++n)
+    for (int j = -Ri; j <= Ri; ++j) {
+      double a = 2.0 * pmfft::kPi * n * j / T;
+      cs[(size_t)n * W + (j + Ri)] = std::cos(a);
+      sn[(size_t)n * W + (j + Ri)] = std::sin(a);
+    }
+  std::vector<double> K((size_t)W * W * W);
+  std::vector<double> A((size_t)W * W * T), B((size_t)W * T * T);
+  for (int d = 0; d < 3; ++d) {
+    for (int z = -Ri; z <= Ri; ++z)
+      for (int y = -Ri; y <= Ri; ++y)
+        for (int x = -Ri; x <= Ri; ++x) {
+          double r = std::sqrt((double)x * x + (double)y * y + (double)z * z);
+          double v = 0.0;
+          if (r > 0 && r <= R) {
+            double S = std::erfc(r / (2.0 * r_s)) + r / (r_s * std::sqrt(pmfft::kPi)) * std::exp(-r * r / (4.0 * r_s * r_s));
+            double rd = d == 0 ? x : (d == 1 ? y : z);
+            v = -G * rd * S / (r * r * r);
+          }
+          K[((size_t)(z + Ri) * W + (y + Ri)) * W + (x + Ri)] = v;
+        }
+    const std::vector<double>& fz = d == 2 ? sn : cs;
+    const std::vector<double>& fy = d == 1 ? sn : cs;
+    const std::vector<double>& fx = d == 0 ? sn : cs;
+    // A[x][y][nz] = sum_z K[z][y][x] fz(nz, z)
+    for (int x = 0; x < W; ++x)
+      for (int y = 0; y < W; ++y)
+        for (int nz = 0; nz < T; ++nz) {
+          double s = 0;
+          for (int z = 0; z < W; ++z) s += K[((size_t)z * W + y) * W + x] * fz[(size_t)nz * W + z];
+          A[((size_t)x * W + y) * T + nz] = s;
+        }
+    // B[x][ny][nz] = sum_y A[x][y][nz] fy(ny, y)
+    for (int x = 0; x < W; ++x)
+      for (int ny = 0; ny < T; ++ny)
+        for (int nz = 0; nz < T; ++nz) {
+          double s = 0;
+          for (int y = 0; y < W; ++y) s += A[((size_t)x * W + y) * T + nz] * fy[(size_t)ny * W + y];
+          B[((size_t)x * T + ny) * T + nz] = s;
+        }
+    const double norm = 1.0 / ((double)T * T * T);
+    for (int nz = 0; nz < T; ++nz)
+      for (int ny = 0; ny < T; ++ny)
+        for (int nx = 0; nx < NH; ++nx) {
+          double s = 0;
+          for (int x = 0; x < W; ++x) s += B[((size_t)x * T + ny) * T + nz] * fx[(size_t)nx * W + x];
+          size_t idx = ((size_t)slot_of_rt(T, nz) * T + slot_of_rt(T, ny)) * NH + nx;
+          out[(size_t)d * T * T * NH + idx] = (float)(-s * norm);
+        }
+  }
+  return out;
+}
+
+std::vector<float2> twiddles(int N) {
+  std::vector<float2> tw(N);
+  for (int j = 0; j < N; ++j) {
+    double a = 2.0 * pmfft::kPi * j / N;
+    tw[j] = make_float2((float)std::cos(a), (float)-std::sin(a));
+  }
+  return tw;
+}
+
+// Cell-block shapes for the fused passes: full x rows when they fit, 2x2 rows when there is room.
+Blk choose_blk(const Geom& g, bool fixed, bool deposit) {
+  Blk b{};
+  b.RX = g.ncmp;
+  b.RY = b.RZ = 1;
+  Geo geo{g.nf, g.rc, g.nc, g.rcmp, g.ncmp, g.ncell(), g.two};
+  const size_t cap = 96 * 1024;
+  if (deposit) {
+    while (b.RX > 1 && deposit_codes_smem(geo, b, fixed) > cap) b.RX /= 2;
+    Blk b2 = b;
+    b2.RY = b2.RZ = 2;
+    int64_t nblk2 = (int64_t)(g.ncmp / b2.RX) * (g.ncmp / 2) * (g.ncmp / 2);
+    if (g.ncmp % 2 == 0 && deposit_codes_smem(geo, b2, fixed) <= cap && nblk2 >= 4 * 152) b = b2;
+  }
+  b.nbx = g.ncmp / b.RX;
+  b.nby = g.ncmp / b.RY;
+  b.nbz = g.ncmp / b.RZ;
+  return b;
+}
+
+Geo to_geo(const Geom& g) { return Geo{g.nf, g.rc, g.nc, g.rcmp, g.ncmp, g.ncell(), g.two}; }
+
+PCodes view(const pm_codes_t& c, bool vel16) { return PCodes{c.pos, c.vel, c.vmax, c.n, vel16}; }
+
+int check_species(pm_handle* h, int s) {
+  if (s < 0 || s > 1) return fail(h, PM_ERR_ARG, "species must be 0 or 1");
+  return PM_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- Timer --
+namespace pm {
+static std::atomic<long long> g_launch_count{0};
+void note_launches(int k) { g_launch_count.fetch_add(k, std::memory_order_relaxed); }
+
+int Timer::kind(const char* name) {
+  for (size_t i = 0; i < names.size(); ++i)
+    if (names[i] == name) return (int)i;
+  names.push_back(name);
+  total_ms.push_back(0.0);
+  count.push_back(0);
+  return (int)names.size() - 1;
+}
+void Timer::begin(int, cudaStream_t st, cudaEvent_t* out) {
+  cudaEvent_t e;
+  if (!pool.empty()) { e = pool.back(); pool.pop_back(); }
+  else cudaEventCreate(&e);
+  cudaEventRecord(e, st);
+  *out = e;
+}
+void Timer::end(int k, cudaStream_t st, cudaEvent_t start) {
+  cudaEvent_t e;
+  if (!pool.empty()) { e = pool.back(); pool.pop_back(); }
+  else cudaEventCreate(&e);
+  cudaEventRecord(e, st);
+  pending.push_back({k, {start, e}});
+}
+void Timer::flush() {
+  for (auto& p : pending) {
+    cudaEventSynchronize(p.second.second);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, p.second.first, p.second.second);
+    total_ms[p.first] += ms;
+    count[p.first] += 1;
+    pool.push_back(p.second.first);
+    pool.push_back(p.second.second);
+  }
+  pending.clear();
+}
+void Timer::clear() {
+  flush();
+  for (auto& t : total_ms) t = 0.0;
+  for (auto& c : count) c = 0;
+}
+}  // namespace pm
+
+// ------------------------------------------------------------ entry points --
+extern "C" {
+
+int64_t pm_launch_count(void) { return (int64_t)pm::g_launch_count.load(); }
+
+const char* pm_error_string(int code) {
+  switch (code) {
+    case PM_OK: return "ok";
+    case PM_ERR_ARG: return "bad argument";
+    case PM_ERR_CONFIG: return "unsupported configuration";
+    case PM_ERR_CUDA: return "CUDA error";
+    case PM_ERR_CORRUPT: return "corrupt compressed stream";
+    case PM_ERR_OVERFLOW: return "capacity overflow";
+    case PM_ERR_RANGE: return "position out of range";
+    case PM_ERR_TIMEOUT: return "device wait timed out";
+    default: return "unknown error";
+  }
+}
+
+int pm_init(const pm_config_t* cfg, pm_handle_t** out) {
+  if (!cfg || !out) return PM_ERR_ARG;
+  *out = nullptr;
+  pm_handle* h = new pm_handle();
+  h->cfg = *cfg;
+  Geom& g = h->gm;
+  const pm_config_t& c = *cfg;
+  auto bad = [&](const char* m) {
+    std::string s = m;
+    delete h;
+    fprintf(stderr, "pm_init: %s\n", s.c_str());
+    return PM_ERR_CONFIG;
+  };
+  if (c.n_fine <= 0 || c.cmp_ratio <= 0 || !pow2(c.cmp_ratio) || c.n_fine % c.cmp_ratio) return bad("cmp_ratio must be a power of two dividing n_fine");
+  if (c.vel_bits != 8 && c.vel_bits != 16) return bad("vel_bits must be 8 or 16");
+  if (c.deposit_mode != 0 && c.deposit_mode != 1) return bad("deposit_mode must be 0 or 1");
+  if (c.count[0] < 0 || c.count[1] < 0) return bad("negative particle count");
+  g.nf = c.n_fine;
+  g.rcmp = c.cmp_ratio;
+  g.ncmp = c.n_fine / c.cmp_ratio;
+  if ((int64_t)g.ncmp * g.ncmp * g.ncmp >= (int64_t)1 << 32) return bad("too many compression cells");
+  if (c.coarse_ratio == 1) {
+    g.two = false;
+    g.rc = 1;
+    g.nc = 0;
+    g.t = g.nf;
+    g.b = 0;
+    g.T = g.nf;
+    g.nts = 1;
+    if (!supported_fft(g.nf)) return bad("single-mesh n_fine must be 16, 32, 48, 64, 96 or 128");
+  } else {
+    g.two = true;
+    g.rc = c.coarse_ratio;
+    if (c.coarse_ratio != c.cmp_ratio) return bad("two-level mode needs coarse_ratio == cmp_ratio");
+    if (c.n_fine % c.coarse_ratio) return bad("coarse_ratio must divide n_fine");
+    g.nc = c.n_fine / c.coarse_ratio;
+    if (!supported_fft(g.nc)) return bad("coarse mesh edge must be 16, 32, 48, 64, 96 or 128");
+    g.t = c.tile;
+    g.b = c.buffer;
+    g.T = c.tile + 2 * c.buffer;
+    if (g.t <= 0 || g.b < 0 || g.nf % g.t || g.t % 2) return bad("tile must be even and divide n_fine");
+    if (!supported_fft(g.T)) return bad("tile + 2 buffer must be 16, 32, 48, 64, 96 or 128");
+    if (g.T > g.nf) return bad("tile edge exceeds the mesh");
+    if (!(c.r_cut > 0) || c.r_cut > g.b - 2) return bad("r_cut must satisfy 0 < R <= buffer - 2");
+    if (!(c.r_split > 0)) return bad("r_split must be positive");
+    g.nts = g.nf / g.t;
+  }
+  if (!g.two && g.nf % 2) return bad("n_fine must be even");
+  cudaGetDevice(&h->device);
+  h->geo = to_geo(g);
+  const bool fixed = c.deposit_mode == 1;
+  int rc = PM_OK;
+  auto A = [&](auto** p, size_t bytes) {
+    if (rc != PM_OK) return;
+    cudaError_t e = dalloc(h, p, bytes);
+    if (e != cudaSuccess) rc = fail(h, PM_ERR_CUDA, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  };
+  const size_t nf3 = (size_t)g.nfine3(), nc3 = (size_t)g.ncoarse3();
+  A(&h->rho_f, nf3 * 4);
+  A(&h->acc_f, 3 * nf3 * 4);
+  if (g.two) {
+    A(&h->rho_c, nc3 * 4);
+    A(&h->acc_c, 3 * nc3 * 4);
+  }
+  if (fixed) {
+    A(&h->rho_f_fix, nf3 * 8);
+    if (g.two) A(&h->rho_c_fix, nc3 * 8);
+  }
+  const size_t ncell = (size_t)g.ncell();
+  for (int s = 0; s < 2; ++s) {
+    A(&h->off[s], (ncell + 1) * 8);
+    A(&h->newoff[s], (ncell + 1) * 8);
+    A(&h->counts[s], ncell * 4);
+  }
+  A(&h->vmax_bits, 2 * 4);
+  A(&h->partial, scan_partial_bytes((int64_t)ncell));
+  A(&h->status, 4);
+  // plans and tables
+  auto make_plan = [&](SolvePlan& p, int N, int nts, int t, int b, int src_n, int batch, const std::vector<float>& kern) {
+    p.N = N;
+    p.NH = N / 2 + 1;
+    p.nts = nts;
+    p.t = t;
+    p.b = b;
+    p.src_n = src_n;
+    p.batch = batch;
+    A(&p.kern, kern.size() * 4);
+    A(&p.tw, (size_t)N * sizeof(float2));
+    A(&p.spec, (size_t)batch * N * N * p.NH * sizeof(float2));
+    A(&p.spec3, (size_t)batch * 3 * t * N * p.NH * sizeof(float2));
+    if (rc != PM_OK) return;
+    std::vector<float2> tw = twiddles(N);
+    if (cudaMemcpy(p.kern, kern.data(), kern.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(p.tw, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice) != cudaSuccess)
+      rc = fail(h, PM_ERR_CUDA, "kernel table upload failed");
+  };
+  if (g.two) {
+    make_plan(h->plan_mesh, g.nc, 1, g.nc, 0, g.nc, 1, periodic_kernel(g.nc, (double)g.rc, c.G, c.r_split));
+    int ntiles = g.ntiles();
+    int batch = c.tile_batch > 0 ? c.tile_batch : 8;
+    if (batch > ntiles) batch = ntiles;
+    make_plan(h->plan_tiles, g.T, g.nts, g.t, g.b, g.nf, batch, tile_kernel(g.T, c.G, c.r_split, c.r_cut));
+  } else {
+    make_plan(h->plan_mesh, g.nf, 1, g.nf, 0, g.nf, 1, periodic_kernel(g.nf, 1.0, c.G, 0.0));
+  }
+  if (rc == PM_OK) {
+    for (int s = 0; s < 2; ++s)
+      if (cudaMemset(h->counts[s], 0, ncell * 4) != cudaSuccess) rc = fail(h, PM_ERR_CUDA, "memset");
+    if (cudaMemset(h->status, 0, 4) != cudaSuccess) rc = fail(h, PM_ERR_CUDA, "memset");
+    if (cudaDeviceSynchronize() != cudaSuccess) rc = fail(h, PM_ERR_CUDA, "init sync");
+  }
+  h->blk_dep = choose_blk(g, fixed, true);
+  h->blk_ikd = choose_blk(g, fixed, false);
+  if (rc != PM_OK) {
+    fprintf(stderr, "pm_init: %s\n", h->err.c_str());
+    pm_destroy(h);
+    return rc;
+  }
+  *out = h;
+  return PM_OK;
+}
+
+int pm_destroy(pm_handle_t* h) {
+  if (!h) return PM_ERR_ARG;
+  cudaDeviceSynchronize();
+  h->timer.flush();
+  for (auto e : h->timer.pool) cudaEventDestroy(e);
+  for (void* p : h->allocs) cudaFree(p);
+  delete h;
+  return PM_OK;
+}
+
+int pm_geometry(const pm_handle_t* h, int64_t* n_cmp, int64_t* n_coarse, int64_t* n_tiles, int64_t* tile_edge) {
+  if (!h) return PM_ERR_ARG;
+  if (n_cmp) *n_cmp = h->gm.ncmp;
+  if (n_coarse) *n_coarse = h->gm.nc;
+  if (n_tiles) *n_tiles = h->gm.two ? h->gm.ntiles() : 0;
+  if (tile_edge) *tile_edge = h->gm.two ? h->gm.T : 0;
+  return PM_OK;
+}
+
+int pm_decompress(pm_handle_t* h, int species, const pm_codes_t* in, float* x, float* v, void* stream) {
+  if (!h || !in || !x || !v) return fail(h, PM_ERR_ARG, "null argument");
+  if (int r = check_species(h, species)) return r;
+  cudaStream_t st = (cudaStream_t)stream;
+  const bool vel16 = h->cfg.vel_bits == 16;
+  CK(h, scan_codes(*in, h->gm.ncell(), h->off[species], h->partial, h->status, st));
+  CK(h, launch_decompress(view(*in, vel16), h->off[species], h->geo, x, v, st));
+  return PM_OK;
+}
+
+int pm_compress(pm_handle_t* h, int species, const float* x, const float* v, const float* vmax_in, pm_codes_t* out,
+                void* stream) {
+  if (!h || !x || !v || !out || !out->cnt || !out->pos || !out->vel || !out->vmax || !out->n_esc || !out->esc)
+    return fail(h, PM_ERR_ARG, "null argument");
+  if (int r = check_species(h, species)) return r;
+  cudaStream_t st = (cudaStream_t)stream;
+  CK(h, cudaMemsetAsync(h->counts[species], 0, (size_t)h->gm.ncell() * 4, st));
+  CK(h, launch_compress(x, v, out->n, h->geo, h->counts[species], h->vmax_bits + species, vmax_in,
+                        h->newoff[species], *out, h->cfg.vel_bits == 16, h->partial, h->status, st));
+  return PM_OK;
+}
+
+int pm_deposit(pm_handle_t* h, int species, const float* x, int64_t n, float* rho_coarse, float* rho_fine,
+               void* stream) {
+  if (!h || (!x && n) || !rho_fine || (h->gm.two && !rho_coarse)) return fail(h, PM_ERR_ARG, "null argument");
+  if (int r = check_species(h, species)) return r;
+  CK(h, launch_deposit(x, n, (float)h->cfg.mass[species], h->geo, h->gm.two ? rho_coarse : nullptr, rho_fine,
+                       (cudaStream_t)stream));
+  return PM_OK;
+}
+
+int pm_deposit_fixed(pm_handle_t* h, int species, const float* x, int64_t n, int64_t* rho_coarse, int64_t* rho_fine,
+                     void* stream) {
+  if (!h || (!x && n) || !rho_fine || (h->gm.two && !rho_coarse)) return fail(h, PM_ERR_ARG, "null argument");
+  if (int r = check_species(h, species)) return r;
+  long long M = llrint(h->cfg.mass[species] * 4294967296.0);
+  CK(h, launch_deposit_fixed(x, n, M, h->geo, h->gm.two ? (long long*)rho_coarse : nullptr, (long long*)rho_fine,
+                             (cudaStream_t)stream));
+  return PM_OK;
+}
+
+int pm_deposit_codes(pm_handle_t* h, const pm_codes_t in[2], void* rho_coarse, void* rho_fine, void* stream) {
+  if (!h || !in || !rho_fine || (h->gm.two && !rho_coarse)) return fail(h, PM_ERR_ARG, "null argument");
+  for (int s = 0; s < 2; ++s)
+    if (!in[s].cnt || !in[s].pos || !in[s].vel || !in[s].vmax || !in[s].n_esc || !in[s].esc)
+      return fail(h, PM_ERR_ARG, "null codes pointer");
+  cudaStream_t st = (cudaStream_t)stream;
+  const bool fixed = h->cfg.deposit_mode == 1;
+  const bool vel16 = h->cfg.vel_bits == 16;
+  for (int s = 0; s < 2; ++s) CK(h, scan_codes(in[s], h->gm.ncell(), h->off[s], h->partial, h->status, st));
+  long long M0 = llrint(h->cfg.mass[0] * 4294967296.0), M1 = llrint(h->cfg.mass[1] * 4294967296.0);
+  CK(h, launch_deposit_codes(view(in[0], vel16), view(in[1], vel16), h->off[0], h->off[1], h->geo, h->blk_dep,
+                             (float)h->cfg.mass[0], (float)h->cfg.mass[1], M0, M1, h->gm.two ? rho_coarse : nullptr,
+                             rho_fine, fixed, st));
+  return PM_OK;
+}
+
+int pm_tile_density(pm_handle_t* h, const float* rho_fine, int64_t tile, float* out, void* stream) {
+  if (!h || !rho_fine || !out) return fail(h, PM_ERR_ARG, "null argument");
+  if (!h->gm.two || tile < 0 || tile >= h->gm.ntiles()) return fail(h, PM_ERR_ARG, "no such tile");
+  CK(h, tile_window_launch(h->plan_tiles, rho_fine, tile, out, (cudaStream_t)stream));
+  return PM_OK;
+}
+
+static int solve_impl(pm_handle_t* h, const void* rho_c, const void* rho_f, bool fixed, float* acc_c, float* acc_f,
+                      cudaStream_t st) {
+  Timer* tm = h->timer.on ? &h->timer : nullptr;
+  if (h->gm.two) {
+    {
+      TimedScope ts(tm, "solve_coarse", st);
+      CK(h, solve_launch(h->plan_mesh, rho_c, fixed, acc_c, st, nullptr));
+    }
+    CK(h, solve_launch(h->plan_tiles, rho_f, fixed, acc_f, st, tm));
+  } else {
+    CK(h, solve_launch(h->plan_mesh, rho_f, fixed, acc_f, st, tm));
+  }
+  return PM_OK;
+}
+
+int pm_solve(pm_handle_t* h, const float* rho_coarse, const float* rho_fine, float* acc_coarse, float* acc_fine,
+             void* stream) {
+  if (!h || !rho_fine || !acc_fine || (h->gm.two && (!rho_coarse || !acc_coarse)))
+    return fail(h, PM_ERR_ARG, "null argument");
+  return solve_impl(h, rho_coarse, rho_fine, false, acc_coarse, acc_fine, (cudaStream_t)stream);
+}
+
+int pm_solve_fixed(pm_handle_t* h, const int64_t* rho_coarse, const int64_t* rho_fine, float* acc_coarse,
+                   float* acc_fine, void* stream) {
+  if (!h || !rho_fine || !acc_fine || (h->gm.two && (!rho_coarse || !acc_coarse)))
+    return fail(h, PM_ERR_ARG, "null argument");
+  return solve_impl(h, rho_coarse, rho_fine, true, acc_coarse, acc_fine, (cudaStream_t)stream);
+}
+
+int pm_interpolate(pm_handle_t* h, const float* x, int64_t n, const float* acc_coarse, const float* acc_fine, float* a,
+                   void* stream) {
+  if (!h || (n && (!x || !a)) || !acc_fine || (h->gm.two && !acc_coarse)) return fail(h, PM_ERR_ARG, "null argument");
+  CK(h, launch_interpolate(x, n, h->geo, acc_coarse, acc_fine, a, (cudaStream_t)stream));
+  return PM_OK;
+}
+
+int pm_kick_drift(pm_handle_t* h, float* x, float* v, int64_t n, const float* acc_coarse, const float* acc_fine,
+                  double c_kick, double c_drift, void* stream) {
+  if (!h || (n && (!x || !v)) || !acc_fine || (h->gm.two && !acc_coarse)) return fail(h, PM_ERR_ARG, "null argument");
+  CK(h, launch_kick_drift(x, v, n, h->geo, acc_coarse, acc_fine, (float)c_kick, (float)c_drift, (cudaStream_t)stream));
+  return PM_OK;
+}
+
+int pm_step(pm_handle_t* h, const pm_codes_t in[2], pm_codes_t out[2], double c_kick, double c_drift, void* stream) {
+  if (!h || !in || !out) return fail(h, PM_ERR_ARG, "null argument");
+  for (int s = 0; s < 2; ++s) {
+    if (in[s].n != out[s].n) return fail(h, PM_ERR_ARG, "out[s].n must equal in[s].n");
+    if (!in[s].cnt || !in[s].pos || !in[s].vel || !in[s].vmax || !in[s].n_esc || !in[s].esc || !out[s].cnt ||
+        !out[s].pos || !out[s].vel || !out[s].vmax || !out[s].n_esc || !out[s].esc)
+      return fail(h, PM_ERR_ARG, "null codes pointer");
+    if (in[s].pos == out[s].pos) return fail(h, PM_ERR_ARG, "in and out codes must not alias");
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  Timer* tm = h->timer.on ? &h->timer : nullptr;
+  const Geom& g = h->gm;
+  const bool fixed = h->cfg.deposit_mode == 1;
+  const bool vel16 = h->cfg.vel_bits == 16;
+  const int64_t ncell = g.ncell();
+  {
+    TimedScope ts(tm, "scan_in", st);
+    for (int s = 0; s < 2; ++s) CK(h, scan_codes(in[s], ncell, h->off[s], h->partial, h->status, st));
+  }
+  void* rc = fixed ? (void*)h->rho_c_fix : (void*)h->rho_c;
+  void* rf = fixed ? (void*)h->rho_f_fix : (void*)h->rho_f;
+  {
+    TimedScope ts(tm, "deposit", st);
+    CK(h, cudaMemsetAsync(rf, 0, (size_t)g.nfine3() * (fixed ? 8 : 4), st));
+    if (g.two) CK(h, cudaMemsetAsync(rc, 0, (size_t)g.ncoarse3() * (fixed ? 8 : 4), st));
+    long long M0 = llrint(h->cfg.mass[0] * 4294967296.0), M1 = llrint(h->cfg.mass[1] * 4294967296.0);
+    CK(h, launch_deposit_codes(view(in[0], vel16), view(in[1], vel16), h->off[0], h->off[1], h->geo, h->blk_dep,
+                               (float)h->cfg.mass[0], (float)h->cfg.mass[1], M0, M1, g.two ? rc : nullptr, rf, fixed,
+                               st));
+  }
+  if (int r = solve_impl(h, rc, rf, fixed, h->acc_c, h->acc_f, st)) return r;
+  const float ck = (float)c_kick, cd = (float)c_drift;
+  {
+    TimedScope ts(tm, "ikd_count", st);
+    CK(h, cudaMemsetAsync(h->vmax_bits, 0, 8, st));
+    for (int s = 0; s < 2; ++s) {
+      CK(h, cudaMemsetAsync(h->counts[s], 0, (size_t)ncell * 4, st));
+      PCodesOut o{out[s].pos, out[s].vel, out[s].vmax, vel16};
+      CK(h, launch_ikd_codes(0, view(in[s], vel16), h->off[s], h->geo, h->blk_ikd, h->acc_c, h->acc_f, ck, cd,
+                             h->counts[s], h->vmax_bits + s, h->newoff[s], o, h->status, st));
+    }
+  }
+  {
+    TimedScope ts(tm, "scan_out", st);
+    for (int s = 0; s < 2; ++s) {
+      CK(h, launch_set_vmax(h->vmax_bits + s, out[s].vmax, st));
+      CK(h, scan_counts(h->counts[s], ncell, in[s].n, h->newoff[s], out[s], h->partial, h->status, st));
+    }
+  }
+  {
+    TimedScope ts(tm, "ikd_scatter", st);
+    for (int s = 0; s < 2; ++s) {
+      PCodesOut o{out[s].pos, out[s].vel, out[s].vmax, vel16};
+      CK(h, launch_ikd_codes(1, view(in[s], vel16), h->off[s], h->geo, h->blk_ikd, h->acc_c, h->acc_f, ck, cd,
+                             h->counts[s], h->vmax_bits + s, h->newoff[s], o, h->status, st));
+    }
+  }
+  return PM_OK;
+}
+
+static int alloc_codes(pm_handle* h, pm_codes_t& c, int64_t n, int64_t esc_cap) {
+  const int vb = h->cfg.vel_bits == 16 ? 2 : 1;
+  const size_t ncell = (size_t)h->gm.ncell();
+  c.n = n;
+  c.esc_cap = esc_cap;
+  CK(h, dalloc(h, &c.cnt, ncell));
+  CK(h, dalloc(h, &c.esc, (size_t)(esc_cap > 0 ? esc_cap : 1) * 8));
+  CK(h, dalloc(h, &c.n_esc, 4));
+  CK(h, dalloc(h, &c.pos, (size_t)n * 3));
+  void* v = nullptr;
+  CK(h, dalloc(h, &v, (size_t)n * 3 * vb));
+  c.vel = v;
+  CK(h, dalloc(h, &c.vmax, 4));
+  return PM_OK;
+}
+
+static int copy_codes(pm_handle* h, const pm_codes_t& dst, const pm_codes_t& src, int64_t ncell, int vb,
+                      cudaMemcpyKind kind, cudaStream_t st, bool include_esc_all) {
+  CK(h, cudaMemcpyAsync(dst.cnt, src.cnt, (size_t)ncell, kind, st));
+  CK(h, cudaMemcpyAsync(dst.n_esc, src.n_esc, 4, kind, st));
+  int64_t ecap = src.esc_cap < dst.esc_cap ? src.esc_cap : dst.esc_cap;
+  if (include_esc_all && ecap > 0) CK(h, cudaMemcpyAsync(dst.esc, src.esc, (size_t)ecap * 8, kind, st));
+  CK(h, cudaMemcpyAsync(dst.pos, src.pos, (size_t)src.n * 3, kind, st));
+  CK(h, cudaMemcpyAsync(dst.vel, src.vel, (size_t)src.n * 3 * vb, kind, st));
+  CK(h, cudaMemcpyAsync(dst.vmax, src.vmax, 4, kind, st));
+  return PM_OK;
+}
+
+int pm_step_host(pm_handle_t* h, const pm_host_codes_t in[2], pm_host_codes_t out[2], double c_kick, double c_drift,
+                 void* stream) {
+  if (!h || !in || !out) return fail(h, PM_ERR_ARG, "null argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int vb = h->cfg.vel_bits == 16 ? 2 : 1;
+  const int64_t ncell = h->gm.ncell();
+  if (!h->staged) {
+    for (int s = 0; s < 2; ++s) {
+      int64_t cap = in[s].esc_cap > out[s].esc_cap ? in[s].esc_cap : out[s].esc_cap;
+      if (int r = alloc_codes(h, h->stage_in[s], in[s].n, cap)) return r;
+      if (int r = alloc_codes(h, h->stage_out[s], in[s].n, cap)) return r;
+    }
+    h->staged = true;
+  }
+  for (int s = 0; s < 2; ++s)
+    if (h->stage_in[s].n != in[s].n || out[s].n != in[s].n) return fail(h, PM_ERR_ARG, "particle counts changed");
+  for (int s = 0; s < 2; ++s)
+    if (int r = copy_codes(h, h->stage_in[s], in[s], ncell, vb, cudaMemcpyHostToDevice, st, true)) return r;
+  if (int r = pm_step(h, h->stage_in, h->stage_out, c_kick, c_drift, stream)) return r;
+  for (int s = 0; s < 2; ++s)
+    if (int r = copy_codes(h, out[s], h->stage_out[s], ncell, vb, cudaMemcpyDeviceToHost, st, true)) return r;
+  return pm_check(h, stream);
+}
+
+int pm_check(pm_handle_t* h, void* stream) {
+  if (!h) return PM_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  CK(h, cudaStreamSynchronize(st));
+  int s = 0;
+  CK(h, cudaMemcpy(&s, h->status, 4, cudaMemcpyDeviceToHost));
+  CK(h, cudaMemset(h->status, 0, 4));
+  if (s & ST_RANGE) return fail(h, PM_ERR_RANGE, "device validation: position outside [0, n_fine)");
+  if (s & ST_OVERFLOW) return fail(h, PM_ERR_OVERFLOW, "device validation: escape list capacity exceeded");
+  if (s & ST_CORRUPT) return fail(h, PM_ERR_CORRUPT, "device validation: corrupt compressed stream");
+  if (s & ST_TIMEOUT) return fail(h, PM_ERR_TIMEOUT, "device wait timed out");
+  return PM_OK;
+}
+
+int pm_last_error(const pm_handle_t* h, char* buf, size_t n) {
+  if (!h || !buf || n == 0) return PM_ERR_ARG;
+  snprintf(buf, n, "%s", h->err.c_str());
+  return PM_OK;
+}
+
+int pm_set_timing(pm_handle_t* h, int on) {
+  if (!h) return PM_ERR_ARG;
+  h->timer.clear();
+  h->timer.on = on != 0;
+  return PM_OK;
+}
+
+int pm_stage_times(pm_handle_t* h, float* ms, int cap, int* n_stages, char* names, size_t names_cap) {
+  if (!h) return PM_ERR_ARG;
+  h->timer.flush();
+  int n = (int)h->timer.names.size();
+  if (n_stages) *n_stages = n;
+  std::string joined;
+  for (int i = 0; i < n; ++i) {
+    if (ms && i < cap) ms[i] = h->timer.count[i] ? (float)(h->timer.total_ms[i] / h->timer.count[i]) : 0.f;
+    if (i) joined += ";";
+    joined += h->timer.names[i];
+    joined += "#" + std::to_string(h->timer.count[i]);
+  }
+  if (names && names_cap) snprintf(names, names_cap, "%s", joined.c_str());
+  return PM_OK;
+}
+
+int pm_serialize(const pm_host_codes_t* c, int32_t n_cmp, int32_t vel_bits, uint8_t* buf, size_t cap, size_t* len) {
+  if (!c || !len || (vel_bits != 8 && vel_bits != 16) || n_cmp <= 0) return PM_ERR_ARG;
+  const int64_t ncell = (int64_t)n_cmp * n_cmp * n_cmp;
+  const int vb = vel_bits == 16 ? 2 : 1;
+  const uint32_t ne = c->n_esc ? *c->n_esc : 0;
+  // size
+  size_t total = 32;
+  uint32_t ei = 0;
+  int64_t np = 0;
+  std::vector<int64_t> counts((size_t)ncell);
+  for (int64_t cell = 0; cell < ncell; ++cell) {
+    int64_t k = c->cnt[cell];
+    if (k == 255) {
+      if (ei >= ne || c->esc[2 * ei] != (uint32_t)cell) return PM_ERR_CORRUPT;
+      k = c->esc[2 * ei + 1];
+      ++ei;
+      total += 5;
+    } else {
+      total += 1;
+    }
+    counts[(size_t)cell] = k;
+    np += k;
+  }
+  if (np != c->n || ei != ne) return PM_ERR_CORRUPT;
+  total += (size_t)np * (3 + 3 * vb);
+  *len = total;
+  if (!buf) return PM_OK;
+  if (cap < total) return PM_ERR_OVERFLOW;
+  uint8_t* o = buf;
+  const uint32_t ver = 1, ncu = (uint32_t)n_cmp, vbits = (uint32_t)vel_bits, zero = 0;
+  const uint64_t n64 = (uint64_t)c->n;
+  const float vm = *c->vmax;
+  memcpy(o, "PMNU", 4); o += 4;
+  memcpy(o, &ver, 4); o += 4;
+  memcpy(o, &ncu, 4); o += 4;
+  memcpy(o, &vbits, 4); o += 4;
+  memcpy(o, &n64, 8); o += 8;
+  memcpy(o, &vm, 4); o += 4;
+  memcpy(o, &zero, 4); o += 4;
+  int64_t p = 0;
+  for (int64_t cell = 0; cell < ncell; ++cell) {
+    int64_t k = counts[(size_t)cell];
+    if (k >= 255) {
+      *o++ = 255;
+      int32_t k32 = (int32_t)k;
+      memcpy(o, &k32, 4);
+      o += 4;
+    } else {
+      *o++ = (uint8_t)k;
+    }
+    for (int64_t j = 0; j < k; ++j, ++p) {
+      memcpy(o, c->pos + 3 * p, 3);
+      o += 3;
+      for (int d = 0; d < 3; ++d) {
+        if (vb == 2) {
+          uint16_t q = static_cast<const uint16_t*>(c->vel)[3 * p + d];
+          o[0] = (uint8_t)(q & 0xff);
+          o[1] = (uint8_t)(q >> 8);
+          o += 2;
+        } else {
+          *o++ = static_cast<const uint8_t*>(c->vel)[3 * p + d];
+        }
+      }
+    }
+  }
+  return PM_OK;
+}
+
+int pm_deserialize(const uint8_t* buf, size_t len, int32_t n_cmp, int32_t vel_bits, pm_host_codes_t* c) {
+  if (!buf || !c || len < 32) return PM_ERR_ARG;
+  if (memcmp(buf, "PMNU", 4) != 0) return PM_ERR_CORRUPT;
+  uint32_t ver, ncu, vbits;
+  uint64_t n64;
+  float vm;
+  memcpy(&ver, buf + 4, 4);
+  memcpy(&ncu, buf + 8, 4);
+  memcpy(&vbits, buf + 12, 4);
+  memcpy(&n64, buf + 16, 8);
+  memcpy(&vm, buf + 24, 4);
+  if (ver != 1 || (int32_t)ncu != n_cmp || (int32_t)vbits != vel_bits) return PM_ERR_CORRUPT;
+  if ((int64_t)n64 != c->n) return PM_ERR_ARG;
+  const int vb = vel_bits == 16 ? 2 : 1;
+  const int64_t ncell = (int64_t)n_cmp * n_cmp * n_cmp;
+  size_t off = 32;
+  int64_t p = 0;
+  uint32_t ne = 0;
+  for (int64_t cell = 0; cell < ncell; ++cell) {
+    if (off >= len) return PM_ERR_CORRUPT;
+    int64_t k = buf[off++];
+    c->cnt[cell] = (uint8_t)k;
+    if (k == 255) {
+      if (off + 4 > len) return PM_ERR_CORRUPT;
+      int32_t k32;
+      memcpy(&k32, buf + off, 4);
+      off += 4;
+      if (k32 < 255) return PM_ERR_CORRUPT;
+      if ((int64_t)ne >= c->esc_cap) return PM_ERR_OVERFLOW;
+      c->esc[2 * ne] = (uint32_t)cell;
+      c->esc[2 * ne + 1] = (uint32_t)k32;
+      ++ne;
+      k = k32;
+    }
+    if (p + k > c->n) return PM_ERR_CORRUPT;
+    size_t rec = (size_t)(3 + 3 * vb);
+    if (off + (size_t)k * rec > len) return PM_ERR_CORRUPT;
+    for (int64_t j = 0; j < k; ++j, ++p) {
+      memcpy(c->pos + 3 * p, buf + off, 3);
+      off += 3;
+      for (int d = 0; d < 3; ++d) {
+        if (vb == 2) {
+          static_cast<uint16_t*>(c->vel)[3 * p + d] = (uint16_t)(buf[off] | (buf[off + 1] << 8));
+          off += 2;
+        } else {
+          static_cast<uint8_t*>(c->vel)[3 * p + d] = buf[off++];
+        }
+      }
+    }
+  }
+  if (off != len || p != c->n) return PM_ERR_CORRUPT;
+  if (c->n_esc) *c->n_esc = ne;
+  if (c->vmax) *c->vmax = vm;
+  return PM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,882 @@
+// Particle-side kernels of the PM step:
+//   * cell-count scans of the cell-ordered codec (Sec. 2.4): count byte with
+//     the 255 escape, CSR offsets, escape-list compaction;
+//   * decompress / compress of one species (Sec. 2.4);
+//   * CIC deposit (Sec. 2.3 density_interpolation; Sec. 2.1 footnote: both
+//     species, their own masses, one mesh), float32 or int64 fixed point;
+//   * CIC force interpolation, kick and drift;
+//   * the fused step passes that read the codes directly: decode + deposit
+//     (binned in shared memory per block of compression cells), and decode +
+//     interpolate + kick + drift + recompress (count pass, then scatter pass
+//     that recomputes the same update bit for bit).
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "particles.cuh"
+
+namespace pm {
+
+// ------------------------------------------------------------ scan -------
+
+struct V2 {
+  long long a;
+  int b;
+};
+__device__ __forceinline__ V2 v2add(V2 x, V2 y) { return V2{x.a + y.a, x.b + y.b}; }
+
+constexpr int SCAN_THREADS = 256;
+constexpr int SCAN_ITEMS = 8;
+constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
+
+__device__ __forceinline__ V2 warp_incl(V2 v) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    long long a = __shfl_up_sync(0xffffffffu, v.a, o);
+    int b = __shfl_up_sync(0xffffffffu, v.b, o);
+    if (lane >= o) { v.a += a; v.b += b; }
+  }
+  return v;
+}
+
+// Exclusive block scan of one V2 per thread; returns the exclusive prefix and the block total.
+__device__ V2 block_excl(V2 v, V2* total) {
+  __shared__ V2 warp_sums[32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  V2 inc = warp_incl(v);
+  if (lane == 31) warp_sums[wid] = inc;
+  __syncthreads();
+  if (wid == 0) {
+    int nw = blockDim.x >> 5;
+    V2 w = lane < nw ? warp_sums[lane] : V2{0, 0};
+    V2 wi = warp_incl(w);
+    if (lane < nw) warp_sums[lane] = V2{wi.a - w.a, wi.b - w.b};
+    if (lane == nw - 1) warp_sums[31] = wi;
+  }
+  __syncthreads();
+  V2 res = v2add(warp_sums[wid], V2{inc.a - v.a, inc.b - v.b});
+  *total = warp_sums[31];
+  __syncthreads();
+  return res;
+}
+
+// Count of compression cell c from the count byte and the escape list.
+struct CodesCount {
+  const uint8_t* cnt;
+  const uint32_t* esc;
+  const uint32_t* n_esc;
+  int64_t esc_cap;
+  int* status;
+  __device__ V2 operator()(int64_t c) const {
+    unsigned k = cnt[c];
+    if (k != 255u) return V2{(long long)k, 0};
+    long long ne = (long long)*n_esc;
+    if (ne > esc_cap) ne = esc_cap;
+    long long lo = 0, hi = ne - 1;
+    while (lo <= hi) {
+      long long mid = (lo + hi) >> 1;
+      long long cm = esc[2 * mid];
+      if (cm == c) return V2{(long long)esc[2 * mid + 1], 1};
+      if (cm < c) lo = mid + 1; else hi = mid - 1;
+    }
+    atomicOr(status, ST_CORRUPT);
+    return V2{0, 1};
+  }
+};
+
+struct U32Count {
+  const uint32_t* cnt;
+  __device__ V2 operator()(int64_t c) const {
+    unsigned k = cnt[c];
+    return V2{(long long)k, k >= 255u ? 1 : 0};
+  }
+};
+
+template <class Get>
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_reduce(Get get, int64_t n, V2* partial) {
+  const int64_t base = (int64_t)blockIdx.x * SCAN_TILE;
+  V2 s{0, 0};
+  for (int i = threadIdx.x; i < SCAN_TILE; i += SCAN_THREADS) {
+    int64_t j = base + i;
+    if (j < n) s = v2add(s, get(j));
+  }
+  V2 tot;
+  block_excl(s, &tot);
+  if (threadIdx.x == 0) partial[blockIdx.x] = tot;
+}
+
+// Exclusive scan of the partials in place (one block); partial[nb] = grand total.
+__global__ void __launch_bounds__(1024) k_scan_partials(V2* partial, int nb) {
+  __shared__ V2 carry;
+  if (threadIdx.x == 0) carry = V2{0, 0};
+  __syncthreads();
+  for (int base = 0; base < nb; base += blockDim.x) {
+    int i = base + threadIdx.x;
+    V2 v = i < nb ? partial[i] : V2{0, 0};
+    V2 tot;
+    V2 ex = block_excl(v, &tot);
+    V2 c = carry;
+    if (i < nb) partial[i] = v2add(ex, c);
+    __syncthreads();
+    if (threadIdx.x == 0) carry = v2add(c, tot);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partial[nb] = carry;
+}
+
+// Decompress offsets: off[c] = sum_{c' < c} count(c'), off[n] = total; checks total == expect.
+struct PutOffsets {
+  int64_t* off;
+  __device__ void operator()(int64_t c, V2 excl, V2) const { off[c] = excl.a; }
+};
+
+// Compress outputs: CSR offsets, count bytes, ordered escape list.
+struct PutCodes {
+  int64_t* off;
+  uint8_t* cnt;
+  uint32_t* esc;
+  int64_t esc_cap;
+  int* status;
+  __device__ void operator()(int64_t c, V2 excl, V2 v) const {
+    off[c] = excl.a;
+    long long k = v.a;
+    cnt[c] = (uint8_t)(k >= 255 ? 255 : k);
+    if (k >= 255) {
+      if ((int64_t)excl.b < esc_cap) {
+        esc[2 * (int64_t)excl.b] = (uint32_t)c;
+        esc[2 * (int64_t)excl.b + 1] = (uint32_t)k;
+      } else {
+        atomicOr(status, ST_OVERFLOW);
+      }
+    }
+  }
+};
+
+template <class Get, class Put>
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_final(Get get, Put put, int64_t n, const V2* partial) {
+  const int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
+  V2 v[SCAN_ITEMS];
+  V2 s{0, 0};
+#pragma unroll
+  for (int k = 0; k < SCAN_ITEMS; ++k) {
+    int64_t j = base + k;
+    v[k] = j < n ? get(j) : V2{0, 0};
+    s = v2add(s, v[k]);
+  }
+  V2 tot;
+  V2 ex = v2add(block_excl(s, &tot), partial[blockIdx.x]);
+#pragma unroll
+  for (int k = 0; k < SCAN_ITEMS; ++k) {
+    int64_t j = base + k;
+    if (j < n) put(j, ex, v[k]);
+    ex = v2add(ex, v[k]);
+  }
+}
+
+// Writes off[n] = total, checks the total and the escape list, sets n_esc / vmax if asked.
+__global__ void k_scan_finish(const V2* partial, int nb, int64_t n, int64_t expect, int64_t* off, int* status,
+                              uint32_t* n_esc_out, int64_t esc_cap) {
+  V2 t = partial[nb];
+  off[n] = t.a;
+  if (t.a != expect) atomicOr(status, ST_CORRUPT);
+  if (n_esc_out) *n_esc_out = (uint32_t)(t.b < esc_cap ? t.b : esc_cap);
+}
+
+// Every escape entry must name a cell whose byte is 255, hold >= 255, ascend.
+__global__ void k_check_escapes(const uint8_t* cnt, const uint32_t* esc, const uint32_t* n_esc, int64_t esc_cap,
+                                int64_t ncell, const float* vmax, int* status) {
+  long long ne = *n_esc;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    float vm = *vmax;
+    if (!(vm >= 0.f) || isinf(vm)) atomicOr(status, ST_CORRUPT);
+    if (ne > esc_cap) atomicOr(status, ST_CORRUPT);
+  }
+  if (ne > esc_cap) ne = esc_cap;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < ne; i += (long long)gridDim.x * blockDim.x) {
+    uint32_t c = esc[2 * i], k = esc[2 * i + 1];
+    bool bad = (int64_t)c >= ncell || k < 255u || cnt[c] != 255u || (i > 0 && esc[2 * (i - 1)] >= c);
+    if (bad) atomicOr(status, ST_CORRUPT);
+  }
+}
+
+static int scan_blocks(int64_t n) { return (int)((n + SCAN_TILE - 1) / SCAN_TILE); }
+
+cudaError_t scan_codes(const pm_codes_t& in, int64_t ncell, int64_t* off, void* partial_ws, int* status,
+                       cudaStream_t st) {
+  V2* partial = static_cast<V2*>(partial_ws);
+  int nb = scan_blocks(ncell);
+  CodesCount get{in.cnt, in.esc, in.n_esc, in.esc_cap, status};
+  k_check_escapes<<<64, 256, 0, st>>>(in.cnt, in.esc, in.n_esc, in.esc_cap, ncell, in.vmax, status);
+  k_scan_reduce<<<nb, SCAN_THREADS, 0, st>>>(get, ncell, partial);
+  k_scan_partials<<<1, 1024, 0, st>>>(partial, nb);
+  k_scan_final<<<nb, SCAN_THREADS, 0, st>>>(get, PutOffsets{off}, ncell, partial);
+  k_scan_finish<<<1, 1, 0, st>>>(partial, nb, ncell, in.n, off, status, nullptr, 0);
+  note_launches(5);
+  return cudaGetLastError();
+}
+
+cudaError_t scan_counts(const uint32_t* counts, int64_t ncell, int64_t expect, int64_t* off, pm_codes_t& out,
+                        void* partial_ws, int* status, cudaStream_t st) {
+  V2* partial = static_cast<V2*>(partial_ws);
+  int nb = scan_blocks(ncell);
+  U32Count get{counts};
+  k_scan_reduce<<<nb, SCAN_THREADS, 0, st>>>(get, ncell, partial);
+  k_scan_partials<<<1, 1024, 0, st>>>(partial, nb);
+  k_scan_final<<<nb, SCAN_THREADS, 0, st>>>(get, PutCodes{off, out.cnt, out.esc, out.esc_cap, status}, ncell,
+                                             partial);
+  k_scan_finish<<<1, 1, 0, st>>>(partial, nb, ncell, expect, off, status, out.n_esc, out.esc_cap);
+  note_launches(4);
+  return cudaGetLastError();
+}
+
+size_t scan_partial_bytes(int64_t ncell) { return sizeof(V2) * (size_t)(scan_blocks(ncell) + 1); }
+
+// ------------------------------------------------- plain per-particle -----
+
+// Cell of stream index p: the last c with off[c] <= p (binary search over all cells).
+__device__ __forceinline__ int64_t find_cell(const int64_t* off, int64_t ncell, int64_t p) {
+  int64_t lo = 0, hi = ncell - 1;
+  while (lo < hi) {
+    int64_t mid = (lo + hi + 1) >> 1;
+    if (off[mid] <= p) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+__global__ void k_decompress(PCodes in, const int64_t* off, Geo g, float* x, float* v) {
+  const float pscale = (float)g.rcmp / 256.0f;
+  const float vm = *in.vmax;
+  const int half = in.vel16 ? 32768 : 128;
+  const float step = __fmul_rn(vm, 1.0f / (float)half);
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < in.n; p += (int64_t)gridDim.x * blockDim.x) {
+    int64_t c = find_cell(off, g.ncell, p);
+    int cx = (int)(c % g.ncmp), cy = (int)((c / g.ncmp) % g.ncmp), cz = (int)(c / ((int64_t)g.ncmp * g.ncmp));
+    const uint8_t* q = in.pos + 3 * p;
+    x[3 * p + 0] = decode_pos(cx, q[0], pscale);
+    x[3 * p + 1] = decode_pos(cy, q[1], pscale);
+    x[3 * p + 2] = decode_pos(cz, q[2], pscale);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      int qv = in.vel16 ? (int)reinterpret_cast<const uint16_t*>(in.vel)[3 * p + d]
+                        : (int)reinterpret_cast<const uint8_t*>(in.vel)[3 * p + d];
+      v[3 * p + d] = decode_vel(qv, half, step);
+    }
+  }
+}
+
+// Float32 CIC deposit into global meshes with atomics.
+__device__ __forceinline__ void cic_axis(float x, int n, int& i0, int& i1, float& w0, float& w1) {
+  float f = floorf(x);
+  w1 = __fsub_rn(x, f);
+  w0 = __fsub_rn(1.0f, w1);
+  i0 = (int)f;
+  if (i0 >= n) i0 -= n;
+  if (i0 < 0) i0 += n;
+  i1 = (i0 + 1 == n) ? 0 : i0 + 1;
+}
+
+__global__ void k_deposit_global(const float* x, int64_t n, float m, Geo g, float* rho_c, float* rho_f) {
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+    float px = x[3 * p], py = x[3 * p + 1], pz = x[3 * p + 2];
+    int ix[2], iy[2], iz[2];
+    float wx[2], wy[2], wz[2];
+    cic_axis(px, g.nf, ix[0], ix[1], wx[0], wx[1]);
+    cic_axis(py, g.nf, iy[0], iy[1], wy[0], wy[1]);
+    cic_axis(pz, g.nf, iz[0], iz[1], wz[0], wz[1]);
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      int dx = c & 1, dy = (c >> 1) & 1, dz = c >> 2;
+      float w = __fmul_rn(__fmul_rn(wx[dx], wy[dy]), wz[dz]);
+      atomicAdd(&rho_f[((int64_t)iz[dz] * g.nf + iy[dy]) * g.nf + ix[dx]], __fmul_rn(m, w));
+    }
+    if (rho_c) {
+      float s = 1.0f / (float)g.rc;
+      cic_axis(__fmul_rn(px, s), g.nc, ix[0], ix[1], wx[0], wx[1]);
+      cic_axis(__fmul_rn(py, s), g.nc, iy[0], iy[1], wy[0], wy[1]);
+      cic_axis(__fmul_rn(pz, s), g.nc, iz[0], iz[1], wz[0], wz[1]);
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        int dx = c & 1, dy = (c >> 1) & 1, dz = c >> 2;
+        float w = __fmul_rn(__fmul_rn(wx[dx], wy[dy]), wz[dz]);
+        atomicAdd(&rho_c[((int64_t)iz[dz] * g.nc + iy[dy]) * g.nc + ix[dx]], __fmul_rn(m, w));
+      }
+    }
+  }
+}
+
+// Fixed point: weights a1 = floor(f 2^20), mass split hi = (M a1 + 2^19) >> 20, lo = M - hi.
+__device__ __forceinline__ void fixed_axis(float x, int n, int& i0, int& i1, long long& a1) {
+  float f = floorf(x);
+  float fr = __fsub_rn(x, f);
+  a1 = (long long)__fmul_rn(fr, 1048576.0f);
+  i0 = (int)f;
+  if (i0 >= n) i0 -= n;
+  if (i0 < 0) i0 += n;
+  i1 = (i0 + 1 == n) ? 0 : i0 + 1;
+}
+__device__ __forceinline__ void fixed_split(long long M, long long a1, long long& lo, long long& hi) {
+  hi = (M * a1 + (1LL << 19)) >> 20;
+  lo = M - hi;
+}
+__device__ __forceinline__ void fixed_corners(long long M, const long long a[3], long long out[8]) {
+  long long mx[2], my[2], mz[2];
+  fixed_split(M, a[0], mx[0], mx[1]);
+#pragma unroll
+  for (int dx = 0; dx < 2; ++dx) {
+    fixed_split(mx[dx], a[1], my[0], my[1]);
+#pragma unroll
+    for (int dy = 0; dy < 2; ++dy) {
+      fixed_split(my[dy], a[2], mz[0], mz[1]);
+      out[dx + 2 * dy + 0] = mz[0];
+      out[dx + 2 * dy + 4] = mz[1];
+    }
+  }
+}
+
+__global__ void k_deposit_fixed_global(const float* x, int64_t n, long long M, Geo g, long long* rho_c,
+                                       long long* rho_f) {
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+    float pp[3] = {x[3 * p], x[3 * p + 1], x[3 * p + 2]};
+    for (int level = 0; level < 2; ++level) {
+      long long* rho = level == 0 ? rho_f : rho_c;
+      if (!rho) continue;
+      int nn = level == 0 ? g.nf : g.nc;
+      float s = level == 0 ? 1.0f : 1.0f / (float)g.rc;
+      int i0[3], i1[3];
+      long long a1[3];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) fixed_axis(__fmul_rn(pp[d], s), nn, i0[d], i1[d], a1[d]);
+      long long terms[8];
+      fixed_corners(M, a1, terms);
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        int dx = c & 1, dy = (c >> 1) & 1, dz = c >> 2;
+        int gx = dx ? i1[0] : i0[0], gy = dy ? i1[1] : i0[1], gz = dz ? i1[2] : i0[2];
+        atomicAdd(reinterpret_cast<unsigned long long*>(&rho[((int64_t)gz * nn + gy) * nn + gx]),
+                  (unsigned long long)terms[c]);
+      }
+    }
+  }
+}
+
+// CIC gather of a [3][n^3] field; fixed operation order so recomputation is bit-identical.
+__device__ __forceinline__ void gather(const float* __restrict__ F, int n, float px, float py, float pz, float a[3]) {
+  int ix[2], iy[2], iz[2];
+  float wx[2], wy[2], wz[2];
+  cic_axis(px, n, ix[0], ix[1], wx[0], wx[1]);
+  cic_axis(py, n, iy[0], iy[1], wy[0], wy[1]);
+  cic_axis(pz, n, iz[0], iz[1], wz[0], wz[1]);
+  const int64_t n3 = (int64_t)n * n * n;
+  float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    int dx = c & 1, dy = (c >> 1) & 1, dz = c >> 2;
+    float w = __fmul_rn(__fmul_rn(wx[dx], wy[dy]), wz[dz]);
+    int64_t idx = ((int64_t)iz[dz] * n + iy[dy]) * n + ix[dx];
+    s0 = __fmaf_rn(w, __ldg(F + idx), s0);
+    s1 = __fmaf_rn(w, __ldg(F + n3 + idx), s1);
+    s2 = __fmaf_rn(w, __ldg(F + 2 * n3 + idx), s2);
+  }
+  a[0] = s0;
+  a[1] = s1;
+  a[2] = s2;
+}
+
+__device__ __forceinline__ void accel_at(const Geo& g, const float* acc_c, const float* acc_f, float px, float py,
+                                         float pz, float a[3]) {
+  gather(acc_f, g.nf, px, py, pz, a);
+  if (g.two) {
+    float s = 1.0f / (float)g.rc;
+    float b[3];
+    gather(acc_c, g.nc, __fmul_rn(px, s), __fmul_rn(py, s), __fmul_rn(pz, s), b);
+    a[0] = __fadd_rn(b[0], a[0]);
+    a[1] = __fadd_rn(b[1], a[1]);
+    a[2] = __fadd_rn(b[2], a[2]);
+  }
+}
+
+__device__ __forceinline__ float wrap_pos(float x, float nf) {
+  if (x < 0.f) x = __fadd_rn(x, nf);
+  if (x >= nf) x = __fsub_rn(x, nf);
+  if (!(x >= 0.f && x < nf)) {      // moved more than one box length, or rounding onto nf
+    x = __fsub_rn(x, __fmul_rn(nf, floorf(__fdiv_rn(x, nf))));
+    if (!(x >= 0.f && x < nf)) x = 0.f;
+  }
+  return x;
+}
+
+// v' = v + c_k a ; x' = wrap(x + c_d v')
+__device__ __forceinline__ void kick_drift(float x[3], float v[3], const float a[3], float ck, float cd, float nf) {
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    v[d] = __fmaf_rn(ck, a[d], v[d]);
+    x[d] = wrap_pos(__fmaf_rn(cd, v[d], x[d]), nf);
+  }
+}
+
+__global__ void k_interpolate(const float* x, int64_t n, Geo g, const float* acc_c, const float* acc_f, float* a) {
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+    float r[3];
+    accel_at(g, acc_c, acc_f, x[3 * p], x[3 * p + 1], x[3 * p + 2], r);
+    a[3 * p] = r[0];
+    a[3 * p + 1] = r[1];
+    a[3 * p + 2] = r[2];
+  }
+}
+
+__global__ void k_kick_drift(float* x, float* v, int64_t n, Geo g, const float* acc_c, const float* acc_f, float ck,
+                             float cd) {
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+    float xx[3] = {x[3 * p], x[3 * p + 1], x[3 * p + 2]};
+    float vv[3] = {v[3 * p], v[3 * p + 1], v[3 * p + 2]};
+    float a[3];
+    accel_at(g, acc_c, acc_f, xx[0], xx[1], xx[2], a);
+    kick_drift(xx, vv, a, ck, cd, (float)g.nf);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      x[3 * p + d] = xx[d];
+      v[3 * p + d] = vv[d];
+    }
+  }
+}
+
+// ------------------------------------------------ recompress passes ------
+
+// Warp-aggregated count / rank of a cell key; key 0xffffffff = inactive lane.
+__device__ __forceinline__ void count_cell(uint32_t* counts, uint32_t key) {
+  unsigned peers = __match_any_sync(0xffffffffu, key);
+  int leader = __ffs(peers) - 1;
+  if (key != 0xffffffffu && (threadIdx.x & 31) == leader) atomicAdd(counts + key, (unsigned)__popc(peers));
+}
+__device__ __forceinline__ uint32_t take_rank(uint32_t* counts, uint32_t key) {
+  unsigned peers = __match_any_sync(0xffffffffu, key);
+  int lane = threadIdx.x & 31;
+  int leader = __ffs(peers) - 1;
+  unsigned old = 0;
+  if (key != 0xffffffffu && lane == leader) old = atomicSub(counts + key, (unsigned)__popc(peers));
+  old = __shfl_sync(0xffffffffu, old, leader);
+  unsigned below = __popc(peers & ((1u << lane) - 1u));
+  return old - (unsigned)__popc(peers) + below;
+}
+
+__device__ __forceinline__ void block_vmax(float m, uint32_t* vmax_bits) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0 && m > 0.f) atomicMax(vmax_bits, __float_as_uint(m));
+}
+
+__device__ __forceinline__ void write_codes(PCodesOut o, int64_t dst, const float x[3], const float v[3], float inv_r,
+                                            int ncmp, float s, bool vzero) {
+  const int half = o.vel16 ? 32768 : 128;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    int c, q;
+    encode_pos(x[d], inv_r, ncmp, c, q);
+    o.pos[3 * dst + d] = (uint8_t)q;
+    int qv = encode_vel(v[d], s, half, vzero);
+    if (o.vel16) reinterpret_cast<uint16_t*>(o.vel)[3 * dst + d] = (uint16_t)qv;
+    else reinterpret_cast<uint8_t*>(o.vel)[3 * dst + d] = (uint8_t)qv;
+  }
+}
+
+__device__ __forceinline__ uint32_t cell_key(const float x[3], float inv_r, int ncmp) {
+  int c[3], q;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) encode_pos(x[d], inv_r, ncmp, c[d], q);
+  return (uint32_t)(c[0] + ncmp * (c[1] + ncmp * c[2]));
+}
+
+// pm_compress passes over float input.  MODE 0: count cells (+ v_max); MODE 1: scatter codes.
+template <int MODE>
+__global__ void k_compress_pass(const float* x, const float* v, int64_t n, Geo g, uint32_t* counts,
+                                uint32_t* vmax_bits, const float* vmax_in, const int64_t* off, PCodesOut o,
+                                int* status) {
+  const float inv_r = 1.0f / (float)g.rcmp;
+  const float nf = (float)g.nf;
+  float vm = 0.f, s = 0.f;
+  bool vzero = false;
+  if (MODE == 1) {
+    vm = *o.vmax;
+    vzero = !(vm > 0.f);
+    s = vzero ? 0.f : __fdiv_rn(o.vel16 ? 32768.0f : 128.0f, vm);
+  }
+  float local_max = 0.f;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t nround = ((n + stride - 1) / stride) * stride;
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < nround; p += stride) {
+    uint32_t key = 0xffffffffu;
+    float xx[3], vv[3];
+    if (p < n) {
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        xx[d] = x[3 * p + d];
+        vv[d] = v[3 * p + d];
+        local_max = fmaxf(local_max, fabsf(vv[d]));
+      }
+      bool ok = xx[0] >= 0.f && xx[0] < nf && xx[1] >= 0.f && xx[1] < nf && xx[2] >= 0.f && xx[2] < nf;
+      if (ok) key = cell_key(xx, inv_r, g.ncmp);
+      else if (MODE == 0) atomicOr(status, ST_RANGE);
+    }
+    if (MODE == 0) {
+      count_cell(counts, key);
+    } else {
+      uint32_t r = take_rank(counts, key);
+      if (key != 0xffffffffu) {
+        int64_t dst = off[key] + r;
+        if (dst < n && r < 0x80000000u) write_codes(o, dst, xx, vv, inv_r, g.ncmp, s, vzero);
+        else atomicOr(status, ST_CORRUPT);
+      }
+    }
+  }
+  if (MODE == 0 && vmax_in == nullptr) block_vmax(local_max, vmax_bits);
+}
+
+__global__ void k_set_vmax(const uint32_t* vmax_bits, const float* vmax_in, float* out) {
+  *out = vmax_in ? *vmax_in : __uint_as_float(*vmax_bits);
+}
+
+// --------------------------------------------- fused passes over codes ----
+
+// Block of compression cells handled by one CTA: x cells [bx*RX, +RX), rows y [by*RY, +RY), z [bz*RZ, +RZ).
+struct CellBlock {
+  int ix0, iy0, iz0;
+};
+__device__ __forceinline__ CellBlock block_of(const Blk& bk, int bid) {
+  int nbx = bk.nbx, nby = bk.nby;
+  int bx = bid % nbx, by = (bid / nbx) % nby, bz = bid / (nbx * nby);
+  return CellBlock{bx * bk.RX, by * bk.RY, bz * bk.RZ};
+}
+
+// Loads the CSR offsets of the block's rows into smem: roff[r*(RX+1) + i], r = row (y fastest).
+__device__ __forceinline__ void load_row_offsets(const int64_t* off, const Geo& g, const Blk& bk, CellBlock cb,
+                                                 int64_t* roff) {
+  const int nrow = bk.RY * bk.RZ;
+  for (int i = threadIdx.x; i < nrow * (bk.RX + 1); i += blockDim.x) {
+    int r = i / (bk.RX + 1), k = i - r * (bk.RX + 1);
+    int iy = cb.iy0 + r % bk.RY, iz = cb.iz0 + r / bk.RY;
+    int64_t c = (int64_t)cb.ix0 + k + (int64_t)g.ncmp * (iy + (int64_t)g.ncmp * iz);
+    roff[i] = off[c];
+  }
+}
+
+// Index (0..RX-1) of the cell of stream index p within a row's offsets ro[0..RX].
+__device__ __forceinline__ int row_cell(const int64_t* ro, int RX, int64_t p) {
+  int lo = 0, hi = RX - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (ro[mid] <= p) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+template <typename Acc>
+__device__ __forceinline__ void smem_add(Acc* a, Acc v);
+template <> __device__ __forceinline__ void smem_add<float>(float* a, float v) { atomicAdd(a, v); }
+template <> __device__ __forceinline__ void smem_add<long long>(long long* a, long long v) {
+  atomicAdd(reinterpret_cast<unsigned long long*>(a), (unsigned long long)v);
+}
+template <typename Acc>
+__device__ __forceinline__ void global_add(Acc* a, Acc v);
+template <> __device__ __forceinline__ void global_add<float>(float* a, float v) { atomicAdd(a, v); }
+template <> __device__ __forceinline__ void global_add<long long>(long long* a, long long v) {
+  atomicAdd(reinterpret_cast<unsigned long long*>(a), (unsigned long long)v);
+}
+
+// Decode + deposit of both species for one cell block, binned in shared memory.
+// smem: row offsets (2 species), fine region (RX r + 1)(RY r + 1)(RZ r + 1),
+// coarse region (RX + 1)(RY + 1)(RZ + 1) when two-level.
+template <typename Acc>
+__global__ void k_deposit_codes(PCodes c0, PCodes c1, const int64_t* off0, const int64_t* off1, Geo g, Blk bk,
+                                float m0, float m1, long long M0, long long M1, Acc* rho_c, Acc* rho_f) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int r = g.rcmp;
+  const int fx = bk.RX * r + 1, fy = bk.RY * r + 1, fz = bk.RZ * r + 1;
+  const int cx = bk.RX + 1, cy = bk.RY + 1, cz = bk.RZ + 1;
+  const int nrow = bk.RY * bk.RZ;
+  int64_t* roff = reinterpret_cast<int64_t*>(smraw);
+  Acc* sf = reinterpret_cast<Acc*>(roff + 2 * nrow * (bk.RX + 1));
+  Acc* sc = sf + fx * fy * fz;
+  const int nsf = fx * fy * fz, nsc = g.two ? cx * cy * cz : 0;
+  for (int i = threadIdx.x; i < nsf + nsc; i += blockDim.x) sf[i] = (Acc)0;
+  const CellBlock cb = block_of(bk, blockIdx.x);
+  load_row_offsets(off0, g, bk, cb, roff);
+  load_row_offsets(off1, g, bk, cb, roff + nrow * (bk.RX + 1));
+  __syncthreads();
+  const float pscale = (float)r / 256.0f;
+  const int bxf = cb.ix0 * r, byf = cb.iy0 * r, bzf = cb.iz0 * r;
+  for (int s = 0; s < 2; ++s) {
+    const PCodes& cs = s ? c1 : c0;
+    const float m = s ? m1 : m0;
+    const long long M = s ? M1 : M0;
+    const int64_t* ro_s = roff + s * nrow * (bk.RX + 1);
+    for (int row = 0; row < nrow; ++row) {
+      const int64_t* ro = ro_s + row * (bk.RX + 1);
+      const int iy = cb.iy0 + row % bk.RY, iz = cb.iz0 + row / bk.RY;
+      // A corrupt stream (flagged by the scan) may claim more particles than
+      // exist; never read past the caller's n records.
+      const int64_t p0 = ro[0] < cs.n ? ro[0] : cs.n;
+      const int64_t p1 = ro[bk.RX] < cs.n ? ro[bk.RX] : cs.n;
+      for (int64_t p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
+        const int ixl = row_cell(ro, bk.RX, p);
+        const uint8_t* q = cs.pos + 3 * p;
+        float px = decode_pos(cb.ix0 + ixl, q[0], pscale);
+        float py = decode_pos(iy, q[1], pscale);
+        float pz = decode_pos(iz, q[2], pscale);
+        // fine CIC in local region coordinates (no wrap inside the block)
+        float flx = floorf(px), fly = floorf(py), flz = floorf(pz);
+        int lx = (int)flx - bxf, ly = (int)fly - byf, lz = (int)flz - bzf;
+        float w1[3] = {__fsub_rn(px, flx), __fsub_rn(py, fly), __fsub_rn(pz, flz)};
+        if constexpr (sizeof(Acc) == 4) {
+          float w0[3] = {__fsub_rn(1.f, w1[0]), __fsub_rn(1.f, w1[1]), __fsub_rn(1.f, w1[2])};
+#pragma unroll
+          for (int c = 0; c < 8; ++c) {
+            int dx = c & 1, dy = (c >> 1) & 1, dz = c >> 2;
+            float w = __fmul_rn(__fmul_rn(dx ? w1[0] : w0[0], dy ? w1[1] : w0[1]), dz ? w1[2] : w0[2]);
+            smem_add<Acc>(&sf[((lz + dz) * fy + (ly + dy)) * fx + (lx + dx)], (Acc)__fmul_rn(m, w));
+          }
+        } else {
+          long long a1[3] = {(long long)__fmul_rn(w1[0], 1048576.0f), (long long)__fmul_rn(w1[1], 1048576.0f),
+                             (long long)__fmul_rn(w1[2], 1048576.0f)};
+          long long terms[8];
+          fixed_corners(M, a1, terms);
+#pragma unroll
+          for (int c = 0; c < 8; ++c) {
+            int dx = c & 1, dy = (c >> 1) & 1, dz = c >> 2;
+            smem_add<Acc>(&sf[((lz + dz) * fy + (ly + dy)) * fx + (lx + dx)], (Acc)terms[c]);
+          }
+        }
+        if (g.two) {
+          // coarse cell == compression cell (coarse_ratio == cmp_ratio): stencil cells ix, ix+1
+          const float sc_inv = 1.0f / (float)g.rc;
+          float ux = __fmul_rn(px, sc_inv), uy = __fmul_rn(py, sc_inv), uz = __fmul_rn(pz, sc_inv);
+          float gx = floorf(ux), gy = floorf(uy), gz = floorf(uz);
+          int kx = (int)gx - cb.ix0, ky = (int)gy - cb.iy0, kz = (int)gz - cb.iz0;
+          float v1[3] = {__fsub_rn(ux, gx), __fsub_rn(uy, gy), __fsub_rn(uz, gz)};
+          if constexpr (sizeof(Acc) == 4) {
+            float v0[3] = {__fsub_rn(1.f, v1[0]), __fsub_rn(1.f, v1[1]), __fsub_rn(1.f, v1[2])};
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+              int dx = c & 1, dy = (c >> 1) & 1, dz = c >> 2;
+              float w = __fmul_rn(__fmul_rn(dx ? v1[0] : v0[0], dy ? v1[1] : v0[1]), dz ? v1[2] : v0[2]);
+              smem_add<Acc>(&sc[((kz + dz) * cy + (ky + dy)) * cx + (kx + dx)], (Acc)__fmul_rn(m, w));
+            }
+          } else {
+            long long a1[3] = {(long long)__fmul_rn(v1[0], 1048576.0f), (long long)__fmul_rn(v1[1], 1048576.0f),
+                               (long long)__fmul_rn(v1[2], 1048576.0f)};
+            long long terms[8];
+            fixed_corners(M, a1, terms);
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+              int dx = c & 1, dy = (c >> 1) & 1, dz = c >> 2;
+              smem_add<Acc>(&sc[((kz + dz) * cy + (ky + dy)) * cx + (kx + dx)], (Acc)terms[c]);
+            }
+          }
+        }
+      }
+    }
+  }
+  __syncthreads();
+  const int nf = g.nf;
+  for (int i = threadIdx.x; i < nsf; i += blockDim.x) {
+    Acc val = sf[i];
+    if (val == (Acc)0) continue;
+    int lx = i % fx, ly = (i / fx) % fy, lz = i / (fx * fy);
+    int gx = bxf + lx, gy = byf + ly, gz = bzf + lz;
+    if (gx >= nf) gx -= nf;
+    if (gy >= nf) gy -= nf;
+    if (gz >= nf) gz -= nf;
+    global_add<Acc>(&rho_f[((int64_t)gz * nf + gy) * nf + gx], val);
+  }
+  const int nc = g.nc;
+  for (int i = threadIdx.x; i < nsc; i += blockDim.x) {
+    Acc val = sc[i];
+    if (val == (Acc)0) continue;
+    int lx = i % cx, ly = (i / cx) % cy, lz = i / (cx * cy);
+    int gx = cb.ix0 + lx, gy = cb.iy0 + ly, gz = cb.iz0 + lz;
+    if (gx >= nc) gx -= nc;
+    if (gy >= nc) gy -= nc;
+    if (gz >= nc) gz -= nc;
+    global_add<Acc>(&rho_c[((int64_t)gz * nc + gy) * nc + gx], val);
+  }
+}
+
+// Decode + interpolate + kick + drift of one species for one cell block.
+// MODE 0: histogram of new cells + v_max; MODE 1: rank, encode, scatter.
+template <int MODE>
+__global__ void k_ikd_codes(PCodes in, const int64_t* off, Geo g, Blk bk, const float* acc_c, const float* acc_f,
+                            float ck, float cd, uint32_t* counts, uint32_t* vmax_bits, const int64_t* newoff,
+                            PCodesOut o, int* status) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  int64_t* roff = reinterpret_cast<int64_t*>(smraw);
+  const int nrow = bk.RY * bk.RZ;
+  const CellBlock cb = block_of(bk, blockIdx.x);
+  load_row_offsets(off, g, bk, cb, roff);
+  __syncthreads();
+  const float pscale = (float)g.rcmp / 256.0f;
+  const float inv_r = 1.0f / (float)g.rcmp;
+  const float nf = (float)g.nf;
+  const int half = in.vel16 ? 32768 : 128;
+  const float vm_in = *in.vmax;
+  const float step = __fmul_rn(vm_in, 1.0f / (float)half);
+  float s_out = 0.f;
+  bool vzero = false;
+  if (MODE == 1) {
+    float vm = *o.vmax;
+    vzero = !(vm > 0.f);
+    s_out = vzero ? 0.f : __fdiv_rn(o.vel16 ? 32768.0f : 128.0f, vm);
+  }
+  float local_max = 0.f;
+  for (int row = 0; row < nrow; ++row) {
+    const int64_t* ro = roff + row * (bk.RX + 1);
+    const int iy = cb.iy0 + row % bk.RY, iz = cb.iz0 + row / bk.RY;
+    const int64_t p0 = ro[0] < in.n ? ro[0] : in.n;
+    const int64_t p1 = ro[bk.RX] < in.n ? ro[bk.RX] : in.n;
+    const int64_t span = p1 - p0;
+    const int64_t rounds = (span + blockDim.x - 1) / blockDim.x;
+    for (int64_t it = 0; it < rounds; ++it) {
+      const int64_t p = p0 + it * blockDim.x + threadIdx.x;
+      uint32_t key = 0xffffffffu;
+      float x[3], v[3];
+      if (p < p1) {
+        const int ixl = row_cell(ro, bk.RX, p);
+        const uint8_t* q = in.pos + 3 * p;
+        x[0] = decode_pos(cb.ix0 + ixl, q[0], pscale);
+        x[1] = decode_pos(iy, q[1], pscale);
+        x[2] = decode_pos(iz, q[2], pscale);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          int qv = in.vel16 ? (int)reinterpret_cast<const uint16_t*>(in.vel)[3 * p + d]
+                            : (int)reinterpret_cast<const uint8_t*>(in.vel)[3 * p + d];
+          v[d] = decode_vel(qv, half, step);
+        }
+        float a[3];
+        accel_at(g, acc_c, acc_f, x[0], x[1], x[2], a);
+        kick_drift(x, v, a, ck, cd, nf);
+        key = cell_key(x, inv_r, g.ncmp);
+        local_max = fmaxf(local_max, fmaxf(fabsf(v[0]), fmaxf(fabsf(v[1]), fabsf(v[2]))));
+      }
+      if (MODE == 0) {
+        count_cell(counts, key);
+      } else {
+        uint32_t rk = take_rank(counts, key);
+        if (key != 0xffffffffu) {
+          int64_t dst = newoff[key] + rk;
+          if (dst < in.n && rk < 0x80000000u) write_codes(o, dst, x, v, inv_r, g.ncmp, s_out, vzero);
+          else atomicOr(status, ST_CORRUPT);
+        }
+      }
+    }
+  }
+  if (MODE == 0) block_vmax(local_max, vmax_bits);
+}
+
+// ------------------------------------------------------------ launchers --
+
+static int grid_for(int64_t n, int threads) {
+  int64_t b = (n + threads - 1) / threads;
+  if (b > 152 * 32) b = 152 * 32;
+  return (int)(b < 1 ? 1 : b);
+}
+
+cudaError_t launch_decompress(const PCodes& in, const int64_t* off, const Geo& g, float* x, float* v, cudaStream_t st) {
+  if (in.n == 0) return cudaSuccess;
+  k_decompress<<<grid_for(in.n, 256), 256, 0, st>>>(in, off, g, x, v);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_deposit(const float* x, int64_t n, float m, const Geo& g, float* rho_c, float* rho_f, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  k_deposit_global<<<grid_for(n, 256), 256, 0, st>>>(x, n, m, g, rho_c, rho_f);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_deposit_fixed(const float* x, int64_t n, long long M, const Geo& g, long long* rho_c,
+                                 long long* rho_f, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  k_deposit_fixed_global<<<grid_for(n, 256), 256, 0, st>>>(x, n, M, g, rho_c, rho_f);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_interpolate(const float* x, int64_t n, const Geo& g, const float* acc_c, const float* acc_f,
+                               float* a, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  k_interpolate<<<grid_for(n, 256), 256, 0, st>>>(x, n, g, acc_c, acc_f, a);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_kick_drift(float* x, float* v, int64_t n, const Geo& g, const float* acc_c, const float* acc_f,
+                              float ck, float cd, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  k_kick_drift<<<grid_for(n, 256), 256, 0, st>>>(x, v, n, g, acc_c, acc_f, ck, cd);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_compress(const float* x, const float* v, int64_t n, const Geo& g, uint32_t* counts,
+                            uint32_t* vmax_bits, const float* vmax_in, int64_t* off, pm_codes_t& out, bool vel16,
+                            void* partial, int* status, cudaStream_t st) {
+  PCodesOut o{out.pos, out.vel, out.vmax, vel16};
+  cudaMemsetAsync(vmax_bits, 0, sizeof(uint32_t), st);
+  int grid = grid_for(n > 0 ? n : 1, 256);
+  k_compress_pass<0><<<grid, 256, 0, st>>>(x, v, n, g, counts, vmax_bits, vmax_in, off, o, status);
+  k_set_vmax<<<1, 1, 0, st>>>(vmax_bits, vmax_in, out.vmax);
+  cudaError_t e = scan_counts(counts, g.ncell, n, off, out, partial, status, st);
+  if (e != cudaSuccess) return e;
+  k_compress_pass<1><<<grid, 256, 0, st>>>(x, v, n, g, counts, vmax_bits, vmax_in, off, o, status);
+  note_launches(3);
+  return cudaGetLastError();
+}
+
+size_t deposit_codes_smem(const Geo& g, const Blk& bk, bool fixed) {
+  size_t acc = fixed ? 8 : 4;
+  size_t nrow = (size_t)bk.RY * bk.RZ;
+  size_t fine = (size_t)(bk.RX * g.rcmp + 1) * (bk.RY * g.rcmp + 1) * (bk.RZ * g.rcmp + 1);
+  size_t coarse = g.two ? (size_t)(bk.RX + 1) * (bk.RY + 1) * (bk.RZ + 1) : 0;
+  return 2 * nrow * (bk.RX + 1) * sizeof(int64_t) + (fine + coarse) * acc;
+}
+
+cudaError_t launch_deposit_codes(const PCodes& c0, const PCodes& c1, const int64_t* off0, const int64_t* off1,
+                                 const Geo& g, const Blk& bk, float m0, float m1, long long M0, long long M1,
+                                 void* rho_c, void* rho_f, bool fixed, cudaStream_t st) {
+  size_t smem = deposit_codes_smem(g, bk, fixed);
+  int nblk = bk.nbx * bk.nby * bk.nbz;
+  if (fixed) {
+    cudaFuncSetAttribute(k_deposit_codes<long long>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_deposit_codes<long long><<<nblk, 256, smem, st>>>(c0, c1, off0, off1, g, bk, m0, m1, M0, M1,
+                                                       static_cast<long long*>(rho_c), static_cast<long long*>(rho_f));
+  } else {
+    cudaFuncSetAttribute(k_deposit_codes<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_deposit_codes<float><<<nblk, 256, smem, st>>>(c0, c1, off0, off1, g, bk, m0, m1, M0, M1,
+                                                   static_cast<float*>(rho_c), static_cast<float*>(rho_f));
+  }
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ikd_codes(int mode, const PCodes& in, const int64_t* off, const Geo& g, const Blk& bk,
+                             const float* acc_c, const float* acc_f, float ck, float cd, uint32_t* counts,
+                             uint32_t* vmax_bits, const int64_t* newoff, const PCodesOut& o, int* status,
+                             cudaStream_t st) {
+  size_t smem = (size_t)bk.RY * bk.RZ * (bk.RX + 1) * sizeof(int64_t);
+  int nblk = bk.nbx * bk.nby * bk.nbz;
+  if (mode == 0)
+    k_ikd_codes<0><<<nblk, 256, smem, st>>>(in, off, g, bk, acc_c, acc_f, ck, cd, counts, vmax_bits, newoff, o,
+                                            status);
+  else
+    k_ikd_codes<1><<<nblk, 256, smem, st>>>(in, off, g, bk, acc_c, acc_f, ck, cd, counts, vmax_bits, newoff, o,
+                                            status);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_set_vmax(const uint32_t* vmax_bits, float* out, cudaStream_t st) {
+  k_set_vmax<<<1, 1, 0, st>>>(vmax_bits, nullptr, out);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+}  // namespace pm

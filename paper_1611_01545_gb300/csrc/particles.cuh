@@ -1,0 +1,66 @@
+// Device-side views and launchers of the particle kernels (particles.cu).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "pm_common.cuh"
+
+namespace pm {
+
+// Geometry as the particle kernels see it (plain values, passed by value).
+struct Geo {
+  int nf, rc, nc, rcmp, ncmp;
+  int64_t ncell;
+  bool two;
+};
+
+// Cell-block decomposition of the compression mesh for the fused passes.
+struct Blk {
+  int RX, RY, RZ;     // cells per block along x, y, z
+  int nbx, nby, nbz;  // blocks along x, y, z
+};
+
+struct PCodes {
+  const uint8_t* pos;
+  const void* vel;
+  const float* vmax;
+  int64_t n;
+  bool vel16;
+};
+
+struct PCodesOut {
+  uint8_t* pos;
+  void* vel;
+  float* vmax;
+  bool vel16;
+};
+
+cudaError_t scan_codes(const pm_codes_t& in, int64_t ncell, int64_t* off, void* partial_ws, int* status,
+                       cudaStream_t st);
+cudaError_t scan_counts(const uint32_t* counts, int64_t ncell, int64_t expect, int64_t* off, pm_codes_t& out,
+                        void* partial_ws, int* status, cudaStream_t st);
+size_t scan_partial_bytes(int64_t ncell);
+
+cudaError_t launch_decompress(const PCodes& in, const int64_t* off, const Geo& g, float* x, float* v, cudaStream_t st);
+cudaError_t launch_deposit(const float* x, int64_t n, float m, const Geo& g, float* rho_c, float* rho_f,
+                           cudaStream_t st);
+cudaError_t launch_deposit_fixed(const float* x, int64_t n, long long M, const Geo& g, long long* rho_c,
+                                 long long* rho_f, cudaStream_t st);
+cudaError_t launch_interpolate(const float* x, int64_t n, const Geo& g, const float* acc_c, const float* acc_f,
+                               float* a, cudaStream_t st);
+cudaError_t launch_kick_drift(float* x, float* v, int64_t n, const Geo& g, const float* acc_c, const float* acc_f,
+                              float ck, float cd, cudaStream_t st);
+cudaError_t launch_compress(const float* x, const float* v, int64_t n, const Geo& g, uint32_t* counts,
+                            uint32_t* vmax_bits, const float* vmax_in, int64_t* off, pm_codes_t& out, bool vel16,
+                            void* partial, int* status, cudaStream_t st);
+size_t deposit_codes_smem(const Geo& g, const Blk& bk, bool fixed);
+cudaError_t launch_deposit_codes(const PCodes& c0, const PCodes& c1, const int64_t* off0, const int64_t* off1,
+                                 const Geo& g, const Blk& bk, float m0, float m1, long long M0, long long M1,
+                                 void* rho_c, void* rho_f, bool fixed, cudaStream_t st);
+cudaError_t launch_ikd_codes(int mode, const PCodes& in, const int64_t* off, const Geo& g, const Blk& bk,
+                             const float* acc_c, const float* acc_f, float ck, float cd, uint32_t* counts,
+                             uint32_t* vmax_bits, const int64_t* newoff, const PCodesOut& o, int* status,
+                             cudaStream_t st);
+cudaError_t launch_set_vmax(const uint32_t* vmax_bits, float* out, cudaStream_t st);
+
+}  // namespace pm

@@ -1,0 +1,269 @@
+// Fourier-space PM solve on periodic windows (paper Sec. 2.1, Eqs. 1-3).
+//
+// One "problem" is an N^3 window of a periodic source mesh whose cell 0 sits
+// at origin p*t - b (p = problem coordinates): the whole coarse / single mesh
+// (t = N, b = 0), or one buffered fine tile (Fig. 1; N = T = t + 2b).  Three
+// kernels per batch of problems:
+//   A  per z plane: load the real window plane, real-to-complex along x (two
+//      rows packed as one complex row), complex FFT along y -> half spectrum;
+//   B  per ky: FFT along z, multiply by the precomputed kernel of each force
+//      component (i K_d), inverse FFT along z, keep the output z range;
+//   C  per (output z, component): inverse FFT along y, complex-to-real along
+//      x (two rows packed), store the output interior into the destination
+//      mesh [3][n][n][n].
+// The kernel tables already contain the 1/N^3 (tiles) or 1/V (periodic)
+// normalisation, so both transform directions are unnormalised.
+#include <cuda_runtime.h>
+
+#include "fft.cuh"
+#include "pm_common.cuh"
+
+namespace pm {
+using namespace pmfft;
+
+template <int N> struct SolveCfg {
+  static constexpr int NH = N / 2 + 1;
+  static constexpr int threads = (N >= 96) ? 512 : 256;
+  static constexpr size_t smem_a = sizeof(float2) * (N + (size_t)N * N / 2 + (size_t)N * NH);
+  static constexpr size_t smem_b = sizeof(float2) * (N + 2 * (size_t)N * NH);
+};
+
+struct SolveArgs {
+  const void* src;
+  int src_fixed;
+  int src_n;
+  int nts;
+  int t, b;
+  int p0;
+  float2* spec;
+  float2* spec3;
+  const float* kern;
+  const float2* tw;
+  float* dst;
+};
+
+__device__ __forceinline__ int pmod(int a, int n) {
+  int r = a % n;
+  return r < 0 ? r + n : r;
+}
+
+__device__ __forceinline__ void problem_origin(const SolveArgs& a, int p, int& ox, int& oy, int& oz) {
+  int px = p % a.nts, py = (p / a.nts) % a.nts, pz = p / (a.nts * a.nts);
+  ox = px * a.t - a.b;
+  oy = py * a.t - a.b;
+  oz = pz * a.t - a.b;
+}
+
+__device__ __forceinline__ float load_src(const SolveArgs& a, int64_t idx) {
+  if (a.src_fixed) {
+    long long v = static_cast<const long long*>(a.src)[idx];
+    return (float)((double)v * 2.3283064365386963e-10);  // 2^-32
+  }
+  return static_cast<const float*>(a.src)[idx];
+}
+
+template <int N>
+__global__ void __launch_bounds__(SolveCfg<N>::threads) k_solve_a(SolveArgs a) {
+  constexpr int NH = SolveCfg<N>::NH;
+  extern __shared__ float2 sm[];
+  float2* tw = sm;
+  float2* W = sm + N;               // N/2 packed rows of N
+  float2* P = W + N * N / 2;        // N rows (y) of NH
+  for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = a.tw[i];
+  const int z = blockIdx.x;
+  const int pb = blockIdx.y;
+  int ox, oy, oz;
+  problem_origin(a, a.p0 + pb, ox, oy, oz);
+  const int n = a.src_n;
+  const int gz = pmod(oz + z, n);
+  for (int i = threadIdx.x; i < N * N; i += blockDim.x) {
+    int y = i / N, x = i - y * N;
+    int gy = pmod(oy + y, n), gx = pmod(ox + x, n);
+    float v = load_src(a, ((int64_t)gz * n + gy) * n + gx);
+    float* w = reinterpret_cast<float*>(&W[(y >> 1) * N + x]);
+    w[y & 1] = v;
+  }
+  __syncthreads();
+  fft_fwd<N>(W, N / 2, N, 1, tw);
+  // Unpack the two real rows of each packed row: A = (Z_k + conj Z_-k)/2, B = (Z_k - conj Z_-k)/(2i).
+  for (int i = threadIdx.x; i < (N / 2) * NH; i += blockDim.x) {
+    int j = i / NH, k = i - j * NH;
+    float2 zk = W[j * N + slot_of<N>(k)];
+    float2 zm = W[j * N + slot_of<N>((N - k) % N)];
+    P[(2 * j) * NH + k] = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
+    P[(2 * j + 1) * NH + k] = make_float2(0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));
+  }
+  __syncthreads();
+  fft_fwd<N>(P, NH, 1, NH, tw);
+  float2* out = a.spec + ((size_t)pb * N + z) * N * NH;
+  for (int i = threadIdx.x; i < N * NH; i += blockDim.x) out[i] = P[i];
+}
+
+template <int N>
+__global__ void __launch_bounds__(SolveCfg<N>::threads) k_solve_b(SolveArgs a) {
+  constexpr int NH = SolveCfg<N>::NH;
+  extern __shared__ float2 sm[];
+  float2* tw = sm;
+  float2* F = sm + N;          // [z][kx]
+  float2* G = F + N * NH;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = a.tw[i];
+  const int ys = blockIdx.x;   // ky in slot order
+  const int pb = blockIdx.y;
+  const float2* in = a.spec + (size_t)pb * N * N * NH;
+  for (int i = threadIdx.x; i < N * NH; i += blockDim.x) {
+    int z = i / NH, kx = i - z * NH;
+    F[i] = in[((size_t)z * N + ys) * NH + kx];
+  }
+  __syncthreads();
+  fft_fwd<N>(F, NH, 1, NH, tw);
+  for (int d = 0; d < 3; ++d) {
+    const float* K = a.kern + (size_t)d * N * N * NH;
+    for (int i = threadIdx.x; i < N * NH; i += blockDim.x) {
+      int zs = i / NH, kx = i - zs * NH;
+      float k = K[((size_t)zs * N + ys) * NH + kx];
+      float2 f = F[i];
+      G[i] = make_float2(-f.y * k, f.x * k);   // i K f
+    }
+    __syncthreads();
+    fft_inv<N>(G, NH, 1, NH, tw);
+    float2* out = a.spec3 + ((size_t)pb * 3 + d) * a.t * N * NH;
+    for (int i = threadIdx.x; i < a.t * NH; i += blockDim.x) {
+      int zo = i / NH, kx = i - zo * NH;
+      out[((size_t)zo * N + ys) * NH + kx] = G[(zo + a.b) * NH + kx];
+    }
+    __syncthreads();
+  }
+}
+
+template <int N>
+__global__ void __launch_bounds__(SolveCfg<N>::threads) k_solve_c(SolveArgs a) {
+  constexpr int NH = SolveCfg<N>::NH;
+  extern __shared__ float2 sm[];
+  float2* tw = sm;
+  float2* P = sm + N;          // [y][kx]
+  float2* W = P + N * NH;      // t/2 packed rows of N
+  for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = a.tw[i];
+  const int zo = blockIdx.x;
+  const int d = blockIdx.y;
+  const int pb = blockIdx.z;
+  const float2* in = a.spec3 + (((size_t)pb * 3 + d) * a.t + zo) * N * NH;
+  for (int i = threadIdx.x; i < N * NH; i += blockDim.x) P[i] = in[i];
+  __syncthreads();
+  fft_inv<N>(P, NH, 1, NH, tw);
+  const int half_rows = a.t / 2;
+  for (int i = threadIdx.x; i < half_rows * N; i += blockDim.x) {
+    int j = i / N, k = i - j * N;
+    int ya = a.b + 2 * j, yb = ya + 1;
+    float2 A, B;
+    if (k <= N / 2) {
+      A = P[ya * NH + k];
+      B = P[yb * NH + k];
+    } else {
+      A = conjf2(P[ya * NH + (N - k)]);
+      B = conjf2(P[yb * NH + (N - k)]);
+    }
+    W[j * N + slot_of<N>(k)] = make_float2(A.x - B.y, A.y + B.x);   // A + i B
+  }
+  __syncthreads();
+  fft_inv<N>(W, half_rows, N, 1, tw);
+  int ox, oy, oz;
+  problem_origin(a, a.p0 + pb, ox, oy, oz);
+  const int n = a.src_n;
+  // Output cells are interior cells: origin + b + local lies inside [0, n) without wrap.
+  const int gz = oz + a.b + zo;
+  float* dst = a.dst + (size_t)d * n * n * n;
+  for (int i = threadIdx.x; i < a.t * a.t; i += blockDim.x) {
+    int yl = i / a.t, xl = i - yl * a.t;
+    int j = yl >> 1;
+    float2 w = W[j * N + a.b + xl];
+    float v = (yl & 1) ? w.y : w.x;
+    int gy = oy + a.b + yl, gx = ox + a.b + xl;
+    dst[((int64_t)gz * n + gy) * n + gx] = v;
+  }
+}
+
+template <int N>
+__global__ void k_tile_window(const float* src, int src_n, int nts, int t, int b, int64_t tile, float* out) {
+  int px = (int)(tile % nts), py = (int)((tile / nts) % nts), pz = (int)(tile / ((int64_t)nts * nts));
+  int ox = px * t - b, oy = py * t - b, oz = pz * t - b;
+  int64_t total = (int64_t)N * N * N;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    int x = (int)(i % N), y = (int)((i / N) % N), z = (int)(i / ((int64_t)N * N));
+    int gx = pmod(ox + x, src_n), gy = pmod(oy + y, src_n), gz = pmod(oz + z, src_n);
+    out[i] = src[((int64_t)gz * src_n + gy) * src_n + gx];
+  }
+}
+
+template <int N>
+static cudaError_t solve_n(const SolvePlan& p, const void* src, bool fixed, float* dst, cudaStream_t st, Timer* tm) {
+  using C = SolveCfg<N>;
+  static bool attr_done = false;
+  if (!attr_done) {
+    cudaFuncSetAttribute(k_solve_a<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem_a);
+    cudaFuncSetAttribute(k_solve_b<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem_b);
+    cudaFuncSetAttribute(k_solve_c<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem_a);
+    attr_done = true;
+  }
+  const int nprob = p.nts * p.nts * p.nts;
+  for (int p0 = 0; p0 < nprob; p0 += p.batch) {
+    int nb = (nprob - p0 < p.batch) ? (nprob - p0) : p.batch;
+    SolveArgs a{src, fixed ? 1 : 0, p.src_n, p.nts, p.t, p.b, p0, p.spec, p.spec3, p.kern, p.tw, dst};
+    {
+      TimedScope ts(tm, N == p.src_n && p.b == 0 ? "fft_a_mesh" : "fft_a_tiles", st);
+      k_solve_a<N><<<dim3(N, nb), C::threads, C::smem_a, st>>>(a);
+    }
+    {
+      TimedScope ts(tm, N == p.src_n && p.b == 0 ? "fft_b_mesh" : "fft_b_tiles", st);
+      k_solve_b<N><<<dim3(N, nb), C::threads, C::smem_b, st>>>(a);
+    }
+    {
+      TimedScope ts(tm, N == p.src_n && p.b == 0 ? "fft_c_mesh" : "fft_c_tiles", st);
+      k_solve_c<N><<<dim3(p.t, 3, nb), C::threads, C::smem_a, st>>>(a);
+    }
+    note_launches(3);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t solve_launch(const SolvePlan& p, const void* src, bool fixed, float* dst, cudaStream_t st, Timer* tm) {
+  switch (p.N) {
+    case 16: return solve_n<16>(p, src, fixed, dst, st, tm);
+    case 32: return solve_n<32>(p, src, fixed, dst, st, tm);
+    case 48: return solve_n<48>(p, src, fixed, dst, st, tm);
+    case 64: return solve_n<64>(p, src, fixed, dst, st, tm);
+    case 96: return solve_n<96>(p, src, fixed, dst, st, tm);
+    case 128: return solve_n<128>(p, src, fixed, dst, st, tm);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+size_t solve_smem_max(int N) {
+  switch (N) {
+    case 16: return SolveCfg<16>::smem_b > SolveCfg<16>::smem_a ? SolveCfg<16>::smem_b : SolveCfg<16>::smem_a;
+    case 32: return SolveCfg<32>::smem_b > SolveCfg<32>::smem_a ? SolveCfg<32>::smem_b : SolveCfg<32>::smem_a;
+    case 48: return SolveCfg<48>::smem_b > SolveCfg<48>::smem_a ? SolveCfg<48>::smem_b : SolveCfg<48>::smem_a;
+    case 64: return SolveCfg<64>::smem_b > SolveCfg<64>::smem_a ? SolveCfg<64>::smem_b : SolveCfg<64>::smem_a;
+    case 96: return SolveCfg<96>::smem_b > SolveCfg<96>::smem_a ? SolveCfg<96>::smem_b : SolveCfg<96>::smem_a;
+    case 128: return SolveCfg<128>::smem_b > SolveCfg<128>::smem_a ? SolveCfg<128>::smem_b : SolveCfg<128>::smem_a;
+    default: return 0;
+  }
+}
+
+cudaError_t tile_window_launch(const SolvePlan& p, const float* src, int64_t tile, float* out, cudaStream_t st) {
+  int blocks = 256;
+  switch (p.N) {
+    case 16: k_tile_window<16><<<blocks, 256, 0, st>>>(src, p.src_n, p.nts, p.t, p.b, tile, out); break;
+    case 32: k_tile_window<32><<<blocks, 256, 0, st>>>(src, p.src_n, p.nts, p.t, p.b, tile, out); break;
+    case 48: k_tile_window<48><<<blocks, 256, 0, st>>>(src, p.src_n, p.nts, p.t, p.b, tile, out); break;
+    case 64: k_tile_window<64><<<blocks, 256, 0, st>>>(src, p.src_n, p.nts, p.t, p.b, tile, out); break;
+    case 96: k_tile_window<96><<<blocks, 256, 0, st>>>(src, p.src_n, p.nts, p.t, p.b, tile, out); break;
+    case 128: k_tile_window<128><<<blocks, 256, 0, st>>>(src, p.src_n, p.nts, p.t, p.b, tile, out); break;
+    default: return cudaErrorInvalidValue;
+  }
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+}  // namespace pm

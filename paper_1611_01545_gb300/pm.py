@@ -1,0 +1,245 @@
+"""Thin Python binding over the C ABI of libpm (include/pm.h).
+
+Every function here marshals arguments and calls one library entry point;
+torch supplies device memory and the current CUDA stream.  All arithmetic
+of the PM step runs in the library's CUDA kernels.
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+from typing import Dict, Optional, Sequence, Tuple
+
+import torch
+
+from . import _lib
+from ._lib import pm_codes_t, pm_config_t
+
+
+class PMError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{_lib.ERROR_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+@dataclass
+class Codes:
+    """One species' compressed state in device memory (layout of pm_codes_t)."""
+    n: int
+    cnt: torch.Tensor       # uint8 [n_cmp^3]
+    esc: torch.Tensor       # int32 viewed as uint32 pairs [esc_cap, 2]
+    n_esc: torch.Tensor     # int32 [1]
+    pos: torch.Tensor       # uint8 [n, 3]
+    vel: torch.Tensor       # int16 (uint16 bits) or uint8 [n, 3]
+    vmax: torch.Tensor      # float32 [1]
+
+    @staticmethod
+    def empty(n: int, n_cmp: int, vel_bits: int, esc_cap: Optional[int] = None, device="cuda") -> "Codes":
+        ncell = n_cmp ** 3
+        if esc_cap is None:
+            esc_cap = max(1, min(ncell, n // 255 + 1))
+        vdt = torch.int16 if vel_bits == 16 else torch.uint8
+        return Codes(n=n, cnt=torch.empty(ncell, dtype=torch.uint8, device=device),
+                     esc=torch.zeros((esc_cap, 2), dtype=torch.int32, device=device),
+                     n_esc=torch.zeros(1, dtype=torch.int32, device=device),
+                     pos=torch.empty((n, 3), dtype=torch.uint8, device=device),
+                     vel=torch.empty((n, 3), dtype=vdt, device=device),
+                     vmax=torch.zeros(1, dtype=torch.float32, device=device))
+
+    def struct(self) -> pm_codes_t:
+        return pm_codes_t(self.n, self.cnt.data_ptr(), self.esc.data_ptr(), self.esc.shape[0],
+                          self.n_esc.data_ptr(), self.pos.data_ptr(), self.vel.data_ptr(), self.vmax.data_ptr())
+
+    def to(self, device, pin: bool = False) -> "Codes":
+        def mv(t):
+            out = t.to(device)
+            return out.pin_memory() if pin and out.device.type == "cpu" else out
+        return Codes(self.n, mv(self.cnt), mv(self.esc), mv(self.n_esc), mv(self.pos), mv(self.vel), mv(self.vmax))
+
+    def vel_u16(self) -> torch.Tensor:
+        """Velocity codes as int64 values 0..65535 (or 0..255)."""
+        v = self.vel.to(torch.int64)
+        return v & 0xFFFF if self.vel.dtype == torch.int16 else v
+
+
+def config_struct(cfg: Dict) -> pm_config_t:
+    c = pm_config_t()
+    c.n_fine = int(cfg["n_fine"])
+    c.coarse_ratio = int(cfg.get("coarse_ratio", 1))
+    c.tile = int(cfg.get("tile", cfg["n_fine"]))
+    c.buffer = int(cfg.get("buffer", 0))
+    c.cmp_ratio = int(cfg.get("cmp_ratio", 4))
+    c.vel_bits = int(cfg.get("vel_bits", 16))
+    c.deposit_mode = int(cfg.get("deposit_mode", 0))
+    c.tile_batch = int(cfg.get("tile_batch", 0))
+    c.G = float(cfg["G"])
+    c.mass[0], c.mass[1] = (float(m) for m in cfg["mass"])
+    cnt = cfg.get("count", (0, 0))
+    c.count[0], c.count[1] = (int(k) for k in cnt)
+    c.r_split = float(cfg.get("r_split", 0.0))
+    c.r_cut = float(cfg.get("r_cut", 0.0))
+    return c
+
+
+class PM:
+    """Handle around pm_init / pm_destroy with one method per entry point."""
+
+    def __init__(self, cfg: Dict):
+        self.lib = _lib.load()
+        self.cfg = dict(cfg)
+        self._cs = config_struct(cfg)
+        h = ctypes.c_void_p()
+        rc = self.lib.pm_init(ctypes.byref(self._cs), ctypes.byref(h))
+        if rc != _lib.PM_OK:
+            raise PMError(rc, "pm_init failed")
+        self.h = h
+        g = [ctypes.c_int64() for _ in range(4)]
+        self.lib.pm_geometry(self.h, *[ctypes.byref(x) for x in g])
+        self.n_cmp, self.n_coarse, self.n_tiles, self.tile_edge = (int(x.value) for x in g)
+        self.n_fine = int(cfg["n_fine"])
+        self.two_level = int(cfg.get("coarse_ratio", 1)) > 1
+        self.vel_bits = int(cfg.get("vel_bits", 16))
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.pm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _err(self, rc: int):
+        if rc != _lib.PM_OK:
+            buf = ctypes.create_string_buffer(512)
+            self.lib.pm_last_error(self.h, buf, 512)
+            raise PMError(rc, buf.value.decode())
+
+    # ---- entry points -------------------------------------------------
+    def check(self, stream=None):
+        self._err(self.lib.pm_check(self.h, _stream(stream)))
+
+    def empty_codes(self, n: int, esc_cap: Optional[int] = None) -> Codes:
+        return Codes.empty(n, self.n_cmp, self.vel_bits, esc_cap)
+
+    def decompress(self, species: int, codes: Codes, stream=None) -> Tuple[torch.Tensor, torch.Tensor]:
+        x = torch.empty((codes.n, 3), dtype=torch.float32, device="cuda")
+        v = torch.empty((codes.n, 3), dtype=torch.float32, device="cuda")
+        cs = codes.struct()
+        self._err(self.lib.pm_decompress(self.h, species, ctypes.byref(cs), _ptr(x), _ptr(v), _stream(stream)))
+        return x, v
+
+    def compress(self, species: int, x: torch.Tensor, v: torch.Tensor, vmax: Optional[torch.Tensor] = None,
+                 out: Optional[Codes] = None, stream=None) -> Codes:
+        n = x.shape[0]
+        out = out if out is not None else self.empty_codes(n)
+        cs = out.struct()
+        self._err(self.lib.pm_compress(self.h, species, _ptr(x.contiguous()), _ptr(v.contiguous()), _ptr(vmax),
+                                       ctypes.byref(cs), _stream(stream)))
+        return out
+
+    def zeros_meshes(self, fixed: bool = False):
+        dt = torch.int64 if fixed else torch.float32
+        rf = torch.zeros((self.n_fine,) * 3, dtype=dt, device="cuda")
+        rc = torch.zeros((self.n_coarse,) * 3, dtype=dt, device="cuda") if self.two_level else None
+        return rc, rf
+
+    def deposit(self, species: int, x: torch.Tensor, rho_coarse, rho_fine, stream=None):
+        self._err(self.lib.pm_deposit(self.h, species, _ptr(x), x.shape[0], _ptr(rho_coarse), _ptr(rho_fine),
+                                      _stream(stream)))
+
+    def deposit_fixed(self, species: int, x: torch.Tensor, rho_coarse, rho_fine, stream=None):
+        self._err(self.lib.pm_deposit_fixed(self.h, species, _ptr(x), x.shape[0], _ptr(rho_coarse),
+                                            _ptr(rho_fine), _stream(stream)))
+
+    def deposit_codes(self, codes: Sequence[Codes], rho_coarse, rho_fine, stream=None):
+        arr = (pm_codes_t * 2)(codes[0].struct(), codes[1].struct())
+        self._err(self.lib.pm_deposit_codes(self.h, arr, _ptr(rho_coarse), _ptr(rho_fine), _stream(stream)))
+
+    def tile_density(self, rho_fine: torch.Tensor, tile: int, stream=None) -> torch.Tensor:
+        T = self.tile_edge
+        out = torch.empty((T, T, T), dtype=torch.float32, device="cuda")
+        self._err(self.lib.pm_tile_density(self.h, _ptr(rho_fine), tile, _ptr(out), _stream(stream)))
+        return out
+
+    def zeros_acc(self):
+        af = torch.zeros((3,) + (self.n_fine,) * 3, dtype=torch.float32, device="cuda")
+        ac = torch.zeros((3,) + (self.n_coarse,) * 3, dtype=torch.float32, device="cuda") if self.two_level else None
+        return ac, af
+
+    def solve(self, rho_coarse, rho_fine, acc_coarse, acc_fine, stream=None):
+        fn = self.lib.pm_solve_fixed if rho_fine.dtype == torch.int64 else self.lib.pm_solve
+        self._err(fn(self.h, _ptr(rho_coarse), _ptr(rho_fine), _ptr(acc_coarse), _ptr(acc_fine), _stream(stream)))
+
+    def interpolate(self, x: torch.Tensor, acc_coarse, acc_fine, stream=None) -> torch.Tensor:
+        a = torch.empty_like(x)
+        self._err(self.lib.pm_interpolate(self.h, _ptr(x), x.shape[0], _ptr(acc_coarse), _ptr(acc_fine), _ptr(a),
+                                          _stream(stream)))
+        return a
+
+    def kick_drift(self, x, v, acc_coarse, acc_fine, c_kick: float, c_drift: float, stream=None):
+        self._err(self.lib.pm_kick_drift(self.h, _ptr(x), _ptr(v), x.shape[0], _ptr(acc_coarse), _ptr(acc_fine),
+                                         c_kick, c_drift, _stream(stream)))
+
+    def step(self, codes_in: Sequence[Codes], codes_out: Sequence[Codes], c_kick: float, c_drift: float,
+             stream=None):
+        arr_in = (pm_codes_t * 2)(codes_in[0].struct(), codes_in[1].struct())
+        arr_out = (pm_codes_t * 2)(codes_out[0].struct(), codes_out[1].struct())
+        self._err(self.lib.pm_step(self.h, arr_in, arr_out, c_kick, c_drift, _stream(stream)))
+
+    def step_host(self, codes_in: Sequence[Codes], codes_out: Sequence[Codes], c_kick: float, c_drift: float,
+                  stream=None):
+        arr_in = (pm_codes_t * 2)(codes_in[0].struct(), codes_in[1].struct())
+        arr_out = (pm_codes_t * 2)(codes_out[0].struct(), codes_out[1].struct())
+        self._err(self.lib.pm_step_host(self.h, arr_in, arr_out, c_kick, c_drift, _stream(stream)))
+
+    def set_timing(self, on: bool):
+        self._err(self.lib.pm_set_timing(self.h, 1 if on else 0))
+
+    def stage_times(self) -> Dict[str, Tuple[float, int]]:
+        ms = (ctypes.c_float * 64)()
+        n = ctypes.c_int()
+        names = ctypes.create_string_buffer(4096)
+        self._err(self.lib.pm_stage_times(self.h, ms, 64, ctypes.byref(n), names, 4096))
+        out = {}
+        for i, item in enumerate(names.value.decode().split(";") if n.value else []):
+            name, cnt = item.split("#")
+            out[name] = (float(ms[i]), int(cnt))
+        return out
+
+
+def serialize(codes_host: Codes, n_cmp: int, vel_bits: int) -> bytes:
+    """Sec. 2.4 byte stream of host codes (pm_serialize)."""
+    lib = _lib.load()
+    cs = codes_host.struct()
+    ln = ctypes.c_size_t()
+    rc = lib.pm_serialize(ctypes.byref(cs), n_cmp, vel_bits, None, 0, ctypes.byref(ln))
+    if rc != _lib.PM_OK:
+        raise PMError(rc, "pm_serialize (size)")
+    buf = (ctypes.c_uint8 * ln.value)()
+    rc = lib.pm_serialize(ctypes.byref(cs), n_cmp, vel_bits, buf, ln.value, ctypes.byref(ln))
+    if rc != _lib.PM_OK:
+        raise PMError(rc, "pm_serialize")
+    return bytes(buf)
+
+
+def deserialize(data: bytes, n: int, n_cmp: int, vel_bits: int, esc_cap: int = 1024) -> Codes:
+    lib = _lib.load()
+    out = Codes.empty(n, n_cmp, vel_bits, esc_cap, device="cpu")
+    cs = out.struct()
+    buf = (ctypes.c_uint8 * len(data)).from_buffer_copy(data)
+    rc = lib.pm_deserialize(buf, len(data), n_cmp, vel_bits, ctypes.byref(cs))
+    if rc != _lib.PM_OK:
+        raise PMError(rc, "pm_deserialize")
+    return out
