@@ -195,7 +195,9 @@ Blk choose_blk(const Geom& g, bool fixed, bool deposit) {
   b.RY = b.RZ = 1;
   Geo geo{g.nf, g.rc, g.nc, g.rcmp, g.ncmp, g.ncell(), g.two};
   const size_t cap = 96 * 1024;
-  if (deposit) {
+  if (!deposit) {
+    while (b.RX > 1 && ikd_codes_smem(geo, b) > cap) b.RX /= 2;
+  } else {
     while (b.RX > 1 && deposit_codes_smem(geo, b, fixed) > cap) b.RX /= 2;
     Blk b2 = b;
     b2.RY = b2.RZ = 2;
@@ -426,7 +428,7 @@ int pm_geometry(const pm_handle_t* h, int64_t* n_cmp, int64_t* n_coarse, int64_t
 }
 
 int pm_decompress(pm_handle_t* h, int species, const pm_codes_t* in, float* x, float* v, void* stream) {
-  if (!h || !in || !x || !v) return fail(h, PM_ERR_ARG, "null argument");
+  if (!h || !in || (in->n > 0 && (!x || !v))) return fail(h, PM_ERR_ARG, "null argument");
   if (int r = check_species(h, species)) return r;
   cudaStream_t st = (cudaStream_t)stream;
   const bool vel16 = h->cfg.vel_bits == 16;
@@ -437,7 +439,8 @@ int pm_decompress(pm_handle_t* h, int species, const pm_codes_t* in, float* x, f
 
 int pm_compress(pm_handle_t* h, int species, const float* x, const float* v, const float* vmax_in, pm_codes_t* out,
                 void* stream) {
-  if (!h || !x || !v || !out || !out->cnt || !out->pos || !out->vel || !out->vmax || !out->n_esc || !out->esc)
+  if (!h || !out || !out->cnt || !out->pos || !out->vel || !out->vmax || !out->n_esc || !out->esc ||
+      (out->n > 0 && (!x || !v)))
     return fail(h, PM_ERR_ARG, "null argument");
   if (int r = check_species(h, species)) return r;
   cudaStream_t st = (cudaStream_t)stream;

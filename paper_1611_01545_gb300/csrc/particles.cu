@@ -395,6 +395,31 @@ __device__ __forceinline__ void accel_at(const Geo& g, const float* acc_c, const
   }
 }
 
+// The same CIC gather from a shared-memory copy S[3][fz][fy][fx] of the mesh
+// region whose cell (0,0,0) is the global cell (ox, oy, oz); identical
+// arithmetic and order to gather(), so both give the same bits.
+__device__ __forceinline__ void gather_local(const float* S, int fx, int fy, int fz, int ox, int oy, int oz, float px,
+                                             float py, float pz, float a[3]) {
+  float fl[3] = {floorf(px), floorf(py), floorf(pz)};
+  float w1[3] = {__fsub_rn(px, fl[0]), __fsub_rn(py, fl[1]), __fsub_rn(pz, fl[2])};
+  float w0[3] = {__fsub_rn(1.0f, w1[0]), __fsub_rn(1.0f, w1[1]), __fsub_rn(1.0f, w1[2])};
+  const int lx = (int)fl[0] - ox, ly = (int)fl[1] - oy, lz = (int)fl[2] - oz;
+  const int plane = fx * fy * fz;
+  float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    int dx = c & 1, dy = (c >> 1) & 1, dz = c >> 2;
+    float w = __fmul_rn(__fmul_rn(dx ? w1[0] : w0[0], dy ? w1[1] : w0[1]), dz ? w1[2] : w0[2]);
+    int idx = ((lz + dz) * fy + (ly + dy)) * fx + (lx + dx);
+    s0 = __fmaf_rn(w, S[idx], s0);
+    s1 = __fmaf_rn(w, S[plane + idx], s1);
+    s2 = __fmaf_rn(w, S[2 * plane + idx], s2);
+  }
+  a[0] = s0;
+  a[1] = s1;
+  a[2] = s2;
+}
+
 __device__ __forceinline__ float wrap_pos(float x, float nf) {
   if (x < 0.f) x = __fadd_rn(x, nf);
   if (x >= nf) x = __fsub_rn(x, nf);
@@ -582,6 +607,30 @@ template <> __device__ __forceinline__ void global_add<long long>(long long* a, 
   atomicAdd(reinterpret_cast<unsigned long long*>(a), (unsigned long long)v);
 }
 
+// Sums v[] over runs of consecutive lanes holding the same key (the particle
+// stream is cell ordered, so a warp's particles form few runs); returns true
+// on the last lane of each run, which then holds the run's totals.
+template <int K, typename T>
+__device__ __forceinline__ bool run_reduce(unsigned key, T (&v)[K]) {
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const unsigned prev = __shfl_up_sync(FULL, key, 1);
+  const unsigned next = __shfl_down_sync(FULL, key, 1);
+  const bool head = lane == 0 || prev != key;
+  const bool tail = lane == 31 || next != key;
+  const unsigned heads = __ballot_sync(FULL, head);
+  const int start = 31 - __clz(heads & (FULL >> (31 - lane)));
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      T u = __shfl_up_sync(FULL, v[k], o);
+      if (lane - start >= o) v[k] += u;
+    }
+  }
+  return tail;
+}
+
 // Decode + deposit of both species for one cell block, binned in shared memory.
 // smem: row offsets (2 species), fine region (RX r + 1)(RY r + 1)(RZ r + 1),
 // coarse region (RX + 1)(RY + 1)(RZ + 1) when two-level.
@@ -616,59 +665,79 @@ __global__ void k_deposit_codes(PCodes c0, PCodes c1, const int64_t* off0, const
       // exist; never read past the caller's n records.
       const int64_t p0 = ro[0] < cs.n ? ro[0] : cs.n;
       const int64_t p1 = ro[bk.RX] < cs.n ? ro[bk.RX] : cs.n;
-      for (int64_t p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
-        const int ixl = row_cell(ro, bk.RX, p);
-        const uint8_t* q = cs.pos + 3 * p;
-        float px = decode_pos(cb.ix0 + ixl, q[0], pscale);
-        float py = decode_pos(iy, q[1], pscale);
-        float pz = decode_pos(iz, q[2], pscale);
-        // fine CIC in local region coordinates (no wrap inside the block)
-        float flx = floorf(px), fly = floorf(py), flz = floorf(pz);
-        int lx = (int)flx - bxf, ly = (int)fly - byf, lz = (int)flz - bzf;
-        float w1[3] = {__fsub_rn(px, flx), __fsub_rn(py, fly), __fsub_rn(pz, flz)};
-        if constexpr (sizeof(Acc) == 4) {
-          float w0[3] = {__fsub_rn(1.f, w1[0]), __fsub_rn(1.f, w1[1]), __fsub_rn(1.f, w1[2])};
-#pragma unroll
-          for (int c = 0; c < 8; ++c) {
-            int dx = c & 1, dy = (c >> 1) & 1, dz = c >> 2;
-            float w = __fmul_rn(__fmul_rn(dx ? w1[0] : w0[0], dy ? w1[1] : w0[1]), dz ? w1[2] : w0[2]);
-            smem_add<Acc>(&sf[((lz + dz) * fy + (ly + dy)) * fx + (lx + dx)], (Acc)__fmul_rn(m, w));
-          }
-        } else {
-          long long a1[3] = {(long long)__fmul_rn(w1[0], 1048576.0f), (long long)__fmul_rn(w1[1], 1048576.0f),
-                             (long long)__fmul_rn(w1[2], 1048576.0f)};
-          long long terms[8];
-          fixed_corners(M, a1, terms);
-#pragma unroll
-          for (int c = 0; c < 8; ++c) {
-            int dx = c & 1, dy = (c >> 1) & 1, dz = c >> 2;
-            smem_add<Acc>(&sf[((lz + dz) * fy + (ly + dy)) * fx + (lx + dx)], (Acc)terms[c]);
-          }
-        }
-        if (g.two) {
-          // coarse cell == compression cell (coarse_ratio == cmp_ratio): stencil cells ix, ix+1
-          const float sc_inv = 1.0f / (float)g.rc;
-          float ux = __fmul_rn(px, sc_inv), uy = __fmul_rn(py, sc_inv), uz = __fmul_rn(pz, sc_inv);
-          float gx = floorf(ux), gy = floorf(uy), gz = floorf(uz);
-          int kx = (int)gx - cb.ix0, ky = (int)gy - cb.iy0, kz = (int)gz - cb.iz0;
-          float v1[3] = {__fsub_rn(ux, gx), __fsub_rn(uy, gy), __fsub_rn(uz, gz)};
+      const int64_t rounds = (p1 - p0 + blockDim.x - 1) / blockDim.x;
+      for (int64_t it = 0; it < rounds; ++it) {
+        const int64_t p = p0 + it * blockDim.x + threadIdx.x;
+        const bool live = p < p1;
+        int ixl = 0;
+        float px = 0.f, py = 0.f, pz = 0.f;
+        if (live) {
+          ixl = row_cell(ro, bk.RX, p);
+          const uint8_t* q = cs.pos + 3 * p;
+          px = decode_pos(cb.ix0 + ixl, q[0], pscale);
+          py = decode_pos(iy, q[1], pscale);
+          pz = decode_pos(iz, q[2], pscale);
+          // fine CIC in local region coordinates (no wrap inside the block)
+          float flx = floorf(px), fly = floorf(py), flz = floorf(pz);
+          int lx = (int)flx - bxf, ly = (int)fly - byf, lz = (int)flz - bzf;
+          float w1[3] = {__fsub_rn(px, flx), __fsub_rn(py, fly), __fsub_rn(pz, flz)};
           if constexpr (sizeof(Acc) == 4) {
-            float v0[3] = {__fsub_rn(1.f, v1[0]), __fsub_rn(1.f, v1[1]), __fsub_rn(1.f, v1[2])};
+            float w0[3] = {__fsub_rn(1.f, w1[0]), __fsub_rn(1.f, w1[1]), __fsub_rn(1.f, w1[2])};
 #pragma unroll
             for (int c = 0; c < 8; ++c) {
               int dx = c & 1, dy = (c >> 1) & 1, dz = c >> 2;
-              float w = __fmul_rn(__fmul_rn(dx ? v1[0] : v0[0], dy ? v1[1] : v0[1]), dz ? v1[2] : v0[2]);
-              smem_add<Acc>(&sc[((kz + dz) * cy + (ky + dy)) * cx + (kx + dx)], (Acc)__fmul_rn(m, w));
+              float w = __fmul_rn(__fmul_rn(dx ? w1[0] : w0[0], dy ? w1[1] : w0[1]), dz ? w1[2] : w0[2]);
+              smem_add<Acc>(&sf[((lz + dz) * fy + (ly + dy)) * fx + (lx + dx)], (Acc)__fmul_rn(m, w));
             }
           } else {
-            long long a1[3] = {(long long)__fmul_rn(v1[0], 1048576.0f), (long long)__fmul_rn(v1[1], 1048576.0f),
-                               (long long)__fmul_rn(v1[2], 1048576.0f)};
+            long long a1[3] = {(long long)__fmul_rn(w1[0], 1048576.0f), (long long)__fmul_rn(w1[1], 1048576.0f),
+                               (long long)__fmul_rn(w1[2], 1048576.0f)};
             long long terms[8];
             fixed_corners(M, a1, terms);
 #pragma unroll
             for (int c = 0; c < 8; ++c) {
               int dx = c & 1, dy = (c >> 1) & 1, dz = c >> 2;
-              smem_add<Acc>(&sc[((kz + dz) * cy + (ky + dy)) * cx + (kx + dx)], (Acc)terms[c]);
+              smem_add<Acc>(&sf[((lz + dz) * fy + (ly + dy)) * fx + (lx + dx)], (Acc)terms[c]);
+            }
+          }
+        }
+        if (g.two) {
+          // Coarse cell == compression cell (coarse_ratio == cmp_ratio), so every
+          // particle of a run shares its 8 coarse corners: sum the run in
+          // registers and let its last lane do 8 shared-memory adds.
+          Acc cv[8];
+          if (live) {
+            const float sc_inv = 1.0f / (float)g.rc;
+            float ux = __fmul_rn(px, sc_inv), uy = __fmul_rn(py, sc_inv), uz = __fmul_rn(pz, sc_inv);
+            float v1[3] = {__fsub_rn(ux, floorf(ux)), __fsub_rn(uy, floorf(uy)), __fsub_rn(uz, floorf(uz))};
+            if constexpr (sizeof(Acc) == 4) {
+              float v0[3] = {__fsub_rn(1.f, v1[0]), __fsub_rn(1.f, v1[1]), __fsub_rn(1.f, v1[2])};
+#pragma unroll
+              for (int c = 0; c < 8; ++c) {
+                int dx = c & 1, dy = (c >> 1) & 1, dz = c >> 2;
+                float w = __fmul_rn(__fmul_rn(dx ? v1[0] : v0[0], dy ? v1[1] : v0[1]), dz ? v1[2] : v0[2]);
+                cv[c] = (Acc)__fmul_rn(m, w);
+              }
+            } else {
+              long long a1[3] = {(long long)__fmul_rn(v1[0], 1048576.0f), (long long)__fmul_rn(v1[1], 1048576.0f),
+                                 (long long)__fmul_rn(v1[2], 1048576.0f)};
+              long long terms[8];
+              fixed_corners(M, a1, terms);
+#pragma unroll
+              for (int c = 0; c < 8; ++c) cv[c] = (Acc)terms[c];
+            }
+          } else {
+#pragma unroll
+            for (int c = 0; c < 8; ++c) cv[c] = (Acc)0;
+          }
+          const unsigned key = live ? (unsigned)ixl : 0xffffffffu;
+          if (run_reduce<8, Acc>(key, cv) && live) {
+            // coarse stencil cells: cell ixl and ixl + 1 along x, row and row + 1 along y, z
+            const int kx = ixl, ky = row % bk.RY, kz = row / bk.RY;
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+              int dx = c & 1, dy = (c >> 1) & 1, dz = c >> 2;
+              smem_add<Acc>(&sc[((kz + dz) * cy + (ky + dy)) * cx + (kx + dx)], cv[c]);
             }
           }
         }
@@ -701,16 +770,58 @@ __global__ void k_deposit_codes(PCodes c0, PCodes c1, const int64_t* off0, const
 }
 
 // Decode + interpolate + kick + drift of one species for one cell block.
+// The block's force region (fine: (RX r + 1)(RY r + 1)(RZ r + 1) cells, coarse:
+// (RX + 1)(RY + 1)(RZ + 1) cells, 3 components each) is first copied to
+// shared memory with coalesced row loads, then gathered per particle.
 // MODE 0: histogram of new cells + v_max; MODE 1: rank, encode, scatter.
 template <int MODE>
 __global__ void k_ikd_codes(PCodes in, const int64_t* off, Geo g, Blk bk, const float* acc_c, const float* acc_f,
                             float ck, float cd, uint32_t* counts, uint32_t* vmax_bits, const int64_t* newoff,
                             PCodesOut o, int* status) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  int64_t* roff = reinterpret_cast<int64_t*>(smraw);
+  const int r = g.rcmp;
   const int nrow = bk.RY * bk.RZ;
+  const int fx = bk.RX * r + 1, fy = bk.RY * r + 1, fz = bk.RZ * r + 1;
+  const int cx = bk.RX + 1, cy = bk.RY + 1, cz = bk.RZ + 1;
+  int64_t* roff = reinterpret_cast<int64_t*>(smraw);
+  float* sf = reinterpret_cast<float*>(roff + nrow * (bk.RX + 1));
+  float* sc = sf + 3 * fx * fy * fz;
   const CellBlock cb = block_of(bk, blockIdx.x);
   load_row_offsets(off, g, bk, cb, roff);
+  const int bxf = cb.ix0 * r, byf = cb.iy0 * r, bzf = cb.iz0 * r;
+  {
+    const int nf = g.nf;
+    const int64_t nf3 = (int64_t)nf * nf * nf;
+    const int lines = 3 * fz * fy;
+    for (int li = threadIdx.x >> 5; li < lines; li += blockDim.x >> 5) {
+      int comp = li / (fz * fy), rem = li - comp * fz * fy;
+      int lz = rem / fy, ly = rem - lz * fy;
+      int gz = bzf + lz, gy = byf + ly;
+      if (gz >= nf) gz -= nf;
+      if (gy >= nf) gy -= nf;
+      const float* src = acc_f + comp * nf3 + ((int64_t)gz * nf + gy) * nf;
+      float* dst = sf + (int64_t)li * fx;
+      for (int lx = threadIdx.x & 31; lx < fx; lx += 32) {
+        int gx = bxf + lx;
+        if (gx >= nf) gx -= nf;
+        dst[lx] = __ldg(src + gx);
+      }
+    }
+    if (g.two) {
+      const int nc = g.nc;
+      const int64_t nc3 = (int64_t)nc * nc * nc;
+      for (int i = threadIdx.x; i < 3 * cx * cy * cz; i += blockDim.x) {
+        int comp = i / (cx * cy * cz), rem = i - comp * cx * cy * cz;
+        int lz = rem / (cx * cy), rem2 = rem - lz * cx * cy;
+        int ly = rem2 / cx, lx = rem2 - ly * cx;
+        int gx = cb.ix0 + lx, gy = cb.iy0 + ly, gz = cb.iz0 + lz;
+        if (gx >= nc) gx -= nc;
+        if (gy >= nc) gy -= nc;
+        if (gz >= nc) gz -= nc;
+        sc[i] = __ldg(acc_c + comp * nc3 + ((int64_t)gz * nc + gy) * nc + gx);
+      }
+    }
+  }
   __syncthreads();
   const float pscale = (float)g.rcmp / 256.0f;
   const float inv_r = 1.0f / (float)g.rcmp;
@@ -718,6 +829,7 @@ __global__ void k_ikd_codes(PCodes in, const int64_t* off, Geo g, Blk bk, const 
   const int half = in.vel16 ? 32768 : 128;
   const float vm_in = *in.vmax;
   const float step = __fmul_rn(vm_in, 1.0f / (float)half);
+  const float cinv = g.two ? 1.0f / (float)g.rc : 1.0f;
   float s_out = 0.f;
   bool vzero = false;
   if (MODE == 1) {
@@ -750,7 +862,15 @@ __global__ void k_ikd_codes(PCodes in, const int64_t* off, Geo g, Blk bk, const 
           v[d] = decode_vel(qv, half, step);
         }
         float a[3];
-        accel_at(g, acc_c, acc_f, x[0], x[1], x[2], a);
+        gather_local(sf, fx, fy, fz, bxf, byf, bzf, x[0], x[1], x[2], a);
+        if (g.two) {
+          float b[3];
+          gather_local(sc, cx, cy, cz, cb.ix0, cb.iy0, cb.iz0, __fmul_rn(x[0], cinv), __fmul_rn(x[1], cinv),
+                       __fmul_rn(x[2], cinv), b);
+          a[0] = __fadd_rn(b[0], a[0]);
+          a[1] = __fadd_rn(b[1], a[1]);
+          a[2] = __fadd_rn(b[2], a[2]);
+        }
         kick_drift(x, v, a, ck, cd, nf);
         key = cell_key(x, inv_r, g.ncmp);
         local_max = fmaxf(local_max, fmaxf(fabsf(v[0]), fmaxf(fabsf(v[1]), fabsf(v[2]))));
@@ -831,6 +951,13 @@ cudaError_t launch_compress(const float* x, const float* v, int64_t n, const Geo
   return cudaGetLastError();
 }
 
+size_t ikd_codes_smem(const Geo& g, const Blk& bk) {
+  size_t nrow = (size_t)bk.RY * bk.RZ;
+  size_t fine = (size_t)(bk.RX * g.rcmp + 1) * (bk.RY * g.rcmp + 1) * (bk.RZ * g.rcmp + 1);
+  size_t coarse = g.two ? (size_t)(bk.RX + 1) * (bk.RY + 1) * (bk.RZ + 1) : 0;
+  return nrow * (bk.RX + 1) * sizeof(int64_t) + 3 * (fine + coarse) * sizeof(float);
+}
+
 size_t deposit_codes_smem(const Geo& g, const Blk& bk, bool fixed) {
   size_t acc = fixed ? 8 : 4;
   size_t nrow = (size_t)bk.RY * bk.RZ;
@@ -861,8 +988,13 @@ cudaError_t launch_ikd_codes(int mode, const PCodes& in, const int64_t* off, con
                              const float* acc_c, const float* acc_f, float ck, float cd, uint32_t* counts,
                              uint32_t* vmax_bits, const int64_t* newoff, const PCodesOut& o, int* status,
                              cudaStream_t st) {
-  size_t smem = (size_t)bk.RY * bk.RZ * (bk.RX + 1) * sizeof(int64_t);
+  size_t smem = ikd_codes_smem(g, bk);
   int nblk = bk.nbx * bk.nby * bk.nbz;
+  if (mode == 0) {
+    cudaFuncSetAttribute(k_ikd_codes<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  } else {
+    cudaFuncSetAttribute(k_ikd_codes<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  }
   if (mode == 0)
     k_ikd_codes<0><<<nblk, 256, smem, st>>>(in, off, g, bk, acc_c, acc_f, ck, cd, counts, vmax_bits, newoff, o,
                                             status);

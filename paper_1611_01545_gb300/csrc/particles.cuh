@@ -54,6 +54,7 @@ cudaError_t launch_compress(const float* x, const float* v, int64_t n, const Geo
                             uint32_t* vmax_bits, const float* vmax_in, int64_t* off, pm_codes_t& out, bool vel16,
                             void* partial, int* status, cudaStream_t st);
 size_t deposit_codes_smem(const Geo& g, const Blk& bk, bool fixed);
+size_t ikd_codes_smem(const Geo& g, const Blk& bk);
 cudaError_t launch_deposit_codes(const PCodes& c0, const PCodes& c1, const int64_t* off0, const int64_t* off1,
                                  const Geo& g, const Blk& bk, float m0, float m1, long long M0, long long M1,
                                  void* rho_c, void* rho_f, bool fixed, cudaStream_t st);
