@@ -205,9 +205,11 @@ int pm_kick_drift(pm_handle_t* h, float* x, float* v, int64_t n, const float* ac
 
 /* One fused PM step from compressed state to compressed state for both
  * species: decompress + deposit, solve, interpolate + kick + drift +
- * recompress, with the library's own meshes.  in[s] and out[s] must not
- * alias; out[s].n must equal in[s].n.  v_max of the output is the exact
- * per-species max |v'_d|. */
+ * recompress, with the library's own meshes and per-particle scratch (sized
+ * at pm_init for count[0] + count[1] particles; larger inputs return
+ * PM_ERR_ARG).  in[s] and out[s] must not alias; out[s].n must equal
+ * in[s].n.  v_max of the output is the exact per-species max |v'_d|.
+ * Within a cell the output order is unspecified. */
 int pm_step(pm_handle_t* h, const pm_codes_t in[2], pm_codes_t out[2], double c_kick, double c_drift,
             void* stream);
 

@@ -39,6 +39,11 @@ struct pm_handle {
   void* partial = nullptr;
   int* status = nullptr;
   Blk blk_dep{}, blk_ikd{};
+  // per-particle scratch of the fused step (stream order, both species)
+  int64_t scratch_n = 0;
+  uint32_t* tkey = nullptr;
+  uint32_t* tpos = nullptr;
+  float* tv = nullptr;
   std::vector<void*> allocs;
   Timer timer;
   // staging for pm_step_host
@@ -195,8 +200,9 @@ Blk choose_blk(const Geom& g, bool fixed, bool deposit) {
   b.RY = b.RZ = 1;
   Geo geo{g.nf, g.rc, g.nc, g.rcmp, g.ncmp, g.ncell(), g.two};
   const size_t cap = 96 * 1024;
+  b.D = 2;
   if (!deposit) {
-    while (b.RX > 1 && ikd_codes_smem(geo, b) > cap) b.RX /= 2;
+    while (b.RX > 1 && ikd_count_smem(geo, b) > cap) b.RX /= 2;
   } else {
     while (b.RX > 1 && deposit_codes_smem(geo, b, fixed) > cap) b.RX /= 2;
     Blk b2 = b;
@@ -361,6 +367,10 @@ int pm_init(const pm_config_t* cfg, pm_handle_t** out) {
     A(&h->counts[s], ncell * 4);
   }
   A(&h->vmax_bits, 2 * 4);
+  h->scratch_n = c.count[0] + c.count[1];
+  A(&h->tkey, (size_t)h->scratch_n * 4);
+  A(&h->tpos, (size_t)h->scratch_n * 4);
+  A(&h->tv, (size_t)h->scratch_n * 12);
   A(&h->partial, scan_partial_bytes((int64_t)ncell));
   A(&h->status, 4);
   // plans and tables
@@ -439,8 +449,8 @@ int pm_decompress(pm_handle_t* h, int species, const pm_codes_t* in, float* x, f
 
 int pm_compress(pm_handle_t* h, int species, const float* x, const float* v, const float* vmax_in, pm_codes_t* out,
                 void* stream) {
-  if (!h || !out || !out->cnt || !out->pos || !out->vel || !out->vmax || !out->n_esc || !out->esc ||
-      (out->n > 0 && (!x || !v)))
+  if (!h || !out || !out->cnt || !out->vmax || !out->n_esc || !out->esc ||
+      (out->n > 0 && (!x || !v || !out->pos || !out->vel)))
     return fail(h, PM_ERR_ARG, "null argument");
   if (int r = check_species(h, species)) return r;
   cudaStream_t st = (cudaStream_t)stream;
@@ -472,7 +482,7 @@ int pm_deposit_fixed(pm_handle_t* h, int species, const float* x, int64_t n, int
 int pm_deposit_codes(pm_handle_t* h, const pm_codes_t in[2], void* rho_coarse, void* rho_fine, void* stream) {
   if (!h || !in || !rho_fine || (h->gm.two && !rho_coarse)) return fail(h, PM_ERR_ARG, "null argument");
   for (int s = 0; s < 2; ++s)
-    if (!in[s].cnt || !in[s].pos || !in[s].vel || !in[s].vmax || !in[s].n_esc || !in[s].esc)
+    if (!in[s].cnt || !in[s].vmax || !in[s].n_esc || !in[s].esc || (in[s].n > 0 && (!in[s].pos || !in[s].vel)))
       return fail(h, PM_ERR_ARG, "null codes pointer");
   cudaStream_t st = (cudaStream_t)stream;
   const bool fixed = h->cfg.deposit_mode == 1;
@@ -539,11 +549,13 @@ int pm_step(pm_handle_t* h, const pm_codes_t in[2], pm_codes_t out[2], double c_
   if (!h || !in || !out) return fail(h, PM_ERR_ARG, "null argument");
   for (int s = 0; s < 2; ++s) {
     if (in[s].n != out[s].n) return fail(h, PM_ERR_ARG, "out[s].n must equal in[s].n");
-    if (!in[s].cnt || !in[s].pos || !in[s].vel || !in[s].vmax || !in[s].n_esc || !in[s].esc || !out[s].cnt ||
-        !out[s].pos || !out[s].vel || !out[s].vmax || !out[s].n_esc || !out[s].esc)
+    if (!in[s].cnt || !in[s].vmax || !in[s].n_esc || !in[s].esc || !out[s].cnt || !out[s].vmax || !out[s].n_esc ||
+        !out[s].esc || (in[s].n > 0 && (!in[s].pos || !in[s].vel || !out[s].pos || !out[s].vel)))
       return fail(h, PM_ERR_ARG, "null codes pointer");
-    if (in[s].pos == out[s].pos) return fail(h, PM_ERR_ARG, "in and out codes must not alias");
+    if (in[s].n > 0 && in[s].pos == out[s].pos) return fail(h, PM_ERR_ARG, "in and out codes must not alias");
   }
+  if (in[0].n + in[1].n > h->scratch_n)
+    return fail(h, PM_ERR_ARG, "particle counts exceed the pm_config_t counts the handle was sized for");
   cudaStream_t st = (cudaStream_t)stream;
   Timer* tm = h->timer.on ? &h->timer : nullptr;
   const Geom& g = h->gm;
@@ -570,12 +582,10 @@ int pm_step(pm_handle_t* h, const pm_codes_t in[2], pm_codes_t out[2], double c_
   {
     TimedScope ts(tm, "ikd_count", st);
     CK(h, cudaMemsetAsync(h->vmax_bits, 0, 8, st));
-    for (int s = 0; s < 2; ++s) {
-      CK(h, cudaMemsetAsync(h->counts[s], 0, (size_t)ncell * 4, st));
-      PCodesOut o{out[s].pos, out[s].vel, out[s].vmax, vel16};
-      CK(h, launch_ikd_codes(0, view(in[s], vel16), h->off[s], h->geo, h->blk_ikd, h->acc_c, h->acc_f, ck, cd,
-                             h->counts[s], h->vmax_bits + s, h->newoff[s], o, h->status, st));
-    }
+    for (int s = 0; s < 2; ++s) CK(h, cudaMemsetAsync(h->counts[s], 0, (size_t)ncell * 4, st));
+    CK(h, launch_ikd_count(view(in[0], vel16), view(in[1], vel16), h->off[0], h->off[1], h->geo, h->blk_ikd,
+                           h->acc_c, h->acc_f, ck, cd, h->counts[0], h->counts[1], h->vmax_bits, h->tkey, h->tpos,
+                           h->tv, st));
   }
   {
     TimedScope ts(tm, "scan_out", st);
@@ -586,11 +596,9 @@ int pm_step(pm_handle_t* h, const pm_codes_t in[2], pm_codes_t out[2], double c_
   }
   {
     TimedScope ts(tm, "ikd_scatter", st);
-    for (int s = 0; s < 2; ++s) {
-      PCodesOut o{out[s].pos, out[s].vel, out[s].vmax, vel16};
-      CK(h, launch_ikd_codes(1, view(in[s], vel16), h->off[s], h->geo, h->blk_ikd, h->acc_c, h->acc_f, ck, cd,
-                             h->counts[s], h->vmax_bits + s, h->newoff[s], o, h->status, st));
-    }
+    PCodesOut o0{out[0].pos, out[0].vel, out[0].vmax, vel16}, o1{out[1].pos, out[1].vel, out[1].vmax, vel16};
+    CK(h, launch_ikd_scatter(in[0].n, in[1].n, h->off[0], h->off[1], h->geo, h->blk_ikd, h->counts[0], h->counts[1],
+                             h->newoff[0], h->newoff[1], o0, o1, h->tkey, h->tpos, h->tv, h->status, st));
   }
   return PM_OK;
 }

@@ -128,76 +128,108 @@ template <int N> __host__ __device__ constexpr int k_of_slot(int s) {
 }
 
 // Batched transforms over S sequences held in shared memory: element e of
-// sequence q is data[q * ss + e * es].  tw[j] = exp(-2 pi i j / N) (smem).
-// When es == 1 items are enumerated element-fastest, otherwise
+// sequence q is data[q * SS + e * ES].  tw[j] = exp(-2 pi i j / N) (smem).
+// S, SS, ES are compile-time so the item decomposition costs no division.
+// When ES == 1 items are enumerated element-fastest, otherwise
 // sequence-fastest, so a warp touches consecutive addresses.
-template <int N>
-__device__ __forceinline__ void item_split(int w, int S, int inner, bool elem_fast, int& q, int& j) {
-  if (elem_fast) { q = w / inner; j = w - q * inner; }
+template <int S, int INNER, bool ELEM_FAST>
+__device__ __forceinline__ void item_split(int w, int& q, int& j) {
+  if (ELEM_FAST) { q = w / INNER; j = w - q * INNER; }
   else { j = w / S; q = w - j * S; }
 }
 
-template <int N>
-__device__ void fft_fwd(float2* data, int S, int ss, int es, const float2* tw) {
+template <int N, int S, int SS, int ES>
+__device__ __forceinline__ void fft_fwd(float2* data, const float2* tw) {
   constexpr int N1 = Factor<N>::N1, N2 = Factor<N>::N2;
-  const bool ef = (es == 1);
+  constexpr bool EF = (ES == 1);
   for (int w = threadIdx.x; w < S * N2; w += blockDim.x) {
     int q, j2;
-    item_split<N>(w, S, N2, ef, q, j2);
-    float2* base = data + q * ss;
+    item_split<S, N2, EF>(w, q, j2);
+    float2* base = data + q * SS;
     float2 a[N1];
 #pragma unroll
-    for (int j1 = 0; j1 < N1; ++j1) a[j1] = base[(N2 * j1 + j2) * es];
+    for (int j1 = 0; j1 < N1; ++j1) a[j1] = base[(N2 * j1 + j2) * ES];
     Dft<N1, -1>::run(a);
 #pragma unroll
     for (int k1 = 1; k1 < N1; ++k1) a[k1] = cmul(a[k1], tw[(j2 * k1) % N]);
 #pragma unroll
-    for (int k1 = 0; k1 < N1; ++k1) base[(N2 * k1 + j2) * es] = a[k1];
+    for (int k1 = 0; k1 < N1; ++k1) base[(N2 * k1 + j2) * ES] = a[k1];
   }
   __syncthreads();
   for (int w = threadIdx.x; w < S * N1; w += blockDim.x) {
     int q, k1;
-    item_split<N>(w, S, N1, ef, q, k1);
-    float2* base = data + q * ss;
+    item_split<S, N1, EF>(w, q, k1);
+    float2* base = data + q * SS;
     float2 b[N2];
 #pragma unroll
-    for (int j2 = 0; j2 < N2; ++j2) b[j2] = base[(N2 * k1 + j2) * es];
+    for (int j2 = 0; j2 < N2; ++j2) b[j2] = base[(N2 * k1 + j2) * ES];
     Dft<N2, -1>::run(b);
 #pragma unroll
-    for (int k2 = 0; k2 < N2; ++k2) base[(N2 * k1 + k2) * es] = b[k2];
+    for (int k2 = 0; k2 < N2; ++k2) base[(N2 * k1 + k2) * ES] = b[k2];
   }
   __syncthreads();
 }
 
-template <int N>
-__device__ void fft_inv(float2* data, int S, int ss, int es, const float2* tw) {
+template <int N, int S, int SS, int ES>
+__device__ __forceinline__ void fft_inv(float2* data, const float2* tw) {
   constexpr int N1 = Factor<N>::N1, N2 = Factor<N>::N2;
-  const bool ef = (es == 1);
+  constexpr bool EF = (ES == 1);
   for (int w = threadIdx.x; w < S * N1; w += blockDim.x) {
     int q, k1;
-    item_split<N>(w, S, N1, ef, q, k1);
-    float2* base = data + q * ss;
+    item_split<S, N1, EF>(w, q, k1);
+    float2* base = data + q * SS;
     float2 b[N2];
 #pragma unroll
-    for (int k2 = 0; k2 < N2; ++k2) b[k2] = base[(N2 * k1 + k2) * es];
+    for (int k2 = 0; k2 < N2; ++k2) b[k2] = base[(N2 * k1 + k2) * ES];
     Dft<N2, 1>::run(b);
     // b[j2] now holds sum_k2 X[k1 + N1 k2] W_N2^(-j2 k2); apply W_N^(-j2 k1).
 #pragma unroll
     for (int j2 = 1; j2 < N2; ++j2) b[j2] = cmul(b[j2], conjf2(tw[(j2 * k1) % N]));
 #pragma unroll
-    for (int j2 = 0; j2 < N2; ++j2) base[(N2 * k1 + j2) * es] = b[j2];
+    for (int j2 = 0; j2 < N2; ++j2) base[(N2 * k1 + j2) * ES] = b[j2];
   }
   __syncthreads();
   for (int w = threadIdx.x; w < S * N2; w += blockDim.x) {
     int q, j2;
-    item_split<N>(w, S, N2, ef, q, j2);
-    float2* base = data + q * ss;
+    item_split<S, N2, EF>(w, q, j2);
+    float2* base = data + q * SS;
     float2 a[N1];
 #pragma unroll
-    for (int k1 = 0; k1 < N1; ++k1) a[k1] = base[(N2 * k1 + j2) * es];
+    for (int k1 = 0; k1 < N1; ++k1) a[k1] = base[(N2 * k1 + j2) * ES];
     Dft<N1, 1>::run(a);
 #pragma unroll
-    for (int j1 = 0; j1 < N1; ++j1) base[(N2 * j1 + j2) * es] = a[j1];
+    for (int j1 = 0; j1 < N1; ++j1) base[(N2 * j1 + j2) * ES] = a[j1];
+  }
+  __syncthreads();
+}
+
+// Inverse transforms of S contiguous rows (ES == 1, row stride SS) with a
+// runtime row count: items are split by the compile-time factors only.
+template <int N, int SS>
+__device__ __forceinline__ void fft_inv_rows(float2* data, int S, const float2* tw) {
+  constexpr int N1 = Factor<N>::N1, N2 = Factor<N>::N2;
+  for (int w = threadIdx.x; w < S * N1; w += blockDim.x) {
+    const int q = w / N1, k1 = w - q * N1;
+    float2* base = data + q * SS;
+    float2 b[N2];
+#pragma unroll
+    for (int k2 = 0; k2 < N2; ++k2) b[k2] = base[N2 * k1 + k2];
+    Dft<N2, 1>::run(b);
+#pragma unroll
+    for (int j2 = 1; j2 < N2; ++j2) b[j2] = cmul(b[j2], conjf2(tw[(j2 * k1) % N]));
+#pragma unroll
+    for (int j2 = 0; j2 < N2; ++j2) base[N2 * k1 + j2] = b[j2];
+  }
+  __syncthreads();
+  for (int w = threadIdx.x; w < S * N2; w += blockDim.x) {
+    const int q = w / N2, j2 = w - q * N2;
+    float2* base = data + q * SS;
+    float2 a[N1];
+#pragma unroll
+    for (int k1 = 0; k1 < N1; ++k1) a[k1] = base[N2 * k1 + j2];
+    Dft<N1, 1>::run(a);
+#pragma unroll
+    for (int j1 = 0; j1 < N1; ++j1) base[N2 * j1 + j2] = a[j1];
   }
   __syncthreads();
 }

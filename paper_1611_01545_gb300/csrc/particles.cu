@@ -594,16 +594,13 @@ __device__ __forceinline__ int row_cell(const int64_t* ro, int RX, int64_t p) {
   return lo;
 }
 
-template <typename Acc>
-__device__ __forceinline__ void smem_add(Acc* a, Acc v);
-template <> __device__ __forceinline__ void smem_add<float>(float* a, float v) { atomicAdd(a, v); }
-template <> __device__ __forceinline__ void smem_add<long long>(long long* a, long long v) {
+__device__ __forceinline__ void smem_add64(long long* a, long long v) {
   atomicAdd(reinterpret_cast<unsigned long long*>(a), (unsigned long long)v);
 }
-template <typename Acc>
-__device__ __forceinline__ void global_add(Acc* a, Acc v);
-template <> __device__ __forceinline__ void global_add<float>(float* a, float v) { atomicAdd(a, v); }
-template <> __device__ __forceinline__ void global_add<long long>(long long* a, long long v) {
+__device__ __forceinline__ void global_add(float* a, long long v) {
+  atomicAdd(a, __fmul_rn(__ll2float_rn(v), 2.3283064365386963e-10f));  // 2^-32 mass units
+}
+__device__ __forceinline__ void global_add(long long* a, long long v) {
   atomicAdd(reinterpret_cast<unsigned long long*>(a), (unsigned long long)v);
 }
 
@@ -631,22 +628,44 @@ __device__ __forceinline__ bool run_reduce(unsigned key, T (&v)[K]) {
   return tail;
 }
 
+// Mass of one CIC corner in 2^-32 units.  Float mode: m w_x w_y w_z rounded
+// once in float32, then scaled exactly; fixed mode: the conservative integer
+// split of the fixed-point deposit.
+template <bool FIXED>
+__device__ __forceinline__ void corner_masses(float m, long long M, const float w1[3], long long out[8]) {
+  if (FIXED) {
+    long long a1[3] = {(long long)__fmul_rn(w1[0], 1048576.0f), (long long)__fmul_rn(w1[1], 1048576.0f),
+                       (long long)__fmul_rn(w1[2], 1048576.0f)};
+    fixed_corners(M, a1, out);
+  } else {
+    float w0[3] = {__fsub_rn(1.f, w1[0]), __fsub_rn(1.f, w1[1]), __fsub_rn(1.f, w1[2])};
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      int dx = c & 1, dy = (c >> 1) & 1, dz = c >> 2;
+      float w = __fmul_rn(__fmul_rn(dx ? w1[0] : w0[0], dy ? w1[1] : w0[1]), dz ? w1[2] : w0[2]);
+      out[c] = __float2ll_rn(__fmul_rn(__fmul_rn(m, w), 4294967296.0f));
+    }
+  }
+}
+
 // Decode + deposit of both species for one cell block, binned in shared memory.
-// smem: row offsets (2 species), fine region (RX r + 1)(RY r + 1)(RZ r + 1),
-// coarse region (RX + 1)(RY + 1)(RZ + 1) when two-level.
-template <typename Acc>
+// Shared-memory sums are int64 in units of 2^-32 mass (native integer atomics,
+// exact and order-independent within the block); the flush converts to the
+// destination type.  smem: row offsets (2 species), fine region
+// (RX r + 1)(RY r + 1)(RZ r + 1), coarse region (RX + 1)(RY + 1)(RZ + 1).
+template <typename Out, bool FIXED>
 __global__ void k_deposit_codes(PCodes c0, PCodes c1, const int64_t* off0, const int64_t* off1, Geo g, Blk bk,
-                                float m0, float m1, long long M0, long long M1, Acc* rho_c, Acc* rho_f) {
+                                float m0, float m1, long long M0, long long M1, Out* rho_c, Out* rho_f) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const int r = g.rcmp;
   const int fx = bk.RX * r + 1, fy = bk.RY * r + 1, fz = bk.RZ * r + 1;
   const int cx = bk.RX + 1, cy = bk.RY + 1, cz = bk.RZ + 1;
   const int nrow = bk.RY * bk.RZ;
   int64_t* roff = reinterpret_cast<int64_t*>(smraw);
-  Acc* sf = reinterpret_cast<Acc*>(roff + 2 * nrow * (bk.RX + 1));
-  Acc* sc = sf + fx * fy * fz;
+  long long* sf = reinterpret_cast<long long*>(roff + 2 * nrow * (bk.RX + 1));
+  long long* sc = sf + fx * fy * fz;
   const int nsf = fx * fy * fz, nsc = g.two ? cx * cy * cz : 0;
-  for (int i = threadIdx.x; i < nsf + nsc; i += blockDim.x) sf[i] = (Acc)0;
+  for (int i = threadIdx.x; i < nsf + nsc; i += blockDim.x) sf[i] = 0;
   const CellBlock cb = block_of(bk, blockIdx.x);
   load_row_offsets(off0, g, bk, cb, roff);
   load_row_offsets(off1, g, bk, cb, roff + nrow * (bk.RX + 1));
@@ -681,63 +700,35 @@ __global__ void k_deposit_codes(PCodes c0, PCodes c1, const int64_t* off0, const
           float flx = floorf(px), fly = floorf(py), flz = floorf(pz);
           int lx = (int)flx - bxf, ly = (int)fly - byf, lz = (int)flz - bzf;
           float w1[3] = {__fsub_rn(px, flx), __fsub_rn(py, fly), __fsub_rn(pz, flz)};
-          if constexpr (sizeof(Acc) == 4) {
-            float w0[3] = {__fsub_rn(1.f, w1[0]), __fsub_rn(1.f, w1[1]), __fsub_rn(1.f, w1[2])};
+          long long t8[8];
+          corner_masses<FIXED>(m, M, w1, t8);
 #pragma unroll
-            for (int c = 0; c < 8; ++c) {
-              int dx = c & 1, dy = (c >> 1) & 1, dz = c >> 2;
-              float w = __fmul_rn(__fmul_rn(dx ? w1[0] : w0[0], dy ? w1[1] : w0[1]), dz ? w1[2] : w0[2]);
-              smem_add<Acc>(&sf[((lz + dz) * fy + (ly + dy)) * fx + (lx + dx)], (Acc)__fmul_rn(m, w));
-            }
-          } else {
-            long long a1[3] = {(long long)__fmul_rn(w1[0], 1048576.0f), (long long)__fmul_rn(w1[1], 1048576.0f),
-                               (long long)__fmul_rn(w1[2], 1048576.0f)};
-            long long terms[8];
-            fixed_corners(M, a1, terms);
-#pragma unroll
-            for (int c = 0; c < 8; ++c) {
-              int dx = c & 1, dy = (c >> 1) & 1, dz = c >> 2;
-              smem_add<Acc>(&sf[((lz + dz) * fy + (ly + dy)) * fx + (lx + dx)], (Acc)terms[c]);
-            }
+          for (int c = 0; c < 8; ++c) {
+            int dx = c & 1, dy = (c >> 1) & 1, dz = c >> 2;
+            smem_add64(&sf[((lz + dz) * fy + (ly + dy)) * fx + (lx + dx)], t8[c]);
           }
         }
         if (g.two) {
           // Coarse cell == compression cell (coarse_ratio == cmp_ratio), so every
           // particle of a run shares its 8 coarse corners: sum the run in
           // registers and let its last lane do 8 shared-memory adds.
-          Acc cv[8];
+          long long cv[8];
           if (live) {
             const float sc_inv = 1.0f / (float)g.rc;
             float ux = __fmul_rn(px, sc_inv), uy = __fmul_rn(py, sc_inv), uz = __fmul_rn(pz, sc_inv);
             float v1[3] = {__fsub_rn(ux, floorf(ux)), __fsub_rn(uy, floorf(uy)), __fsub_rn(uz, floorf(uz))};
-            if constexpr (sizeof(Acc) == 4) {
-              float v0[3] = {__fsub_rn(1.f, v1[0]), __fsub_rn(1.f, v1[1]), __fsub_rn(1.f, v1[2])};
-#pragma unroll
-              for (int c = 0; c < 8; ++c) {
-                int dx = c & 1, dy = (c >> 1) & 1, dz = c >> 2;
-                float w = __fmul_rn(__fmul_rn(dx ? v1[0] : v0[0], dy ? v1[1] : v0[1]), dz ? v1[2] : v0[2]);
-                cv[c] = (Acc)__fmul_rn(m, w);
-              }
-            } else {
-              long long a1[3] = {(long long)__fmul_rn(v1[0], 1048576.0f), (long long)__fmul_rn(v1[1], 1048576.0f),
-                                 (long long)__fmul_rn(v1[2], 1048576.0f)};
-              long long terms[8];
-              fixed_corners(M, a1, terms);
-#pragma unroll
-              for (int c = 0; c < 8; ++c) cv[c] = (Acc)terms[c];
-            }
+            corner_masses<FIXED>(m, M, v1, cv);
           } else {
 #pragma unroll
-            for (int c = 0; c < 8; ++c) cv[c] = (Acc)0;
+            for (int c = 0; c < 8; ++c) cv[c] = 0;
           }
           const unsigned key = live ? (unsigned)ixl : 0xffffffffu;
-          if (run_reduce<8, Acc>(key, cv) && live) {
-            // coarse stencil cells: cell ixl and ixl + 1 along x, row and row + 1 along y, z
+          if (run_reduce<8, long long>(key, cv) && live) {
             const int kx = ixl, ky = row % bk.RY, kz = row / bk.RY;
 #pragma unroll
             for (int c = 0; c < 8; ++c) {
               int dx = c & 1, dy = (c >> 1) & 1, dz = c >> 2;
-              smem_add<Acc>(&sc[((kz + dz) * cy + (ky + dy)) * cx + (kx + dx)], cv[c]);
+              smem_add64(&sc[((kz + dz) * cy + (ky + dy)) * cx + (kx + dx)], cv[c]);
             }
           }
         }
@@ -747,47 +738,91 @@ __global__ void k_deposit_codes(PCodes c0, PCodes c1, const int64_t* off0, const
   __syncthreads();
   const int nf = g.nf;
   for (int i = threadIdx.x; i < nsf; i += blockDim.x) {
-    Acc val = sf[i];
-    if (val == (Acc)0) continue;
+    long long val = sf[i];
+    if (val == 0) continue;
     int lx = i % fx, ly = (i / fx) % fy, lz = i / (fx * fy);
     int gx = bxf + lx, gy = byf + ly, gz = bzf + lz;
     if (gx >= nf) gx -= nf;
     if (gy >= nf) gy -= nf;
     if (gz >= nf) gz -= nf;
-    global_add<Acc>(&rho_f[((int64_t)gz * nf + gy) * nf + gx], val);
+    global_add(&rho_f[((int64_t)gz * nf + gy) * nf + gx], val);
   }
   const int nc = g.nc;
   for (int i = threadIdx.x; i < nsc; i += blockDim.x) {
-    Acc val = sc[i];
-    if (val == (Acc)0) continue;
+    long long val = sc[i];
+    if (val == 0) continue;
     int lx = i % cx, ly = (i / cx) % cy, lz = i / (cx * cy);
     int gx = cb.ix0 + lx, gy = cb.iy0 + ly, gz = cb.iz0 + lz;
     if (gx >= nc) gx -= nc;
     if (gy >= nc) gy -= nc;
     if (gz >= nc) gz -= nc;
-    global_add<Acc>(&rho_c[((int64_t)gz * nc + gy) * nc + gx], val);
+    global_add(&rho_c[((int64_t)gz * nc + gy) * nc + gx], val);
   }
 }
 
-// Decode + interpolate + kick + drift of one species for one cell block.
-// The block's force region (fine: (RX r + 1)(RY r + 1)(RZ r + 1) cells, coarse:
-// (RX + 1)(RY + 1)(RZ + 1) cells, 3 components each) is first copied to
-// shared memory with coalesced row loads, then gathered per particle.
-// MODE 0: histogram of new cells + v_max; MODE 1: rank, encode, scatter.
-template <int MODE>
-__global__ void k_ikd_codes(PCodes in, const int64_t* off, Geo g, Blk bk, const float* acc_c, const float* acc_f,
-                            float ck, float cd, uint32_t* counts, uint32_t* vmax_bits, const int64_t* newoff,
-                            PCodesOut o, int* status) {
+// Window of destination compression cells owned by a cell block's histogram:
+// the block widened by D cells on each side (clamped to the mesh), periodic.
+struct Win {
+  int ox, oy, oz, wx, wy, wz;
+};
+__device__ __forceinline__ Win window_of(const Geo& g, const Blk& bk, CellBlock cb) {
+  Win w;
+  const int n = g.ncmp, D = bk.D;
+  w.wx = bk.RX + 2 * D < n ? bk.RX + 2 * D : n;
+  w.wy = bk.RY + 2 * D < n ? bk.RY + 2 * D : n;
+  w.wz = bk.RZ + 2 * D < n ? bk.RZ + 2 * D : n;
+  w.ox = w.wx == n ? 0 : cb.ix0 - D;
+  w.oy = w.wy == n ? 0 : cb.iy0 - D;
+  w.oz = w.wz == n ? 0 : cb.iz0 - D;
+  return w;
+}
+// Window slot of compression cell `key`, or -1 outside the window.
+__device__ __forceinline__ int window_slot(const Geo& g, const Win& w, uint32_t key) {
+  const int n = g.ncmp;
+  int cx = (int)(key % (uint32_t)n), cy = (int)((key / (uint32_t)n) % (uint32_t)n), cz = (int)(key / ((uint32_t)n * n));
+  int lx = cx - w.ox, ly = cy - w.oy, lz = cz - w.oz;
+  if (lx < 0) lx += n;
+  if (ly < 0) ly += n;
+  if (lz < 0) lz += n;
+  if (lx >= w.wx || ly >= w.wy || lz >= w.wz) return -1;
+  return (lz * w.wy + ly) * w.wx + lx;
+}
+__device__ __forceinline__ uint32_t window_cell(const Geo& g, const Win& w, int slot) {
+  const int n = g.ncmp;
+  int lx = slot % w.wx, ly = (slot / w.wx) % w.wy, lz = slot / (w.wx * w.wy);
+  int cx = w.ox + lx, cy = w.oy + ly, cz = w.oz + lz;
+  if (cx < 0) cx += n; else if (cx >= n) cx -= n;
+  if (cy < 0) cy += n; else if (cy >= n) cy -= n;
+  if (cz < 0) cz += n; else if (cz >= n) cz -= n;
+  return (uint32_t)(cx + n * (cy + n * cz));
+}
+
+// Pass 1 of interpolate + kick + drift + recompress, both species of one cell
+// block: the block's force region (fine: (RX r + 1)(RY r + 1)(RZ r + 1) cells,
+// coarse: (RX + 1)(RY + 1)(RZ + 1), 3 components) is copied to shared memory
+// with coalesced row loads; every particle is decoded, gathered, kicked and
+// drifted; its new cell, in-cell position bytes and new velocity go to the
+// step's scratch arrays in stream order; new-cell counts are histogrammed in
+// shared memory over the block's window (far movers: global atomics) and
+// flushed once per window cell; per-species max |v'_d| is reduced.
+__global__ void k_ikd_count(PCodes c0, PCodes c1, const int64_t* off0, const int64_t* off1, Geo g, Blk bk,
+                            const float* acc_c, const float* acc_f, float ck, float cd, uint32_t* counts0,
+                            uint32_t* counts1, uint32_t* vmax_bits, uint32_t* tkey, uint32_t* tpos, float* tv) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const int r = g.rcmp;
   const int nrow = bk.RY * bk.RZ;
   const int fx = bk.RX * r + 1, fy = bk.RY * r + 1, fz = bk.RZ * r + 1;
   const int cx = bk.RX + 1, cy = bk.RY + 1, cz = bk.RZ + 1;
-  int64_t* roff = reinterpret_cast<int64_t*>(smraw);
-  float* sf = reinterpret_cast<float*>(roff + nrow * (bk.RX + 1));
-  float* sc = sf + 3 * fx * fy * fz;
   const CellBlock cb = block_of(bk, blockIdx.x);
-  load_row_offsets(off, g, bk, cb, roff);
+  const Win win = window_of(g, bk, cb);
+  const int W = win.wx * win.wy * win.wz;
+  int64_t* roff = reinterpret_cast<int64_t*>(smraw);
+  uint32_t* hist = reinterpret_cast<uint32_t*>(roff + 2 * nrow * (bk.RX + 1));
+  float* sf = reinterpret_cast<float*>(hist + 2 * W);
+  float* sc = sf + 3 * fx * fy * fz;
+  load_row_offsets(off0, g, bk, cb, roff);
+  load_row_offsets(off1, g, bk, cb, roff + nrow * (bk.RX + 1));
+  for (int i = threadIdx.x; i < 2 * W; i += blockDim.x) hist[i] = 0;
   const int bxf = cb.ix0 * r, byf = cb.iy0 * r, bzf = cb.iz0 * r;
   {
     const int nf = g.nf;
@@ -823,35 +858,28 @@ __global__ void k_ikd_codes(PCodes in, const int64_t* off, Geo g, Blk bk, const 
     }
   }
   __syncthreads();
-  const float pscale = (float)g.rcmp / 256.0f;
-  const float inv_r = 1.0f / (float)g.rcmp;
+  const float pscale = (float)r / 256.0f;
+  const float inv_r = 1.0f / (float)r;
   const float nf = (float)g.nf;
-  const int half = in.vel16 ? 32768 : 128;
-  const float vm_in = *in.vmax;
-  const float step = __fmul_rn(vm_in, 1.0f / (float)half);
   const float cinv = g.two ? 1.0f / (float)g.rc : 1.0f;
-  float s_out = 0.f;
-  bool vzero = false;
-  if (MODE == 1) {
-    float vm = *o.vmax;
-    vzero = !(vm > 0.f);
-    s_out = vzero ? 0.f : __fdiv_rn(o.vel16 ? 32768.0f : 128.0f, vm);
-  }
-  float local_max = 0.f;
-  for (int row = 0; row < nrow; ++row) {
-    const int64_t* ro = roff + row * (bk.RX + 1);
-    const int iy = cb.iy0 + row % bk.RY, iz = cb.iz0 + row / bk.RY;
-    const int64_t p0 = ro[0] < in.n ? ro[0] : in.n;
-    const int64_t p1 = ro[bk.RX] < in.n ? ro[bk.RX] : in.n;
-    const int64_t span = p1 - p0;
-    const int64_t rounds = (span + blockDim.x - 1) / blockDim.x;
-    for (int64_t it = 0; it < rounds; ++it) {
-      const int64_t p = p0 + it * blockDim.x + threadIdx.x;
-      uint32_t key = 0xffffffffu;
-      float x[3], v[3];
-      if (p < p1) {
+  for (int s = 0; s < 2; ++s) {
+    const PCodes& in = s ? c1 : c0;
+    uint32_t* counts = s ? counts1 : counts0;
+    uint32_t* hs = hist + s * W;
+    const int64_t toff = s ? c0.n : 0;
+    const int half = in.vel16 ? 32768 : 128;
+    const float step = __fmul_rn(*in.vmax, 1.0f / (float)half);
+    float local_max = 0.f;
+    const int64_t* ro_s = roff + s * nrow * (bk.RX + 1);
+    for (int row = 0; row < nrow; ++row) {
+      const int64_t* ro = ro_s + row * (bk.RX + 1);
+      const int iy = cb.iy0 + row % bk.RY, iz = cb.iz0 + row / bk.RY;
+      const int64_t p0 = ro[0] < in.n ? ro[0] : in.n;
+      const int64_t p1 = ro[bk.RX] < in.n ? ro[bk.RX] : in.n;
+      for (int64_t p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
         const int ixl = row_cell(ro, bk.RX, p);
         const uint8_t* q = in.pos + 3 * p;
+        float x[3], v[3], a[3];
         x[0] = decode_pos(cb.ix0 + ixl, q[0], pscale);
         x[1] = decode_pos(iy, q[1], pscale);
         x[2] = decode_pos(iz, q[2], pscale);
@@ -861,7 +889,6 @@ __global__ void k_ikd_codes(PCodes in, const int64_t* off, Geo g, Blk bk, const 
                             : (int)reinterpret_cast<const uint8_t*>(in.vel)[3 * p + d];
           v[d] = decode_vel(qv, half, step);
         }
-        float a[3];
         gather_local(sf, fx, fy, fz, bxf, byf, bzf, x[0], x[1], x[2], a);
         if (g.two) {
           float b[3];
@@ -872,22 +899,118 @@ __global__ void k_ikd_codes(PCodes in, const int64_t* off, Geo g, Blk bk, const 
           a[2] = __fadd_rn(b[2], a[2]);
         }
         kick_drift(x, v, a, ck, cd, nf);
-        key = cell_key(x, inv_r, g.ncmp);
+        int cc[3], qq[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) encode_pos(x[d], inv_r, g.ncmp, cc[d], qq[d]);
+        const uint32_t key = (uint32_t)(cc[0] + g.ncmp * (cc[1] + g.ncmp * cc[2]));
+        const int64_t t = toff + p;
+        tkey[t] = key;
+        tpos[t] = (uint32_t)qq[0] | ((uint32_t)qq[1] << 8) | ((uint32_t)qq[2] << 16);
+        tv[3 * t] = v[0];
+        tv[3 * t + 1] = v[1];
+        tv[3 * t + 2] = v[2];
         local_max = fmaxf(local_max, fmaxf(fabsf(v[0]), fmaxf(fabsf(v[1]), fabsf(v[2]))));
+        const int slot = window_slot(g, win, key);
+        if (slot >= 0) atomicAdd(hs + slot, 1u);
+        else atomicAdd(counts + key, 1u);
       }
-      if (MODE == 0) {
-        count_cell(counts, key);
-      } else {
-        uint32_t rk = take_rank(counts, key);
-        if (key != 0xffffffffu) {
-          int64_t dst = newoff[key] + rk;
-          if (dst < in.n && rk < 0x80000000u) write_codes(o, dst, x, v, inv_r, g.ncmp, s_out, vzero);
-          else atomicOr(status, ST_CORRUPT);
+    }
+    block_vmax(local_max, vmax_bits + s);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < 2 * W; i += blockDim.x) {
+    uint32_t k = hist[i];
+    if (k) atomicAdd((i < W ? counts0 : counts1) + window_cell(g, win, i < W ? i : i - W), k);
+  }
+}
+
+// Pass 2: place every particle of a cell block in its new cell.  Phase 1
+// histograms the block's new cells over its window; phase 2 reserves one
+// contiguous range per window cell from the cell's global cursor (counts,
+// counted down to zero); phase 3 hands out slots from those ranges with
+// shared-memory atomics (far movers take single global slots), quantises the
+// velocity with the new v_max and writes the codes.
+__global__ void k_ikd_scatter(int64_t n0, int64_t n1, const int64_t* off0, const int64_t* off1, Geo g, Blk bk,
+                              uint32_t* counts0, uint32_t* counts1, const int64_t* newoff0, const int64_t* newoff1,
+                              PCodesOut o0, PCodesOut o1, const uint32_t* tkey, const uint32_t* tpos, const float* tv,
+                              int* status) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int nrow = bk.RY * bk.RZ;
+  const CellBlock cb = block_of(bk, blockIdx.x);
+  const Win win = window_of(g, bk, cb);
+  const int W = win.wx * win.wy * win.wz;
+  int64_t* roff = reinterpret_cast<int64_t*>(smraw);
+  unsigned long long* base = reinterpret_cast<unsigned long long*>(roff + 2 * nrow * (bk.RX + 1));
+  uint32_t* hist = reinterpret_cast<uint32_t*>(base + 2 * W);
+  load_row_offsets(off0, g, bk, cb, roff);
+  load_row_offsets(off1, g, bk, cb, roff + nrow * (bk.RX + 1));
+  for (int i = threadIdx.x; i < 2 * W; i += blockDim.x) hist[i] = 0;
+  __syncthreads();
+  for (int s = 0; s < 2; ++s) {
+    const int64_t n = s ? n1 : n0;
+    const int64_t toff = s ? n0 : 0;
+    for (int row = 0; row < nrow; ++row) {
+      const int64_t* ro = roff + (s * nrow + row) * (bk.RX + 1);
+      const int64_t p0 = ro[0] < n ? ro[0] : n, p1 = ro[bk.RX] < n ? ro[bk.RX] : n;
+      for (int64_t p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
+        const int slot = window_slot(g, win, tkey[toff + p]);
+        if (slot >= 0) atomicAdd(hist + s * W + slot, 1u);
+      }
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < 2 * W; i += blockDim.x) {
+    uint32_t k = hist[i];
+    if (!k) continue;
+    const int s = i < W ? 0 : 1;
+    const uint32_t cell = window_cell(g, win, i - s * W);
+    uint32_t* counts = s ? counts1 : counts0;
+    const int64_t* newoff = s ? newoff1 : newoff0;
+    uint32_t top = atomicSub(counts + cell, k);
+    base[i] = (unsigned long long)(newoff[cell] + (int64_t)top - (int64_t)k);
+  }
+  __syncthreads();
+  for (int s = 0; s < 2; ++s) {
+    const int64_t n = s ? n1 : n0;
+    const int64_t toff = s ? n0 : 0;
+    const PCodesOut& o = s ? o1 : o0;
+    uint32_t* counts = s ? counts1 : counts0;
+    const int64_t* newoff = s ? newoff1 : newoff0;
+    const int half = o.vel16 ? 32768 : 128;
+    const float vm = *o.vmax;
+    const bool vzero = !(vm > 0.f);
+    const float sv = vzero ? 0.f : __fdiv_rn(o.vel16 ? 32768.0f : 128.0f, vm);
+    for (int row = 0; row < nrow; ++row) {
+      const int64_t* ro = roff + (s * nrow + row) * (bk.RX + 1);
+      const int64_t p0 = ro[0] < n ? ro[0] : n, p1 = ro[bk.RX] < n ? ro[bk.RX] : n;
+      for (int64_t p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
+        const int64_t t = toff + p;
+        const uint32_t key = tkey[t];
+        const int slot = window_slot(g, win, key);
+        int64_t dst;
+        if (slot >= 0) {
+          dst = (int64_t)atomicAdd(base + s * W + slot, 1ull);
+        } else {
+          uint32_t top = atomicSub(counts + key, 1u);
+          dst = newoff[key] + (int64_t)top - 1;
+        }
+        if (dst < 0 || dst >= n) {
+          atomicOr(status, ST_CORRUPT);
+          continue;
+        }
+        const uint32_t pq = tpos[t];
+        o.pos[3 * dst] = (uint8_t)(pq & 0xff);
+        o.pos[3 * dst + 1] = (uint8_t)((pq >> 8) & 0xff);
+        o.pos[3 * dst + 2] = (uint8_t)((pq >> 16) & 0xff);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          int qv = encode_vel(tv[3 * t + d], sv, half, vzero);
+          if (o.vel16) reinterpret_cast<uint16_t*>(o.vel)[3 * dst + d] = (uint16_t)qv;
+          else reinterpret_cast<uint8_t*>(o.vel)[3 * dst + d] = (uint8_t)qv;
         }
       }
     }
   }
-  if (MODE == 0) block_vmax(local_max, vmax_bits);
 }
 
 // ------------------------------------------------------------ launchers --
@@ -951,19 +1074,32 @@ cudaError_t launch_compress(const float* x, const float* v, int64_t n, const Geo
   return cudaGetLastError();
 }
 
-size_t ikd_codes_smem(const Geo& g, const Blk& bk) {
+size_t ikd_count_smem(const Geo& g, const Blk& bk) {
   size_t nrow = (size_t)bk.RY * bk.RZ;
   size_t fine = (size_t)(bk.RX * g.rcmp + 1) * (bk.RY * g.rcmp + 1) * (bk.RZ * g.rcmp + 1);
   size_t coarse = g.two ? (size_t)(bk.RX + 1) * (bk.RY + 1) * (bk.RZ + 1) : 0;
-  return nrow * (bk.RX + 1) * sizeof(int64_t) + 3 * (fine + coarse) * sizeof(float);
+  return 2 * nrow * (bk.RX + 1) * sizeof(int64_t) + 2 * (size_t)window_cells(g, bk) * 4 +
+         3 * (fine + coarse) * sizeof(float);
 }
 
-size_t deposit_codes_smem(const Geo& g, const Blk& bk, bool fixed) {
-  size_t acc = fixed ? 8 : 4;
+size_t ikd_scatter_smem(const Geo& g, const Blk& bk) {
+  size_t nrow = (size_t)bk.RY * bk.RZ;
+  return 2 * nrow * (bk.RX + 1) * sizeof(int64_t) + 2 * (size_t)window_cells(g, bk) * (8 + 4);
+}
+
+int window_cells(const Geo& g, const Blk& bk) {
+  const int n = g.ncmp;
+  int wx = bk.RX + 2 * bk.D < n ? bk.RX + 2 * bk.D : n;
+  int wy = bk.RY + 2 * bk.D < n ? bk.RY + 2 * bk.D : n;
+  int wz = bk.RZ + 2 * bk.D < n ? bk.RZ + 2 * bk.D : n;
+  return wx * wy * wz;
+}
+
+size_t deposit_codes_smem(const Geo& g, const Blk& bk, bool) {
   size_t nrow = (size_t)bk.RY * bk.RZ;
   size_t fine = (size_t)(bk.RX * g.rcmp + 1) * (bk.RY * g.rcmp + 1) * (bk.RZ * g.rcmp + 1);
   size_t coarse = g.two ? (size_t)(bk.RX + 1) * (bk.RY + 1) * (bk.RZ + 1) : 0;
-  return 2 * nrow * (bk.RX + 1) * sizeof(int64_t) + (fine + coarse) * acc;
+  return 2 * nrow * (bk.RX + 1) * sizeof(int64_t) + (fine + coarse) * sizeof(long long);
 }
 
 cudaError_t launch_deposit_codes(const PCodes& c0, const PCodes& c1, const int64_t* off0, const int64_t* off1,
@@ -972,35 +1108,41 @@ cudaError_t launch_deposit_codes(const PCodes& c0, const PCodes& c1, const int64
   size_t smem = deposit_codes_smem(g, bk, fixed);
   int nblk = bk.nbx * bk.nby * bk.nbz;
   if (fixed) {
-    cudaFuncSetAttribute(k_deposit_codes<long long>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_deposit_codes<long long><<<nblk, 256, smem, st>>>(c0, c1, off0, off1, g, bk, m0, m1, M0, M1,
-                                                       static_cast<long long*>(rho_c), static_cast<long long*>(rho_f));
+    cudaFuncSetAttribute(k_deposit_codes<long long, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_deposit_codes<long long, true><<<nblk, 256, smem, st>>>(c0, c1, off0, off1, g, bk, m0, m1, M0, M1,
+                                                              static_cast<long long*>(rho_c),
+                                                              static_cast<long long*>(rho_f));
   } else {
-    cudaFuncSetAttribute(k_deposit_codes<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_deposit_codes<float><<<nblk, 256, smem, st>>>(c0, c1, off0, off1, g, bk, m0, m1, M0, M1,
-                                                   static_cast<float*>(rho_c), static_cast<float*>(rho_f));
+    cudaFuncSetAttribute(k_deposit_codes<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_deposit_codes<float, false><<<nblk, 256, smem, st>>>(c0, c1, off0, off1, g, bk, m0, m1, M0, M1,
+                                                           static_cast<float*>(rho_c), static_cast<float*>(rho_f));
   }
   note_launches(1);
   return cudaGetLastError();
 }
 
-cudaError_t launch_ikd_codes(int mode, const PCodes& in, const int64_t* off, const Geo& g, const Blk& bk,
-                             const float* acc_c, const float* acc_f, float ck, float cd, uint32_t* counts,
-                             uint32_t* vmax_bits, const int64_t* newoff, const PCodesOut& o, int* status,
-                             cudaStream_t st) {
-  size_t smem = ikd_codes_smem(g, bk);
+cudaError_t launch_ikd_count(const PCodes& c0, const PCodes& c1, const int64_t* off0, const int64_t* off1,
+                             const Geo& g, const Blk& bk, const float* acc_c, const float* acc_f, float ck, float cd,
+                             uint32_t* counts0, uint32_t* counts1, uint32_t* vmax_bits, uint32_t* tkey,
+                             uint32_t* tpos, float* tv, cudaStream_t st) {
+  size_t smem = ikd_count_smem(g, bk);
   int nblk = bk.nbx * bk.nby * bk.nbz;
-  if (mode == 0) {
-    cudaFuncSetAttribute(k_ikd_codes<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  } else {
-    cudaFuncSetAttribute(k_ikd_codes<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  }
-  if (mode == 0)
-    k_ikd_codes<0><<<nblk, 256, smem, st>>>(in, off, g, bk, acc_c, acc_f, ck, cd, counts, vmax_bits, newoff, o,
-                                            status);
-  else
-    k_ikd_codes<1><<<nblk, 256, smem, st>>>(in, off, g, bk, acc_c, acc_f, ck, cd, counts, vmax_bits, newoff, o,
-                                            status);
+  cudaFuncSetAttribute(k_ikd_count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_ikd_count<<<nblk, 256, smem, st>>>(c0, c1, off0, off1, g, bk, acc_c, acc_f, ck, cd, counts0, counts1, vmax_bits,
+                                       tkey, tpos, tv);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ikd_scatter(int64_t n0, int64_t n1, const int64_t* off0, const int64_t* off1, const Geo& g,
+                               const Blk& bk, uint32_t* counts0, uint32_t* counts1, const int64_t* newoff0,
+                               const int64_t* newoff1, const PCodesOut& o0, const PCodesOut& o1, const uint32_t* tkey,
+                               const uint32_t* tpos, const float* tv, int* status, cudaStream_t st) {
+  size_t smem = ikd_scatter_smem(g, bk);
+  int nblk = bk.nbx * bk.nby * bk.nbz;
+  cudaFuncSetAttribute(k_ikd_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_ikd_scatter<<<nblk, 256, smem, st>>>(n0, n1, off0, off1, g, bk, counts0, counts1, newoff0, newoff1, o0, o1, tkey,
+                                         tpos, tv, status);
   note_launches(1);
   return cudaGetLastError();
 }

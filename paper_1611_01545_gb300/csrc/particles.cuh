@@ -18,6 +18,7 @@ struct Geo {
 struct Blk {
   int RX, RY, RZ;     // cells per block along x, y, z
   int nbx, nby, nbz;  // blocks along x, y, z
+  int D;              // half-width (cells) of the new-cell histogram window
 };
 
 struct PCodes {
@@ -54,14 +55,20 @@ cudaError_t launch_compress(const float* x, const float* v, int64_t n, const Geo
                             uint32_t* vmax_bits, const float* vmax_in, int64_t* off, pm_codes_t& out, bool vel16,
                             void* partial, int* status, cudaStream_t st);
 size_t deposit_codes_smem(const Geo& g, const Blk& bk, bool fixed);
-size_t ikd_codes_smem(const Geo& g, const Blk& bk);
+size_t ikd_count_smem(const Geo& g, const Blk& bk);
+size_t ikd_scatter_smem(const Geo& g, const Blk& bk);
+int window_cells(const Geo& g, const Blk& bk);
 cudaError_t launch_deposit_codes(const PCodes& c0, const PCodes& c1, const int64_t* off0, const int64_t* off1,
                                  const Geo& g, const Blk& bk, float m0, float m1, long long M0, long long M1,
                                  void* rho_c, void* rho_f, bool fixed, cudaStream_t st);
-cudaError_t launch_ikd_codes(int mode, const PCodes& in, const int64_t* off, const Geo& g, const Blk& bk,
-                             const float* acc_c, const float* acc_f, float ck, float cd, uint32_t* counts,
-                             uint32_t* vmax_bits, const int64_t* newoff, const PCodesOut& o, int* status,
-                             cudaStream_t st);
+cudaError_t launch_ikd_count(const PCodes& c0, const PCodes& c1, const int64_t* off0, const int64_t* off1,
+                             const Geo& g, const Blk& bk, const float* acc_c, const float* acc_f, float ck, float cd,
+                             uint32_t* counts0, uint32_t* counts1, uint32_t* vmax_bits, uint32_t* tkey,
+                             uint32_t* tpos, float* tv, cudaStream_t st);
+cudaError_t launch_ikd_scatter(int64_t n0, int64_t n1, const int64_t* off0, const int64_t* off1, const Geo& g,
+                               const Blk& bk, uint32_t* counts0, uint32_t* counts1, const int64_t* newoff0,
+                               const int64_t* newoff1, const PCodesOut& o0, const PCodesOut& o1, const uint32_t* tkey,
+                               const uint32_t* tpos, const float* tv, int* status, cudaStream_t st);
 cudaError_t launch_set_vmax(const uint32_t* vmax_bits, float* out, cudaStream_t st);
 
 }  // namespace pm

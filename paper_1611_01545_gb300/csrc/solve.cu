@@ -84,7 +84,7 @@ __global__ void __launch_bounds__(SolveCfg<N>::threads) k_solve_a(SolveArgs a) {
     w[y & 1] = v;
   }
   __syncthreads();
-  fft_fwd<N>(W, N / 2, N, 1, tw);
+  fft_fwd<N, N / 2, N, 1>(W, tw);
   // Unpack the two real rows of each packed row: A = (Z_k + conj Z_-k)/2, B = (Z_k - conj Z_-k)/(2i).
   for (int i = threadIdx.x; i < (N / 2) * NH; i += blockDim.x) {
     int j = i / NH, k = i - j * NH;
@@ -94,7 +94,7 @@ __global__ void __launch_bounds__(SolveCfg<N>::threads) k_solve_a(SolveArgs a) {
     P[(2 * j + 1) * NH + k] = make_float2(0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));
   }
   __syncthreads();
-  fft_fwd<N>(P, NH, 1, NH, tw);
+  fft_fwd<N, NH, 1, NH>(P, tw);
   float2* out = a.spec + ((size_t)pb * N + z) * N * NH;
   for (int i = threadIdx.x; i < N * NH; i += blockDim.x) out[i] = P[i];
 }
@@ -115,7 +115,7 @@ __global__ void __launch_bounds__(SolveCfg<N>::threads) k_solve_b(SolveArgs a) {
     F[i] = in[((size_t)z * N + ys) * NH + kx];
   }
   __syncthreads();
-  fft_fwd<N>(F, NH, 1, NH, tw);
+  fft_fwd<N, NH, 1, NH>(F, tw);
   for (int d = 0; d < 3; ++d) {
     const float* K = a.kern + (size_t)d * N * N * NH;
     for (int i = threadIdx.x; i < N * NH; i += blockDim.x) {
@@ -125,7 +125,7 @@ __global__ void __launch_bounds__(SolveCfg<N>::threads) k_solve_b(SolveArgs a) {
       G[i] = make_float2(-f.y * k, f.x * k);   // i K f
     }
     __syncthreads();
-    fft_inv<N>(G, NH, 1, NH, tw);
+    fft_inv<N, NH, 1, NH>(G, tw);
     float2* out = a.spec3 + ((size_t)pb * 3 + d) * a.t * N * NH;
     for (int i = threadIdx.x; i < a.t * NH; i += blockDim.x) {
       int zo = i / NH, kx = i - zo * NH;
@@ -149,7 +149,7 @@ __global__ void __launch_bounds__(SolveCfg<N>::threads) k_solve_c(SolveArgs a) {
   const float2* in = a.spec3 + (((size_t)pb * 3 + d) * a.t + zo) * N * NH;
   for (int i = threadIdx.x; i < N * NH; i += blockDim.x) P[i] = in[i];
   __syncthreads();
-  fft_inv<N>(P, NH, 1, NH, tw);
+  fft_inv<N, NH, 1, NH>(P, tw);
   const int half_rows = a.t / 2;
   for (int i = threadIdx.x; i < half_rows * N; i += blockDim.x) {
     int j = i / N, k = i - j * N;
@@ -165,7 +165,7 @@ __global__ void __launch_bounds__(SolveCfg<N>::threads) k_solve_c(SolveArgs a) {
     W[j * N + slot_of<N>(k)] = make_float2(A.x - B.y, A.y + B.x);   // A + i B
   }
   __syncthreads();
-  fft_inv<N>(W, half_rows, N, 1, tw);
+  fft_inv_rows<N, N>(W, half_rows, tw);
   int ox, oy, oz;
   problem_origin(a, a.p0 + pb, ox, oy, oz);
   const int n = a.src_n;

@@ -76,7 +76,7 @@ def _gaussian_field(rng: np.random.Generator, n: int, slope: float, smooth: floa
     amp = np.zeros_like(k2)
     nz = k2 > 0
     amp[nz] = k2[nz] ** (slope / 4.0) * np.exp(-0.5 * k2[nz] * smooth * smooth)
-    return np.fft.irfftn(wk * amp, s=(n, n, n))
+    return np.fft.irfftn(wk * amp, s=(n, n, n), axes=(0, 1, 2))
 
 
 def zeldovich_lattice(rng: np.random.Generator, n_side: int, n_fine: int, rms_disp: float = 0.5,
@@ -91,7 +91,8 @@ def zeldovich_lattice(rng: np.random.Generator, n_side: int, n_fine: int, rms_di
     KZ, KY, KX = np.meshgrid(kz, kz, kx, indexing="ij")
     k2 = KX ** 2 + KY ** 2 + KZ ** 2
     k2[0, 0, 0] = 1.0
-    psi = np.stack([np.fft.irfftn(1j * kd * dk / k2, s=(n_side,) * 3) for kd in (KX, KY, KZ)], axis=-1)
+    psi = np.stack([np.fft.irfftn(1j * kd * dk / k2, s=(n_side,) * 3, axes=(0, 1, 2)) for kd in (KX, KY, KZ)],
+                    axis=-1)
     psi = psi.reshape(-1, 3)
     psi *= rms_disp / np.sqrt(np.mean(np.sum(psi * psi, axis=1)))
     sp = n_fine / n_side
