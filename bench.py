@@ -139,8 +139,9 @@ def build_state(pm, w, torch):
 
 
 def codes_bytes(c, vel_bits):
+    """Bytes of one species' in-memory codes (padded 4-byte position words)."""
     vb = 2 if vel_bits == 16 else 1
-    return c.cnt.numel() + c.esc.numel() * 4 + 4 + c.n * 3 * (1 + vb) + 4
+    return c.cnt.numel() + c.esc.numel() * 4 + 4 + c.n * 4 * (1 + vb) + 4
 
 
 def run_gb300(args):

@@ -100,9 +100,13 @@ typedef struct pm_config {
  *           particles, ascending by cell (the paper's 4-byte count).
  *  esc_cap  capacity of esc in pairs (written by compress, read by decompress).
  *  n_esc    device uint32: number of valid pairs in esc.
- *  pos      [n][3] uint8 in-cell offsets: floor(256 * offset / cell width).
- *  vel      [n][3] uint16 (vel_bits 16) or uint8 (vel_bits 8):
- *           floor(v 2^(b-1) / v_max + 2^(b-1)) clamped to [0, 2^b - 1].
+ *  pos      [n][4] uint8: in-cell offsets (px, py, pz) = floor(256 * offset /
+ *           cell width), then one zero pad byte (a 4-byte word per particle).
+ *  vel      [n][4] uint16 (vel_bits 16) or uint8 (vel_bits 8): (vx, vy, vz,
+ *           0) with v_d -> floor(v_d 2^(b-1) / v_max + 2^(b-1)) clamped to
+ *           [0, 2^b - 1].  The pad makes every particle's codes one aligned
+ *           word each (8 or 12 bytes in memory); the serialized stream of
+ *           pm_serialize carries no pads (9 or 6 bytes per particle).
  *  vmax     device float32: v_max of this species, max over particles and
  *           components of |v_d| (the paper's per-species header value).
  * Particles are stored cell by cell in cell order; within a cell the order

@@ -193,22 +193,20 @@ std::vector<float2> twiddles(int N) {
   return tw;
 }
 
-// Cell-block shapes for the fused passes: full x rows when they fit, 2x2 rows when there is room.
+// Cell-block shapes for the fused passes.  Deposit: full x rows, one row per
+// block unless the bins would not fit (small blocks keep many warps per SM).
+// Interpolate/recompress: the force region staged per block must stay under
+// about 100 KB so two 512-thread blocks share an SM.
 Blk choose_blk(const Geom& g, bool fixed, bool deposit) {
   Blk b{};
   b.RX = g.ncmp;
   b.RY = b.RZ = 1;
-  Geo geo{g.nf, g.rc, g.nc, g.rcmp, g.ncmp, g.ncell(), g.two};
-  const size_t cap = 96 * 1024;
   b.D = 2;
+  Geo geo{g.nf, g.rc, g.nc, g.rcmp, g.ncmp, g.ncell(), g.two};
   if (!deposit) {
-    while (b.RX > 1 && ikd_count_smem(geo, b) > cap) b.RX /= 2;
+    while (b.RX > 1 && b.RX % 2 == 0 && ikd_count_smem(geo, b) > 100 * 1024) b.RX /= 2;
   } else {
-    while (b.RX > 1 && deposit_codes_smem(geo, b, fixed) > cap) b.RX /= 2;
-    Blk b2 = b;
-    b2.RY = b2.RZ = 2;
-    int64_t nblk2 = (int64_t)(g.ncmp / b2.RX) * (g.ncmp / 2) * (g.ncmp / 2);
-    if (g.ncmp % 2 == 0 && deposit_codes_smem(geo, b2, fixed) <= cap && nblk2 >= 4 * 152) b = b2;
+    while (b.RX > 1 && b.RX % 2 == 0 && deposit_codes_smem(geo, b, fixed) > 64 * 1024) b.RX /= 2;
   }
   b.nbx = g.ncmp / b.RX;
   b.nby = g.ncmp / b.RY;
@@ -218,7 +216,12 @@ Blk choose_blk(const Geom& g, bool fixed, bool deposit) {
 
 Geo to_geo(const Geom& g) { return Geo{g.nf, g.rc, g.nc, g.rcmp, g.ncmp, g.ncell(), g.two}; }
 
-PCodes view(const pm_codes_t& c, bool vel16) { return PCodes{c.pos, c.vel, c.vmax, c.n, vel16}; }
+PCodes view(const pm_codes_t& c, bool vel16) {
+  return PCodes{reinterpret_cast<const uint32_t*>(c.pos), c.vel, c.vmax, c.n, vel16};
+}
+PCodesOut oview(const pm_codes_t& c, bool vel16) {
+  return PCodesOut{reinterpret_cast<uint32_t*>(c.pos), c.vel, c.vmax, vel16};
+}
 
 int check_species(pm_handle* h, int s) {
   if (s < 0 || s > 1) return fail(h, PM_ERR_ARG, "species must be 0 or 1");
@@ -596,7 +599,7 @@ int pm_step(pm_handle_t* h, const pm_codes_t in[2], pm_codes_t out[2], double c_
   }
   {
     TimedScope ts(tm, "ikd_scatter", st);
-    PCodesOut o0{out[0].pos, out[0].vel, out[0].vmax, vel16}, o1{out[1].pos, out[1].vel, out[1].vmax, vel16};
+    PCodesOut o0 = oview(out[0], vel16), o1 = oview(out[1], vel16);
     CK(h, launch_ikd_scatter(in[0].n, in[1].n, h->off[0], h->off[1], h->geo, h->blk_ikd, h->counts[0], h->counts[1],
                              h->newoff[0], h->newoff[1], o0, o1, h->tkey, h->tpos, h->tv, h->status, st));
   }
@@ -611,9 +614,9 @@ static int alloc_codes(pm_handle* h, pm_codes_t& c, int64_t n, int64_t esc_cap) 
   CK(h, dalloc(h, &c.cnt, ncell));
   CK(h, dalloc(h, &c.esc, (size_t)(esc_cap > 0 ? esc_cap : 1) * 8));
   CK(h, dalloc(h, &c.n_esc, 4));
-  CK(h, dalloc(h, &c.pos, (size_t)n * 3));
+  CK(h, dalloc(h, &c.pos, (size_t)n * 4));
   void* v = nullptr;
-  CK(h, dalloc(h, &v, (size_t)n * 3 * vb));
+  CK(h, dalloc(h, &v, (size_t)n * 4 * vb));
   c.vel = v;
   CK(h, dalloc(h, &c.vmax, 4));
   return PM_OK;
@@ -625,8 +628,8 @@ static int copy_codes(pm_handle* h, const pm_codes_t& dst, const pm_codes_t& src
   CK(h, cudaMemcpyAsync(dst.n_esc, src.n_esc, 4, kind, st));
   int64_t ecap = src.esc_cap < dst.esc_cap ? src.esc_cap : dst.esc_cap;
   if (include_esc_all && ecap > 0) CK(h, cudaMemcpyAsync(dst.esc, src.esc, (size_t)ecap * 8, kind, st));
-  CK(h, cudaMemcpyAsync(dst.pos, src.pos, (size_t)src.n * 3, kind, st));
-  CK(h, cudaMemcpyAsync(dst.vel, src.vel, (size_t)src.n * 3 * vb, kind, st));
+  CK(h, cudaMemcpyAsync(dst.pos, src.pos, (size_t)src.n * 4, kind, st));
+  CK(h, cudaMemcpyAsync(dst.vel, src.vel, (size_t)src.n * 4 * vb, kind, st));
   CK(h, cudaMemcpyAsync(dst.vmax, src.vmax, 4, kind, st));
   return PM_OK;
 }
@@ -749,16 +752,16 @@ int pm_serialize(const pm_host_codes_t* c, int32_t n_cmp, int32_t vel_bits, uint
       *o++ = (uint8_t)k;
     }
     for (int64_t j = 0; j < k; ++j, ++p) {
-      memcpy(o, c->pos + 3 * p, 3);
+      memcpy(o, c->pos + 4 * p, 3);
       o += 3;
       for (int d = 0; d < 3; ++d) {
         if (vb == 2) {
-          uint16_t q = static_cast<const uint16_t*>(c->vel)[3 * p + d];
+          uint16_t q = static_cast<const uint16_t*>(c->vel)[4 * p + d];
           o[0] = (uint8_t)(q & 0xff);
           o[1] = (uint8_t)(q >> 8);
           o += 2;
         } else {
-          *o++ = static_cast<const uint8_t*>(c->vel)[3 * p + d];
+          *o++ = static_cast<const uint8_t*>(c->vel)[4 * p + d];
         }
       }
     }
@@ -804,16 +807,19 @@ int pm_deserialize(const uint8_t* buf, size_t len, int32_t n_cmp, int32_t vel_bi
     size_t rec = (size_t)(3 + 3 * vb);
     if (off + (size_t)k * rec > len) return PM_ERR_CORRUPT;
     for (int64_t j = 0; j < k; ++j, ++p) {
-      memcpy(c->pos + 3 * p, buf + off, 3);
+      memcpy(c->pos + 4 * p, buf + off, 3);
+      c->pos[4 * p + 3] = 0;
       off += 3;
       for (int d = 0; d < 3; ++d) {
         if (vb == 2) {
-          static_cast<uint16_t*>(c->vel)[3 * p + d] = (uint16_t)(buf[off] | (buf[off + 1] << 8));
+          static_cast<uint16_t*>(c->vel)[4 * p + d] = (uint16_t)(buf[off] | (buf[off + 1] << 8));
           off += 2;
         } else {
-          static_cast<uint8_t*>(c->vel)[3 * p + d] = buf[off++];
+          static_cast<uint8_t*>(c->vel)[4 * p + d] = buf[off++];
         }
       }
+      if (vb == 2) static_cast<uint16_t*>(c->vel)[4 * p + 3] = 0;
+      else static_cast<uint8_t*>(c->vel)[4 * p + 3] = 0;
     }
   }
   if (off != len || p != c->n) return PM_ERR_CORRUPT;

@@ -128,7 +128,8 @@ template <int N> __host__ __device__ constexpr int k_of_slot(int s) {
 }
 
 // Batched transforms over S sequences held in shared memory: element e of
-// sequence q is data[q * SS + e * ES].  tw[j] = exp(-2 pi i j / N) (smem).
+// sequence q is data[q * SS + e * ES].  tw[j] = exp(-2 pi i j / N) (smem);
+// twiddle indices j2 k1 stay below N1 N2 = N, so no reduction is needed.
 // S, SS, ES are compile-time so the item decomposition costs no division.
 // When ES == 1 items are enumerated element-fastest, otherwise
 // sequence-fastest, so a warp touches consecutive addresses.
@@ -151,7 +152,7 @@ __device__ __forceinline__ void fft_fwd(float2* data, const float2* tw) {
     for (int j1 = 0; j1 < N1; ++j1) a[j1] = base[(N2 * j1 + j2) * ES];
     Dft<N1, -1>::run(a);
 #pragma unroll
-    for (int k1 = 1; k1 < N1; ++k1) a[k1] = cmul(a[k1], tw[(j2 * k1) % N]);
+    for (int k1 = 1; k1 < N1; ++k1) a[k1] = cmul(a[k1], tw[j2 * k1]);
 #pragma unroll
     for (int k1 = 0; k1 < N1; ++k1) base[(N2 * k1 + j2) * ES] = a[k1];
   }
@@ -184,7 +185,7 @@ __device__ __forceinline__ void fft_inv(float2* data, const float2* tw) {
     Dft<N2, 1>::run(b);
     // b[j2] now holds sum_k2 X[k1 + N1 k2] W_N2^(-j2 k2); apply W_N^(-j2 k1).
 #pragma unroll
-    for (int j2 = 1; j2 < N2; ++j2) b[j2] = cmul(b[j2], conjf2(tw[(j2 * k1) % N]));
+    for (int j2 = 1; j2 < N2; ++j2) b[j2] = cmul(b[j2], conjf2(tw[j2 * k1]));
 #pragma unroll
     for (int j2 = 0; j2 < N2; ++j2) base[(N2 * k1 + j2) * ES] = b[j2];
   }
@@ -216,7 +217,7 @@ __device__ __forceinline__ void fft_inv_rows(float2* data, int S, const float2* 
     for (int k2 = 0; k2 < N2; ++k2) b[k2] = base[N2 * k1 + k2];
     Dft<N2, 1>::run(b);
 #pragma unroll
-    for (int j2 = 1; j2 < N2; ++j2) b[j2] = cmul(b[j2], conjf2(tw[(j2 * k1) % N]));
+    for (int j2 = 1; j2 < N2; ++j2) b[j2] = cmul(b[j2], conjf2(tw[j2 * k1]));
 #pragma unroll
     for (int j2 = 0; j2 < N2; ++j2) base[N2 * k1 + j2] = b[j2];
   }

@@ -251,16 +251,14 @@ __global__ void k_decompress(PCodes in, const int64_t* off, Geo g, float* x, flo
   for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < in.n; p += (int64_t)gridDim.x * blockDim.x) {
     int64_t c = find_cell(off, g.ncell, p);
     int cx = (int)(c % g.ncmp), cy = (int)((c / g.ncmp) % g.ncmp), cz = (int)(c / ((int64_t)g.ncmp * g.ncmp));
-    const uint8_t* q = in.pos + 3 * p;
+    int q[3], qv[3];
+    unpack_pos(in.pos[p], q);
+    load_vel(in.vel, in.vel16, p, qv);
     x[3 * p + 0] = decode_pos(cx, q[0], pscale);
     x[3 * p + 1] = decode_pos(cy, q[1], pscale);
     x[3 * p + 2] = decode_pos(cz, q[2], pscale);
 #pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      int qv = in.vel16 ? (int)reinterpret_cast<const uint16_t*>(in.vel)[3 * p + d]
-                        : (int)reinterpret_cast<const uint8_t*>(in.vel)[3 * p + d];
-      v[3 * p + d] = decode_vel(qv, half, step);
-    }
+    for (int d = 0; d < 3; ++d) v[3 * p + d] = decode_vel(qv[d], half, step);
   }
 }
 
@@ -493,15 +491,15 @@ __device__ __forceinline__ void block_vmax(float m, uint32_t* vmax_bits) {
 __device__ __forceinline__ void write_codes(PCodesOut o, int64_t dst, const float x[3], const float v[3], float inv_r,
                                             int ncmp, float s, bool vzero) {
   const int half = o.vel16 ? 32768 : 128;
+  int q[3], qv[3];
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
-    int c, q;
-    encode_pos(x[d], inv_r, ncmp, c, q);
-    o.pos[3 * dst + d] = (uint8_t)q;
-    int qv = encode_vel(v[d], s, half, vzero);
-    if (o.vel16) reinterpret_cast<uint16_t*>(o.vel)[3 * dst + d] = (uint16_t)qv;
-    else reinterpret_cast<uint8_t*>(o.vel)[3 * dst + d] = (uint8_t)qv;
+    int c;
+    encode_pos(x[d], inv_r, ncmp, c, q[d]);
+    qv[d] = encode_vel(v[d], s, half, vzero);
   }
+  o.pos[dst] = (uint32_t)q[0] | ((uint32_t)q[1] << 8) | ((uint32_t)q[2] << 16);
+  store_vel(o.vel, o.vel16, dst, qv);
 }
 
 __device__ __forceinline__ uint32_t cell_key(const float x[3], float inv_r, int ncmp) {
@@ -594,12 +592,11 @@ __device__ __forceinline__ int row_cell(const int64_t* ro, int RX, int64_t p) {
   return lo;
 }
 
-__device__ __forceinline__ void smem_add64(long long* a, long long v) {
+__device__ __forceinline__ void smem_acc(long long* a, long long v) {
   atomicAdd(reinterpret_cast<unsigned long long*>(a), (unsigned long long)v);
 }
-__device__ __forceinline__ void global_add(float* a, long long v) {
-  atomicAdd(a, __fmul_rn(__ll2float_rn(v), 2.3283064365386963e-10f));  // 2^-32 mass units
-}
+__device__ __forceinline__ void smem_acc(float* a, float v) { atomicAdd(a, v); }
+__device__ __forceinline__ void global_add(float* a, float v) { atomicAdd(a, v); }
 __device__ __forceinline__ void global_add(long long* a, long long v) {
   atomicAdd(reinterpret_cast<unsigned long long*>(a), (unsigned long long)v);
 }
@@ -628,44 +625,40 @@ __device__ __forceinline__ bool run_reduce(unsigned key, T (&v)[K]) {
   return tail;
 }
 
-// Mass of one CIC corner in 2^-32 units.  Float mode: m w_x w_y w_z rounded
-// once in float32, then scaled exactly; fixed mode: the conservative integer
-// split of the fixed-point deposit.
-template <bool FIXED>
-__device__ __forceinline__ void corner_masses(float m, long long M, const float w1[3], long long out[8]) {
-  if (FIXED) {
-    long long a1[3] = {(long long)__fmul_rn(w1[0], 1048576.0f), (long long)__fmul_rn(w1[1], 1048576.0f),
-                       (long long)__fmul_rn(w1[2], 1048576.0f)};
-    fixed_corners(M, a1, out);
-  } else {
-    float w0[3] = {__fsub_rn(1.f, w1[0]), __fsub_rn(1.f, w1[1]), __fsub_rn(1.f, w1[2])};
+// Mass of each CIC corner: float mode m w_x w_y w_z in float32; fixed mode
+// the conservative integer split of the fixed-point deposit (2^-32 units).
+__device__ __forceinline__ void corner_masses(float m, long long, const float w1[3], float out[8]) {
+  float w0[3] = {__fsub_rn(1.f, w1[0]), __fsub_rn(1.f, w1[1]), __fsub_rn(1.f, w1[2])};
 #pragma unroll
-    for (int c = 0; c < 8; ++c) {
-      int dx = c & 1, dy = (c >> 1) & 1, dz = c >> 2;
-      float w = __fmul_rn(__fmul_rn(dx ? w1[0] : w0[0], dy ? w1[1] : w0[1]), dz ? w1[2] : w0[2]);
-      out[c] = __float2ll_rn(__fmul_rn(__fmul_rn(m, w), 4294967296.0f));
-    }
+  for (int c = 0; c < 8; ++c) {
+    int dx = c & 1, dy = (c >> 1) & 1, dz = c >> 2;
+    float w = __fmul_rn(__fmul_rn(dx ? w1[0] : w0[0], dy ? w1[1] : w0[1]), dz ? w1[2] : w0[2]);
+    out[c] = __fmul_rn(m, w);
   }
 }
+__device__ __forceinline__ void corner_masses(float, long long M, const float w1[3], long long out[8]) {
+  long long a1[3] = {(long long)__fmul_rn(w1[0], 1048576.0f), (long long)__fmul_rn(w1[1], 1048576.0f),
+                     (long long)__fmul_rn(w1[2], 1048576.0f)};
+  fixed_corners(M, a1, out);
+}
 
-// Decode + deposit of both species for one cell block, binned in shared memory.
-// Shared-memory sums are int64 in units of 2^-32 mass (native integer atomics,
-// exact and order-independent within the block); the flush converts to the
-// destination type.  smem: row offsets (2 species), fine region
+// Decode + deposit of both species for one cell block, binned in shared memory
+// (float32, or int64 in units of 2^-32 mass for the fixed-point mode) and
+// flushed once per cell.  smem: row offsets (2 species), fine region
 // (RX r + 1)(RY r + 1)(RZ r + 1), coarse region (RX + 1)(RY + 1)(RZ + 1).
-template <typename Out, bool FIXED>
+template <typename Acc>
 __global__ void k_deposit_codes(PCodes c0, PCodes c1, const int64_t* off0, const int64_t* off1, Geo g, Blk bk,
-                                float m0, float m1, long long M0, long long M1, Out* rho_c, Out* rho_f) {
+                                float m0, float m1, long long M0, long long M1, Acc* rho_c, Acc* rho_f) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const int r = g.rcmp;
   const int fx = bk.RX * r + 1, fy = bk.RY * r + 1, fz = bk.RZ * r + 1;
   const int cx = bk.RX + 1, cy = bk.RY + 1, cz = bk.RZ + 1;
   const int nrow = bk.RY * bk.RZ;
   int64_t* roff = reinterpret_cast<int64_t*>(smraw);
-  long long* sf = reinterpret_cast<long long*>(roff + 2 * nrow * (bk.RX + 1));
-  long long* sc = sf + fx * fy * fz;
+  Acc* sf = reinterpret_cast<Acc*>(roff + 2 * nrow * (bk.RX + 1));
+  Acc* sc = sf + fx * fy * fz;
   const int nsf = fx * fy * fz, nsc = g.two ? cx * cy * cz : 0;
-  for (int i = threadIdx.x; i < nsf + nsc; i += blockDim.x) sf[i] = 0;
+  for (int i = threadIdx.x; i < nsf + nsc; i += blockDim.x) sf[i] = (Acc)0;
   const CellBlock cb = block_of(bk, blockIdx.x);
   load_row_offsets(off0, g, bk, cb, roff);
   load_row_offsets(off1, g, bk, cb, roff + nrow * (bk.RX + 1));
@@ -692,7 +685,8 @@ __global__ void k_deposit_codes(PCodes c0, PCodes c1, const int64_t* off0, const
         float px = 0.f, py = 0.f, pz = 0.f;
         if (live) {
           ixl = row_cell(ro, bk.RX, p);
-          const uint8_t* q = cs.pos + 3 * p;
+          int q[3];
+          unpack_pos(cs.pos[p], q);
           px = decode_pos(cb.ix0 + ixl, q[0], pscale);
           py = decode_pos(iy, q[1], pscale);
           pz = decode_pos(iz, q[2], pscale);
@@ -700,35 +694,35 @@ __global__ void k_deposit_codes(PCodes c0, PCodes c1, const int64_t* off0, const
           float flx = floorf(px), fly = floorf(py), flz = floorf(pz);
           int lx = (int)flx - bxf, ly = (int)fly - byf, lz = (int)flz - bzf;
           float w1[3] = {__fsub_rn(px, flx), __fsub_rn(py, fly), __fsub_rn(pz, flz)};
-          long long t8[8];
-          corner_masses<FIXED>(m, M, w1, t8);
+          Acc t8[8];
+          corner_masses(m, M, w1, t8);
 #pragma unroll
           for (int c = 0; c < 8; ++c) {
             int dx = c & 1, dy = (c >> 1) & 1, dz = c >> 2;
-            smem_add64(&sf[((lz + dz) * fy + (ly + dy)) * fx + (lx + dx)], t8[c]);
+            smem_acc(&sf[((lz + dz) * fy + (ly + dy)) * fx + (lx + dx)], t8[c]);
           }
         }
         if (g.two) {
           // Coarse cell == compression cell (coarse_ratio == cmp_ratio), so every
           // particle of a run shares its 8 coarse corners: sum the run in
           // registers and let its last lane do 8 shared-memory adds.
-          long long cv[8];
+          Acc cv[8];
           if (live) {
             const float sc_inv = 1.0f / (float)g.rc;
             float ux = __fmul_rn(px, sc_inv), uy = __fmul_rn(py, sc_inv), uz = __fmul_rn(pz, sc_inv);
             float v1[3] = {__fsub_rn(ux, floorf(ux)), __fsub_rn(uy, floorf(uy)), __fsub_rn(uz, floorf(uz))};
-            corner_masses<FIXED>(m, M, v1, cv);
+            corner_masses(m, M, v1, cv);
           } else {
 #pragma unroll
-            for (int c = 0; c < 8; ++c) cv[c] = 0;
+            for (int c = 0; c < 8; ++c) cv[c] = (Acc)0;
           }
           const unsigned key = live ? (unsigned)ixl : 0xffffffffu;
-          if (run_reduce<8, long long>(key, cv) && live) {
+          if (run_reduce<8, Acc>(key, cv) && live) {
             const int kx = ixl, ky = row % bk.RY, kz = row / bk.RY;
 #pragma unroll
             for (int c = 0; c < 8; ++c) {
               int dx = c & 1, dy = (c >> 1) & 1, dz = c >> 2;
-              smem_add64(&sc[((kz + dz) * cy + (ky + dy)) * cx + (kx + dx)], cv[c]);
+              smem_acc(&sc[((kz + dz) * cy + (ky + dy)) * cx + (kx + dx)], cv[c]);
             }
           }
         }
@@ -738,8 +732,8 @@ __global__ void k_deposit_codes(PCodes c0, PCodes c1, const int64_t* off0, const
   __syncthreads();
   const int nf = g.nf;
   for (int i = threadIdx.x; i < nsf; i += blockDim.x) {
-    long long val = sf[i];
-    if (val == 0) continue;
+    Acc val = sf[i];
+    if (val == (Acc)0) continue;
     int lx = i % fx, ly = (i / fx) % fy, lz = i / (fx * fy);
     int gx = bxf + lx, gy = byf + ly, gz = bzf + lz;
     if (gx >= nf) gx -= nf;
@@ -749,8 +743,8 @@ __global__ void k_deposit_codes(PCodes c0, PCodes c1, const int64_t* off0, const
   }
   const int nc = g.nc;
   for (int i = threadIdx.x; i < nsc; i += blockDim.x) {
-    long long val = sc[i];
-    if (val == 0) continue;
+    Acc val = sc[i];
+    if (val == (Acc)0) continue;
     int lx = i % cx, ly = (i / cx) % cy, lz = i / (cx * cy);
     int gx = cb.ix0 + lx, gy = cb.iy0 + ly, gz = cb.iz0 + lz;
     if (gx >= nc) gx -= nc;
@@ -878,17 +872,15 @@ __global__ void k_ikd_count(PCodes c0, PCodes c1, const int64_t* off0, const int
       const int64_t p1 = ro[bk.RX] < in.n ? ro[bk.RX] : in.n;
       for (int64_t p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
         const int ixl = row_cell(ro, bk.RX, p);
-        const uint8_t* q = in.pos + 3 * p;
+        int q[3], qv[3];
+        unpack_pos(in.pos[p], q);
+        load_vel(in.vel, in.vel16, p, qv);
         float x[3], v[3], a[3];
         x[0] = decode_pos(cb.ix0 + ixl, q[0], pscale);
         x[1] = decode_pos(iy, q[1], pscale);
         x[2] = decode_pos(iz, q[2], pscale);
 #pragma unroll
-        for (int d = 0; d < 3; ++d) {
-          int qv = in.vel16 ? (int)reinterpret_cast<const uint16_t*>(in.vel)[3 * p + d]
-                            : (int)reinterpret_cast<const uint8_t*>(in.vel)[3 * p + d];
-          v[d] = decode_vel(qv, half, step);
-        }
+        for (int d = 0; d < 3; ++d) v[d] = decode_vel(qv[d], half, step);
         gather_local(sf, fx, fy, fz, bxf, byf, bzf, x[0], x[1], x[2], a);
         if (g.two) {
           float b[3];
@@ -998,16 +990,11 @@ __global__ void k_ikd_scatter(int64_t n0, int64_t n1, const int64_t* off0, const
           atomicOr(status, ST_CORRUPT);
           continue;
         }
-        const uint32_t pq = tpos[t];
-        o.pos[3 * dst] = (uint8_t)(pq & 0xff);
-        o.pos[3 * dst + 1] = (uint8_t)((pq >> 8) & 0xff);
-        o.pos[3 * dst + 2] = (uint8_t)((pq >> 16) & 0xff);
+        o.pos[dst] = tpos[t];
+        int qv[3];
 #pragma unroll
-        for (int d = 0; d < 3; ++d) {
-          int qv = encode_vel(tv[3 * t + d], sv, half, vzero);
-          if (o.vel16) reinterpret_cast<uint16_t*>(o.vel)[3 * dst + d] = (uint16_t)qv;
-          else reinterpret_cast<uint8_t*>(o.vel)[3 * dst + d] = (uint8_t)qv;
-        }
+        for (int d = 0; d < 3; ++d) qv[d] = encode_vel(tv[3 * t + d], sv, half, vzero);
+        store_vel(o.vel, o.vel16, dst, qv);
       }
     }
   }
@@ -1062,7 +1049,7 @@ cudaError_t launch_kick_drift(float* x, float* v, int64_t n, const Geo& g, const
 cudaError_t launch_compress(const float* x, const float* v, int64_t n, const Geo& g, uint32_t* counts,
                             uint32_t* vmax_bits, const float* vmax_in, int64_t* off, pm_codes_t& out, bool vel16,
                             void* partial, int* status, cudaStream_t st) {
-  PCodesOut o{out.pos, out.vel, out.vmax, vel16};
+  PCodesOut o{reinterpret_cast<uint32_t*>(out.pos), out.vel, out.vmax, vel16};
   cudaMemsetAsync(vmax_bits, 0, sizeof(uint32_t), st);
   int grid = grid_for(n > 0 ? n : 1, 256);
   k_compress_pass<0><<<grid, 256, 0, st>>>(x, v, n, g, counts, vmax_bits, vmax_in, off, o, status);
@@ -1095,11 +1082,11 @@ int window_cells(const Geo& g, const Blk& bk) {
   return wx * wy * wz;
 }
 
-size_t deposit_codes_smem(const Geo& g, const Blk& bk, bool) {
+size_t deposit_codes_smem(const Geo& g, const Blk& bk, bool fixed) {
   size_t nrow = (size_t)bk.RY * bk.RZ;
   size_t fine = (size_t)(bk.RX * g.rcmp + 1) * (bk.RY * g.rcmp + 1) * (bk.RZ * g.rcmp + 1);
   size_t coarse = g.two ? (size_t)(bk.RX + 1) * (bk.RY + 1) * (bk.RZ + 1) : 0;
-  return 2 * nrow * (bk.RX + 1) * sizeof(int64_t) + (fine + coarse) * sizeof(long long);
+  return 2 * nrow * (bk.RX + 1) * sizeof(int64_t) + (fine + coarse) * (fixed ? 8 : 4);
 }
 
 cudaError_t launch_deposit_codes(const PCodes& c0, const PCodes& c1, const int64_t* off0, const int64_t* off1,
@@ -1108,14 +1095,13 @@ cudaError_t launch_deposit_codes(const PCodes& c0, const PCodes& c1, const int64
   size_t smem = deposit_codes_smem(g, bk, fixed);
   int nblk = bk.nbx * bk.nby * bk.nbz;
   if (fixed) {
-    cudaFuncSetAttribute(k_deposit_codes<long long, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_deposit_codes<long long, true><<<nblk, 256, smem, st>>>(c0, c1, off0, off1, g, bk, m0, m1, M0, M1,
-                                                              static_cast<long long*>(rho_c),
-                                                              static_cast<long long*>(rho_f));
+    cudaFuncSetAttribute(k_deposit_codes<long long>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_deposit_codes<long long><<<nblk, 256, smem, st>>>(c0, c1, off0, off1, g, bk, m0, m1, M0, M1,
+                                                       static_cast<long long*>(rho_c), static_cast<long long*>(rho_f));
   } else {
-    cudaFuncSetAttribute(k_deposit_codes<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_deposit_codes<float, false><<<nblk, 256, smem, st>>>(c0, c1, off0, off1, g, bk, m0, m1, M0, M1,
-                                                           static_cast<float*>(rho_c), static_cast<float*>(rho_f));
+    cudaFuncSetAttribute(k_deposit_codes<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_deposit_codes<float><<<nblk, 256, smem, st>>>(c0, c1, off0, off1, g, bk, m0, m1, M0, M1,
+                                                   static_cast<float*>(rho_c), static_cast<float*>(rho_f));
   }
   note_launches(1);
   return cudaGetLastError();
@@ -1128,7 +1114,7 @@ cudaError_t launch_ikd_count(const PCodes& c0, const PCodes& c1, const int64_t* 
   size_t smem = ikd_count_smem(g, bk);
   int nblk = bk.nbx * bk.nby * bk.nbz;
   cudaFuncSetAttribute(k_ikd_count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k_ikd_count<<<nblk, 256, smem, st>>>(c0, c1, off0, off1, g, bk, acc_c, acc_f, ck, cd, counts0, counts1, vmax_bits,
+  k_ikd_count<<<nblk, 512, smem, st>>>(c0, c1, off0, off1, g, bk, acc_c, acc_f, ck, cd, counts0, counts1, vmax_bits,
                                        tkey, tpos, tv);
   note_launches(1);
   return cudaGetLastError();
@@ -1141,7 +1127,7 @@ cudaError_t launch_ikd_scatter(int64_t n0, int64_t n1, const int64_t* off0, cons
   size_t smem = ikd_scatter_smem(g, bk);
   int nblk = bk.nbx * bk.nby * bk.nbz;
   cudaFuncSetAttribute(k_ikd_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k_ikd_scatter<<<nblk, 256, smem, st>>>(n0, n1, off0, off1, g, bk, counts0, counts1, newoff0, newoff1, o0, o1, tkey,
+  k_ikd_scatter<<<nblk, 512, smem, st>>>(n0, n1, off0, off1, g, bk, counts0, counts1, newoff0, newoff1, o0, o1, tkey,
                                          tpos, tv, status);
   note_launches(1);
   return cudaGetLastError();

@@ -22,7 +22,7 @@ struct Blk {
 };
 
 struct PCodes {
-  const uint8_t* pos;
+  const uint32_t* pos;
   const void* vel;
   const float* vmax;
   int64_t n;
@@ -30,7 +30,7 @@ struct PCodes {
 };
 
 struct PCodesOut {
-  uint8_t* pos;
+  uint32_t* pos;
   void* vel;
   float* vmax;
   bool vel16;

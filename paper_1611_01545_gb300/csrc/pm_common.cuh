@@ -99,6 +99,35 @@ __device__ __forceinline__ int encode_vel(float v, float s, int half, bool zero)
   int q = (f < 0.f) ? 0 : (f > (float)(2 * half - 1) ? 2 * half - 1 : (int)f);
   return q;
 }
+// In-memory codes hold one padded word per particle: position bytes
+// (px, py, pz, 0) as a uint32; velocity codes (vx, vy, vz, 0) as a uint32
+// (8-bit codes) or as four uint16 in a uint64 (16-bit codes).
+__device__ __forceinline__ void unpack_pos(uint32_t w, int q[3]) {
+  q[0] = (int)(w & 0xffu);
+  q[1] = (int)((w >> 8) & 0xffu);
+  q[2] = (int)((w >> 16) & 0xffu);
+}
+__device__ __forceinline__ void load_vel(const void* vel, bool vel16, int64_t p, int q[3]) {
+  if (vel16) {
+    unsigned long long w = reinterpret_cast<const unsigned long long*>(vel)[p];
+    q[0] = (int)(w & 0xffffull);
+    q[1] = (int)((w >> 16) & 0xffffull);
+    q[2] = (int)((w >> 32) & 0xffffull);
+  } else {
+    uint32_t w = reinterpret_cast<const uint32_t*>(vel)[p];
+    q[0] = (int)(w & 0xffu);
+    q[1] = (int)((w >> 8) & 0xffu);
+    q[2] = (int)((w >> 16) & 0xffu);
+  }
+}
+__device__ __forceinline__ void store_vel(void* vel, bool vel16, int64_t p, const int q[3]) {
+  if (vel16)
+    reinterpret_cast<unsigned long long*>(vel)[p] =
+        (unsigned long long)q[0] | ((unsigned long long)q[1] << 16) | ((unsigned long long)q[2] << 32);
+  else
+    reinterpret_cast<uint32_t*>(vel)[p] = (uint32_t)q[0] | ((uint32_t)q[1] << 8) | ((uint32_t)q[2] << 16);
+}
+
 // In-cell byte and cell coordinate of x in [0, nf): u = x / rcmp (exact).
 __device__ __forceinline__ void encode_pos(float x, float inv_r, int ncmp, int& c, int& q) {
   float u = __fmul_rn(x, inv_r);

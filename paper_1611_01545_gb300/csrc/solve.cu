@@ -75,10 +75,14 @@ __global__ void __launch_bounds__(SolveCfg<N>::threads) k_solve_a(SolveArgs a) {
   int ox, oy, oz;
   problem_origin(a, a.p0 + pb, ox, oy, oz);
   const int n = a.src_n;
-  const int gz = pmod(oz + z, n);
+  // origins lie in (-n, n) and N <= n, so one conditional wrap suffices
+  int gz = oz + z;
+  gz += gz < 0 ? n : (gz >= n ? -n : 0);
   for (int i = threadIdx.x; i < N * N; i += blockDim.x) {
     int y = i / N, x = i - y * N;
-    int gy = pmod(oy + y, n), gx = pmod(ox + x, n);
+    int gy = oy + y, gx = ox + x;
+    gy += gy < 0 ? n : (gy >= n ? -n : 0);
+    gx += gx < 0 ? n : (gx >= n ? -n : 0);
     float v = load_src(a, ((int64_t)gz * n + gy) * n + gx);
     float* w = reinterpret_cast<float*>(&W[(y >> 1) * N + x]);
     w[y & 1] = v;

@@ -38,8 +38,8 @@ class Codes:
     cnt: torch.Tensor       # uint8 [n_cmp^3]
     esc: torch.Tensor       # int32 viewed as uint32 pairs [esc_cap, 2]
     n_esc: torch.Tensor     # int32 [1]
-    pos: torch.Tensor       # uint8 [n, 3]
-    vel: torch.Tensor       # int16 (uint16 bits) or uint8 [n, 3]
+    pos: torch.Tensor       # uint8 [n, 4]: px, py, pz, 0
+    vel: torch.Tensor       # int16 (uint16 bits) or uint8 [n, 4]: vx, vy, vz, 0
     vmax: torch.Tensor      # float32 [1]
 
     @staticmethod
@@ -51,8 +51,8 @@ class Codes:
         return Codes(n=n, cnt=torch.empty(ncell, dtype=torch.uint8, device=device),
                      esc=torch.zeros((esc_cap, 2), dtype=torch.int32, device=device),
                      n_esc=torch.zeros(1, dtype=torch.int32, device=device),
-                     pos=torch.empty((n, 3), dtype=torch.uint8, device=device),
-                     vel=torch.empty((n, 3), dtype=vdt, device=device),
+                     pos=torch.zeros((n, 4), dtype=torch.uint8, device=device),
+                     vel=torch.zeros((n, 4), dtype=vdt, device=device),
                      vmax=torch.zeros(1, dtype=torch.float32, device=device))
 
     def struct(self) -> pm_codes_t:
@@ -66,8 +66,8 @@ class Codes:
         return Codes(self.n, mv(self.cnt), mv(self.esc), mv(self.n_esc), mv(self.pos), mv(self.vel), mv(self.vmax))
 
     def vel_u16(self) -> torch.Tensor:
-        """Velocity codes as int64 values 0..65535 (or 0..255)."""
-        v = self.vel.to(torch.int64)
+        """Velocity codes [n, 3] as int64 values 0..65535 (or 0..255)."""
+        v = self.vel[:, :3].to(torch.int64)
         return v & 0xFFFF if self.vel.dtype == torch.int16 else v
 
 

@@ -14,11 +14,16 @@ def lib_codes_from_oracle(c: codec.Codes, device="cuda", esc_cap=None):
     esc = np.zeros((cap, 2), np.uint32)
     esc[:c.esc_cell.size, 0] = c.esc_cell
     esc[:c.esc_cell.size, 1] = c.esc_count
-    vel = c.vel.astype(np.uint16).view(np.int16) if c.vel_bits == 16 else c.vel.astype(np.uint8)
+    pos = np.zeros((n, 4), np.uint8)
+    pos[:, :3] = c.pos
+    vel = np.zeros((n, 4), np.uint16 if c.vel_bits == 16 else np.uint8)
+    vel[:, :3] = c.vel
+    if c.vel_bits == 16:
+        vel = vel.view(np.int16)
     return Codes(n=n, cnt=torch.from_numpy(c.cnt.copy()).to(device),
                  esc=torch.from_numpy(esc.view(np.int32)).to(device),
                  n_esc=torch.tensor([c.esc_cell.size], dtype=torch.int32, device=device),
-                 pos=torch.from_numpy(c.pos.copy()).to(device),
+                 pos=torch.from_numpy(pos).to(device),
                  vel=torch.from_numpy(np.ascontiguousarray(vel)).to(device),
                  vmax=torch.tensor([float(c.vmax)], dtype=torch.float32, device=device))
 
@@ -28,9 +33,11 @@ def oracle_codes_from_lib(c, n_cmp: int, vel_bits: int) -> codec.Codes:
     esc = c.esc.cpu().numpy().view(np.uint32)[:ne]
     vel = c.vel.cpu().numpy()
     vel = vel.view(np.uint16) if vel_bits == 16 else vel.astype(np.uint8)
+    pos = c.pos.cpu().numpy()
+    assert np.all(pos[:, 3] == 0) and np.all(vel[:, 3] == 0), "pad bytes must be zero"
     return codec.Codes(n_cmp=n_cmp, vel_bits=vel_bits, cnt=c.cnt.cpu().numpy().copy(),
-                       esc_cell=esc[:, 0].copy(), esc_count=esc[:, 1].copy(), pos=c.pos.cpu().numpy().copy(),
-                       vel=vel.copy(), vmax=np.float32(c.vmax.cpu().item()))
+                       esc_cell=esc[:, 0].copy(), esc_count=esc[:, 1].copy(), pos=pos[:, :3].copy(),
+                       vel=vel[:, :3].copy(), vmax=np.float32(c.vmax.cpu().item()))
 
 
 def records(c: codec.Codes) -> np.ndarray:

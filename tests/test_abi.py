@@ -50,8 +50,12 @@ def _host_codes(c: codec.Codes):
     keep["cnt"] = np.ascontiguousarray(c.cnt)
     keep["esc"] = esc
     keep["n_esc"] = np.array([c.esc_cell.size], np.uint32)
-    keep["pos"] = np.ascontiguousarray(c.pos)
-    keep["vel"] = np.ascontiguousarray(c.vel)
+    pos = np.zeros((c.n, 4), np.uint8)
+    pos[:, :3] = c.pos
+    vel = np.zeros((c.n, 4), c.vel.dtype)
+    vel[:, :3] = c.vel
+    keep["pos"] = pos
+    keep["vel"] = vel
     keep["vmax"] = np.array([c.vmax], np.float32)
     s = pm_codes_t(c.n, keep["cnt"].ctypes.data, keep["esc"].ctypes.data, esc.shape[0], keep["n_esc"].ctypes.data,
                    keep["pos"].ctypes.data, keep["vel"].ctypes.data, keep["vmax"].ctypes.data)
@@ -73,8 +77,9 @@ def test_host_serializer_matches_golden(lib, case):
     s2, keep2 = _host_codes(d)
     src = (ctypes.c_uint8 * len(case["hex"])).from_buffer_copy(case["hex"])
     assert lib.pm_deserialize(src, len(case["hex"]), case["n_cmp"], case["vel_bits"], ctypes.byref(s2)) == 0
-    np.testing.assert_array_equal(keep2["pos"], c.pos)
-    np.testing.assert_array_equal(keep2["vel"], c.vel)
+    np.testing.assert_array_equal(keep2["pos"][:, :3], c.pos)
+    np.testing.assert_array_equal(keep2["vel"][:, :3], c.vel)
+    assert np.all(keep2["pos"][:, 3] == 0) and np.all(keep2["vel"][:, 3] == 0)
     np.testing.assert_array_equal(keep2["cnt"], c.cnt)
     assert keep2["vmax"][0] == c.vmax
 
