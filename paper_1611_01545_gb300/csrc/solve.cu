@@ -54,15 +54,20 @@ __device__ __forceinline__ void problem_origin(const SolveArgs& a, int p, int& o
   oz = pz * a.t - a.b;
 }
 
-__device__ __forceinline__ float load_src(const SolveArgs& a, int64_t idx) {
-  if (a.src_fixed) {
-    long long v = static_cast<const long long*>(a.src)[idx];
-    return (float)((double)v * 2.3283064365386963e-10);  // 2^-32
-  }
-  return static_cast<const float*>(a.src)[idx];
+// Row loops below give each warp whole rows and each lane strided columns, so
+// row indices are computed once per row and no division is needed.
+#define PM_ROWS(row, nrows) for (int row = threadIdx.x >> 5; row < (nrows); row += (blockDim.x >> 5))
+#define PM_COLS(col, ncols) for (int col = threadIdx.x & 31; col < (ncols); col += 32)
+
+template <bool FIXED>
+__device__ __forceinline__ float src_value(const void* src, int64_t idx) {
+  if (FIXED) return (float)((double)static_cast<const long long*>(src)[idx] * 2.3283064365386963e-10);  // 2^-32
+  return __ldg(static_cast<const float*>(src) + idx);
 }
 
-template <int N>
+__device__ __forceinline__ int wrap1(int g, int n) { return g < 0 ? g + n : (g >= n ? g - n : g); }
+
+template <int N, bool FIXED>
 __global__ void __launch_bounds__(SolveCfg<N>::threads) k_solve_a(SolveArgs a) {
   constexpr int NH = SolveCfg<N>::NH;
   extern __shared__ float2 sm[];
@@ -76,31 +81,30 @@ __global__ void __launch_bounds__(SolveCfg<N>::threads) k_solve_a(SolveArgs a) {
   problem_origin(a, a.p0 + pb, ox, oy, oz);
   const int n = a.src_n;
   // origins lie in (-n, n) and N <= n, so one conditional wrap suffices
-  int gz = oz + z;
-  gz += gz < 0 ? n : (gz >= n ? -n : 0);
-  for (int i = threadIdx.x; i < N * N; i += blockDim.x) {
-    int y = i / N, x = i - y * N;
-    int gy = oy + y, gx = ox + x;
-    gy += gy < 0 ? n : (gy >= n ? -n : 0);
-    gx += gx < 0 ? n : (gx >= n ? -n : 0);
-    float v = load_src(a, ((int64_t)gz * n + gy) * n + gx);
-    float* w = reinterpret_cast<float*>(&W[(y >> 1) * N + x]);
-    w[y & 1] = v;
+  const int gz = wrap1(oz + z, n);
+  PM_ROWS(y, N) {
+    const int64_t rowbase = ((int64_t)gz * n + wrap1(oy + y, n)) * n;
+    float* w = reinterpret_cast<float*>(W + (y >> 1) * N) + (y & 1);
+    PM_COLS(x, N) w[2 * x] = src_value<FIXED>(a.src, rowbase + wrap1(ox + x, n));
   }
   __syncthreads();
   fft_fwd<N, N / 2, N, 1>(W, tw);
   // Unpack the two real rows of each packed row: A = (Z_k + conj Z_-k)/2, B = (Z_k - conj Z_-k)/(2i).
-  for (int i = threadIdx.x; i < (N / 2) * NH; i += blockDim.x) {
-    int j = i / NH, k = i - j * NH;
-    float2 zk = W[j * N + slot_of<N>(k)];
-    float2 zm = W[j * N + slot_of<N>((N - k) % N)];
-    P[(2 * j) * NH + k] = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
-    P[(2 * j + 1) * NH + k] = make_float2(0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));
+  PM_ROWS(j, N / 2) {
+    const float2* Wj = W + j * N;
+    PM_COLS(k, NH) {
+      float2 zk = Wj[slot_of<N>(k)];
+      float2 zm = Wj[slot_of<N>(k == 0 ? 0 : N - k)];
+      P[(2 * j) * NH + k] = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
+      P[(2 * j + 1) * NH + k] = make_float2(0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));
+    }
   }
   __syncthreads();
   fft_fwd<N, NH, 1, NH>(P, tw);
-  float2* out = a.spec + ((size_t)pb * N + z) * N * NH;
-  for (int i = threadIdx.x; i < N * NH; i += blockDim.x) out[i] = P[i];
+  // N * NH is even for every supported N: copy two complex values per access.
+  float4* out = reinterpret_cast<float4*>(a.spec + ((size_t)pb * N + z) * N * NH);
+  const float4* P4 = reinterpret_cast<const float4*>(P);
+  for (int i = threadIdx.x; i < N * NH / 2; i += blockDim.x) out[i] = P4[i];
 }
 
 template <int N>
@@ -113,27 +117,30 @@ __global__ void __launch_bounds__(SolveCfg<N>::threads) k_solve_b(SolveArgs a) {
   for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = a.tw[i];
   const int ys = blockIdx.x;   // ky in slot order
   const int pb = blockIdx.y;
-  const float2* in = a.spec + (size_t)pb * N * N * NH;
-  for (int i = threadIdx.x; i < N * NH; i += blockDim.x) {
-    int z = i / NH, kx = i - z * NH;
-    F[i] = in[((size_t)z * N + ys) * NH + kx];
+  const float2* in = a.spec + (size_t)pb * N * N * NH + (size_t)ys * NH;
+  PM_ROWS(z, N) {
+    const float2* src = in + (size_t)z * N * NH;
+    PM_COLS(kx, NH) F[z * NH + kx] = src[kx];
   }
   __syncthreads();
   fft_fwd<N, NH, 1, NH>(F, tw);
   for (int d = 0; d < 3; ++d) {
-    const float* K = a.kern + (size_t)d * N * N * NH;
-    for (int i = threadIdx.x; i < N * NH; i += blockDim.x) {
-      int zs = i / NH, kx = i - zs * NH;
-      float k = K[((size_t)zs * N + ys) * NH + kx];
-      float2 f = F[i];
-      G[i] = make_float2(-f.y * k, f.x * k);   // i K f
+    const float* K = a.kern + (size_t)d * N * N * NH + (size_t)ys * NH;
+    PM_ROWS(zs, N) {
+      const float* Kz = K + (size_t)zs * N * NH;
+      PM_COLS(kx, NH) {
+        float k = __ldg(Kz + kx);
+        float2 f = F[zs * NH + kx];
+        G[zs * NH + kx] = make_float2(-f.y * k, f.x * k);   // i K f
+      }
     }
     __syncthreads();
     fft_inv<N, NH, 1, NH>(G, tw);
-    float2* out = a.spec3 + ((size_t)pb * 3 + d) * a.t * N * NH;
-    for (int i = threadIdx.x; i < a.t * NH; i += blockDim.x) {
-      int zo = i / NH, kx = i - zo * NH;
-      out[((size_t)zo * N + ys) * NH + kx] = G[(zo + a.b) * NH + kx];
+    float2* out = a.spec3 + ((size_t)pb * 3 + d) * a.t * N * NH + (size_t)ys * NH;
+    PM_ROWS(zo, a.t) {
+      float2* dst = out + (size_t)zo * N * NH;
+      const float2* g = G + (zo + a.b) * NH;
+      PM_COLS(kx, NH) dst[kx] = g[kx];
     }
     __syncthreads();
   }
@@ -150,23 +157,27 @@ __global__ void __launch_bounds__(SolveCfg<N>::threads) k_solve_c(SolveArgs a) {
   const int zo = blockIdx.x;
   const int d = blockIdx.y;
   const int pb = blockIdx.z;
-  const float2* in = a.spec3 + (((size_t)pb * 3 + d) * a.t + zo) * N * NH;
-  for (int i = threadIdx.x; i < N * NH; i += blockDim.x) P[i] = in[i];
+  const float4* in = reinterpret_cast<const float4*>(a.spec3 + (((size_t)pb * 3 + d) * a.t + zo) * N * NH);
+  float4* P4 = reinterpret_cast<float4*>(P);
+  for (int i = threadIdx.x; i < N * NH / 2; i += blockDim.x) P4[i] = in[i];
   __syncthreads();
   fft_inv<N, NH, 1, NH>(P, tw);
   const int half_rows = a.t / 2;
-  for (int i = threadIdx.x; i < half_rows * N; i += blockDim.x) {
-    int j = i / N, k = i - j * N;
-    int ya = a.b + 2 * j, yb = ya + 1;
-    float2 A, B;
-    if (k <= N / 2) {
-      A = P[ya * NH + k];
-      B = P[yb * NH + k];
-    } else {
-      A = conjf2(P[ya * NH + (N - k)]);
-      B = conjf2(P[yb * NH + (N - k)]);
+  PM_ROWS(j, half_rows) {
+    const float2* Pa = P + (a.b + 2 * j) * NH;
+    const float2* Pb = Pa + NH;
+    float2* Wj = W + j * N;
+    PM_COLS(k, N) {
+      float2 A, B;
+      if (k <= N / 2) {
+        A = Pa[k];
+        B = Pb[k];
+      } else {
+        A = conjf2(Pa[N - k]);
+        B = conjf2(Pb[N - k]);
+      }
+      Wj[slot_of<N>(k)] = make_float2(A.x - B.y, A.y + B.x);   // A + i B
     }
-    W[j * N + slot_of<N>(k)] = make_float2(A.x - B.y, A.y + B.x);   // A + i B
   }
   __syncthreads();
   fft_inv_rows<N, N>(W, half_rows, tw);
@@ -175,14 +186,11 @@ __global__ void __launch_bounds__(SolveCfg<N>::threads) k_solve_c(SolveArgs a) {
   const int n = a.src_n;
   // Output cells are interior cells: origin + b + local lies inside [0, n) without wrap.
   const int gz = oz + a.b + zo;
-  float* dst = a.dst + (size_t)d * n * n * n;
-  for (int i = threadIdx.x; i < a.t * a.t; i += blockDim.x) {
-    int yl = i / a.t, xl = i - yl * a.t;
-    int j = yl >> 1;
-    float2 w = W[j * N + a.b + xl];
-    float v = (yl & 1) ? w.y : w.x;
-    int gy = oy + a.b + yl, gx = ox + a.b + xl;
-    dst[((int64_t)gz * n + gy) * n + gx] = v;
+  float* dst = a.dst + (size_t)d * n * n * n + ((int64_t)gz * n + oy + a.b) * n + ox + a.b;
+  PM_ROWS(yl, a.t) {
+    const float* w = reinterpret_cast<const float*>(W + (yl >> 1) * N + a.b) + (yl & 1);
+    float* drow = dst + (int64_t)yl * n;
+    PM_COLS(xl, a.t) drow[xl] = w[2 * xl];
   }
 }
 
@@ -203,7 +211,8 @@ static cudaError_t solve_n(const SolvePlan& p, const void* src, bool fixed, floa
   using C = SolveCfg<N>;
   static bool attr_done = false;
   if (!attr_done) {
-    cudaFuncSetAttribute(k_solve_a<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem_a);
+    cudaFuncSetAttribute(k_solve_a<N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem_a);
+    cudaFuncSetAttribute(k_solve_a<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem_a);
     cudaFuncSetAttribute(k_solve_b<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem_b);
     cudaFuncSetAttribute(k_solve_c<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem_a);
     attr_done = true;
@@ -214,7 +223,8 @@ static cudaError_t solve_n(const SolvePlan& p, const void* src, bool fixed, floa
     SolveArgs a{src, fixed ? 1 : 0, p.src_n, p.nts, p.t, p.b, p0, p.spec, p.spec3, p.kern, p.tw, dst};
     {
       TimedScope ts(tm, N == p.src_n && p.b == 0 ? "fft_a_mesh" : "fft_a_tiles", st);
-      k_solve_a<N><<<dim3(N, nb), C::threads, C::smem_a, st>>>(a);
+      if (fixed) k_solve_a<N, true><<<dim3(N, nb), C::threads, C::smem_a, st>>>(a);
+      else k_solve_a<N, false><<<dim3(N, nb), C::threads, C::smem_a, st>>>(a);
     }
     {
       TimedScope ts(tm, N == p.src_n && p.b == 0 ? "fft_b_mesh" : "fft_b_tiles", st);
