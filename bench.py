@@ -104,7 +104,8 @@ def algorithmic_bytes(cfg, counts, vel_bits):
     NH = T // 2 + 1
     vb = 2 if vel_bits == 16 else 1
     N = sum(counts)
-    batch = cfg.get("tile_batch", 8) or 8
+    n_tiles = (nf // t) ** 3
+    batch = min(cfg.get("tile_batch", 0) or 1024, n_tiles)
     nc = nf // cfg["coarse_ratio"]
     ncell = (nf // cfg["cmp_ratio"]) ** 3
     per_tile_a = T ** 3 * 4 + T * T * NH * 8
@@ -365,7 +366,7 @@ def main():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     p.add_argument("--workload", default="two_level256")
-    p.add_argument("--tile-batch", type=int, default=8)
+    p.add_argument("--tile-batch", type=int, default=0)
     p.add_argument("--no-cpu-baseline", action="store_true")
     args = p.parse_args()
     res = run_reference(args) if args.impl == "reference" else run_gb300(args)

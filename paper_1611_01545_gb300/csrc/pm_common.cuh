@@ -51,7 +51,6 @@ void note_launches(int k);
 cudaError_t solve_launch(const SolvePlan& p, const void* src, bool src_fixed, float* dst, cudaStream_t st,
                          struct Timer* timer);
 cudaError_t tile_window_launch(const SolvePlan& p, const float* src, int64_t tile, float* out, cudaStream_t st);
-size_t solve_smem_max(int N);
 
 // Per-launch CUDA-event timing, accumulated by kind.
 struct Timer {

@@ -90,14 +90,13 @@ __global__ void __launch_bounds__(SolveCfg<N>::threads) k_solve_a(SolveArgs a) {
   __syncthreads();
   fft_fwd<N, N / 2, N, 1>(W, tw);
   // Unpack the two real rows of each packed row: A = (Z_k + conj Z_-k)/2, B = (Z_k - conj Z_-k)/(2i).
-  PM_ROWS(j, N / 2) {
+  for (int i = threadIdx.x; i < (N / 2) * NH; i += blockDim.x) {
+    const int j = i / NH, k = i - j * NH;
     const float2* Wj = W + j * N;
-    PM_COLS(k, NH) {
-      float2 zk = Wj[slot_of<N>(k)];
-      float2 zm = Wj[slot_of<N>(k == 0 ? 0 : N - k)];
-      P[(2 * j) * NH + k] = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
-      P[(2 * j + 1) * NH + k] = make_float2(0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));
-    }
+    float2 zk = Wj[slot_of<N>(k)];
+    float2 zm = Wj[slot_of<N>(k == 0 ? 0 : N - k)];
+    P[(2 * j) * NH + k] = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
+    P[(2 * j + 1) * NH + k] = make_float2(0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));
   }
   __syncthreads();
   fft_fwd<N, NH, 1, NH>(P, tw);
@@ -107,42 +106,63 @@ __global__ void __launch_bounds__(SolveCfg<N>::threads) k_solve_a(SolveArgs a) {
   for (int i = threadIdx.x; i < N * NH / 2; i += blockDim.x) out[i] = P4[i];
 }
 
+// Pass B works on one ky row and one half of the kx columns (KC = ceil(NH/2)
+// columns, the second half starting at column KC): forward z FFT, the three
+// kernel products i K_d F written side by side, then one batched inverse z
+// FFT over all 3 KC columns, so a block needs only a few barriers.
+template <int N> struct PassB {
+  static constexpr int NH = N / 2 + 1;
+  static constexpr int KC = (NH + 1) / 2;
+  static constexpr int threads = (N >= 96) ? 384 : 256;
+  static constexpr size_t smem = sizeof(float2) * (N + 4 * (size_t)N * KC);
+};
+
 template <int N>
-__global__ void __launch_bounds__(SolveCfg<N>::threads) k_solve_b(SolveArgs a) {
-  constexpr int NH = SolveCfg<N>::NH;
+__global__ void __launch_bounds__(PassB<N>::threads) k_solve_b(SolveArgs a) {
+  constexpr int NH = PassB<N>::NH, KC = PassB<N>::KC;
   extern __shared__ float2 sm[];
   float2* tw = sm;
-  float2* F = sm + N;          // [z][kx]
-  float2* G = F + N * NH;
+  float2* F = sm + N;             // [z][KC]
+  float2* G = F + N * KC;         // [z][3 KC]: component d in columns d KC .. d KC + KC - 1
   for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = a.tw[i];
-  const int ys = blockIdx.x;   // ky in slot order
-  const int pb = blockIdx.y;
-  const float2* in = a.spec + (size_t)pb * N * N * NH + (size_t)ys * NH;
-  PM_ROWS(z, N) {
-    const float2* src = in + (size_t)z * N * NH;
-    PM_COLS(kx, NH) F[z * NH + kx] = src[kx];
+  const int ys = blockIdx.x;      // ky in slot order
+  const int half = blockIdx.y;    // which half of the kx columns
+  const int pb = blockIdx.z;
+  const int kx0 = half * KC;
+  const int ncol = (NH - kx0) < KC ? (NH - kx0) : KC;
+  const float2* in = a.spec + (size_t)pb * N * N * NH + (size_t)ys * NH + kx0;
+  for (int i = threadIdx.x; i < N * KC; i += blockDim.x) {
+    const int z = i / KC, c = i - z * KC;
+    F[i] = c < ncol ? in[(size_t)z * N * NH + c] : make_float2(0.f, 0.f);
   }
   __syncthreads();
-  fft_fwd<N, NH, 1, NH>(F, tw);
-  for (int d = 0; d < 3; ++d) {
-    const float* K = a.kern + (size_t)d * N * N * NH + (size_t)ys * NH;
-    PM_ROWS(zs, N) {
-      const float* Kz = K + (size_t)zs * N * NH;
-      PM_COLS(kx, NH) {
-        float k = __ldg(Kz + kx);
-        float2 f = F[zs * NH + kx];
-        G[zs * NH + kx] = make_float2(-f.y * k, f.x * k);   // i K f
+  fft_fwd<N, KC, 1, KC>(F, tw);
+  const float* K = a.kern + (size_t)ys * NH + kx0;
+  const size_t kstride = (size_t)N * N * NH;
+  for (int i = threadIdx.x; i < N * KC; i += blockDim.x) {
+    const int zs = i / KC, c = i - zs * KC;
+    const float2 f = F[i];
+    float2* g = G + zs * 3 * KC + c;
+    if (c < ncol) {
+      const float* Kz = K + (size_t)zs * N * NH + c;
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        const float k = __ldg(Kz + d * kstride);
+        g[d * KC] = make_float2(-f.y * k, f.x * k);   // i K f
       }
+    } else {
+#pragma unroll
+      for (int d = 0; d < 3; ++d) g[d * KC] = make_float2(0.f, 0.f);
     }
-    __syncthreads();
-    fft_inv<N, NH, 1, NH>(G, tw);
-    float2* out = a.spec3 + ((size_t)pb * 3 + d) * a.t * N * NH + (size_t)ys * NH;
-    PM_ROWS(zo, a.t) {
-      float2* dst = out + (size_t)zo * N * NH;
-      const float2* g = G + (zo + a.b) * NH;
-      PM_COLS(kx, NH) dst[kx] = g[kx];
+  }
+  __syncthreads();
+  fft_inv<N, 3 * KC, 1, 3 * KC>(G, tw);
+  for (int d = 0; d < 3; ++d) {
+    float2* out = a.spec3 + ((size_t)pb * 3 + d) * a.t * N * NH + (size_t)ys * NH + kx0;
+    for (int i = threadIdx.x; i < a.t * KC; i += blockDim.x) {
+      const int zo = i / KC, c = i - zo * KC;
+      if (c < ncol) out[(size_t)zo * N * NH + c] = G[(zo + a.b) * 3 * KC + d * KC + c];
     }
-    __syncthreads();
   }
 }
 
@@ -213,7 +233,7 @@ static cudaError_t solve_n(const SolvePlan& p, const void* src, bool fixed, floa
   if (!attr_done) {
     cudaFuncSetAttribute(k_solve_a<N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem_a);
     cudaFuncSetAttribute(k_solve_a<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem_a);
-    cudaFuncSetAttribute(k_solve_b<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem_b);
+    cudaFuncSetAttribute(k_solve_b<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PassB<N>::smem);
     cudaFuncSetAttribute(k_solve_c<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem_a);
     attr_done = true;
   }
@@ -228,7 +248,7 @@ static cudaError_t solve_n(const SolvePlan& p, const void* src, bool fixed, floa
     }
     {
       TimedScope ts(tm, N == p.src_n && p.b == 0 ? "fft_b_mesh" : "fft_b_tiles", st);
-      k_solve_b<N><<<dim3(N, nb), C::threads, C::smem_b, st>>>(a);
+      k_solve_b<N><<<dim3(N, 2, nb), PassB<N>::threads, PassB<N>::smem, st>>>(a);
     }
     {
       TimedScope ts(tm, N == p.src_n && p.b == 0 ? "fft_c_mesh" : "fft_c_tiles", st);
@@ -250,18 +270,6 @@ cudaError_t solve_launch(const SolvePlan& p, const void* src, bool fixed, float*
     case 96: return solve_n<96>(p, src, fixed, dst, st, tm);
     case 128: return solve_n<128>(p, src, fixed, dst, st, tm);
     default: return cudaErrorInvalidValue;
-  }
-}
-
-size_t solve_smem_max(int N) {
-  switch (N) {
-    case 16: return SolveCfg<16>::smem_b > SolveCfg<16>::smem_a ? SolveCfg<16>::smem_b : SolveCfg<16>::smem_a;
-    case 32: return SolveCfg<32>::smem_b > SolveCfg<32>::smem_a ? SolveCfg<32>::smem_b : SolveCfg<32>::smem_a;
-    case 48: return SolveCfg<48>::smem_b > SolveCfg<48>::smem_a ? SolveCfg<48>::smem_b : SolveCfg<48>::smem_a;
-    case 64: return SolveCfg<64>::smem_b > SolveCfg<64>::smem_a ? SolveCfg<64>::smem_b : SolveCfg<64>::smem_a;
-    case 96: return SolveCfg<96>::smem_b > SolveCfg<96>::smem_a ? SolveCfg<96>::smem_b : SolveCfg<96>::smem_a;
-    case 128: return SolveCfg<128>::smem_b > SolveCfg<128>::smem_a ? SolveCfg<128>::smem_b : SolveCfg<128>::smem_a;
-    default: return 0;
   }
 }
 
