@@ -90,13 +90,14 @@ __global__ void __launch_bounds__(SolveCfg<N>::threads) k_solve_a(SolveArgs a) {
   __syncthreads();
   fft_fwd<N, N / 2, N, 1>(W, tw);
   // Unpack the two real rows of each packed row: A = (Z_k + conj Z_-k)/2, B = (Z_k - conj Z_-k)/(2i).
-  for (int i = threadIdx.x; i < (N / 2) * NH; i += blockDim.x) {
-    const int j = i / NH, k = i - j * NH;
+  PM_ROWS(j, N / 2) {
     const float2* Wj = W + j * N;
-    float2 zk = Wj[slot_of<N>(k)];
-    float2 zm = Wj[slot_of<N>(k == 0 ? 0 : N - k)];
-    P[(2 * j) * NH + k] = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
-    P[(2 * j + 1) * NH + k] = make_float2(0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));
+    PM_COLS(k, NH) {
+      float2 zk = Wj[slot_of<N>(k)];
+      float2 zm = Wj[slot_of<N>(k == 0 ? 0 : N - k)];
+      P[(2 * j) * NH + k] = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
+      P[(2 * j + 1) * NH + k] = make_float2(0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));
+    }
   }
   __syncthreads();
   fft_fwd<N, NH, 1, NH>(P, tw);
