@@ -150,6 +150,27 @@ int pm_geometry(const pm_handle_t* h, int64_t* n_cmp, int64_t* n_coarse, int64_t
  * reports PM_ERR_CORRUPT through pm_check(). */
 int pm_decompress(pm_handle_t* h, int species, const pm_codes_t* in, float* x, float* v, void* stream);
 
+/* pm_decompress for callers that cannot allocate device memory.  The paper
+ * has no counterpart: this exists for embedding applications that own the
+ * whole device memory budget and forbid libraries to allocate, and for host
+ * threads that must not pay the device-wide synchronisation cudaMalloc and
+ * cudaFree can cause.  No handle is needed and nothing is allocated: the
+ * scratch (CSR offsets of at most 64^3 compression cells, scan partials and a
+ * status word, about 2.1 MB) is one fixed __device__ array inside the library,
+ * which every GPU that loads the library keeps until the process exits.
+ *  n_fine, cmp_ratio, vel_bits  as in pm_config_t; (n_fine/cmp_ratio)^3 must
+ *                               not exceed 64^3, else PM_ERR_ARG;
+ *  in, x, v                     as in pm_decompress (device memory, caller-owned).
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture starts.  Every call shares the one array and
+ * leaves its contents behind; calls that overlap on the GPU (other streams,
+ * other host threads) race on it, so the caller must serialise them.  The
+ * call synchronises `stream` before returning and reports a corrupt stream
+ * as PM_ERR_CORRUPT directly (there is no handle to query). */
+int pm_decompress_noalloc(int32_t n_fine, int32_t cmp_ratio, int32_t vel_bits, const pm_codes_t* in, float* x,
+                          float* v, void* stream);
+
 /* Compress one species (Sec. 2.4) from device float32 x, v [in->n][3] (x in
  * [0, n_fine)).  v_max is the exact max |v_d| unless vmax_in (device float)
  * is given.  out->cnt/esc/n_esc/pos/vel/vmax are written; out->n must equal

@@ -41,7 +41,8 @@ class pm_codes_t(ctypes.Structure):
 EXPORTED = ["pm_init", "pm_destroy", "pm_geometry", "pm_decompress", "pm_compress", "pm_deposit",
             "pm_deposit_fixed", "pm_deposit_codes", "pm_tile_density", "pm_solve", "pm_solve_fixed", "pm_interpolate",
             "pm_kick_drift", "pm_step", "pm_step_host", "pm_check", "pm_last_error", "pm_set_timing",
-            "pm_stage_times", "pm_serialize", "pm_deserialize", "pm_error_string", "pm_launch_count"]
+            "pm_stage_times", "pm_serialize", "pm_deserialize", "pm_error_string", "pm_launch_count",
+            "pm_decompress_noalloc"]
 
 _P = ctypes.c_void_p
 _I64 = ctypes.c_int64
@@ -74,6 +75,8 @@ _PROTOS = {
                                       ctypes.POINTER(pm_codes_t)]),
     "pm_error_string": (ctypes.c_char_p, [ctypes.c_int]),
     "pm_launch_count": (ctypes.c_int64, []),
+    "pm_decompress_noalloc": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                             ctypes.POINTER(pm_codes_t), _P, _P, _P]),
 }
 
 _lib = None
