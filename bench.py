@@ -98,7 +98,9 @@ class ClockSampler:
 
 
 def algorithmic_bytes(cfg, counts, vel_bits):
-    """Algorithmic bytes per launch of each kernel kind (see the design notes)."""
+    """Algorithmic bytes per launch of each kernel kind: what the method itself
+    must move (per-unit figures of the design notes), not the scratch or
+    padding of this implementation."""
     nf, t, b = cfg["n_fine"], cfg["tile"], cfg["buffer"]
     T = t + 2 * b
     NH = T // 2 + 1
@@ -115,11 +117,12 @@ def algorithmic_bytes(cfg, counts, vel_bits):
         "fft_a_tiles": batch * per_tile_a,
         "fft_b_tiles": batch * per_tile_b,
         "fft_c_tiles": batch * per_tile_c,
-        # positions + count bytes read, fine + coarse density written once
-        "deposit": N * 3 + 2 * ncell + nf ** 3 * 4 + nc ** 3 * 4,
-        # codes read, fine + coarse force read once
+        # 3 B of position codes per particle and the count bytes read; fine + coarse density written
+        "deposit": N * 3 + 2 * ncell + (nf ** 3 + nc ** 3) * 4,
+        # position + velocity codes read, fine + coarse acceleration read
         "ikd_count": N * 3 * (1 + vb) + 12 * (nf ** 3 + nc ** 3),
-        "ikd_scatter": N * 3 * (1 + vb) * 2 + 12 * (nf ** 3 + nc ** 3),
+        # position + velocity codes written
+        "ikd_scatter": N * 3 * (1 + vb),
     }
 
 

@@ -781,6 +781,19 @@ __device__ __forceinline__ int window_slot(const Geo& g, const Win& w, uint32_t 
   if (lx >= w.wx || ly >= w.wy || lz >= w.wz) return -1;
   return (lz * w.wy + ly) * w.wx + lx;
 }
+// Window slot of the compression cell with coordinates (cx, cy, cz), or -1.
+__device__ __forceinline__ int window_slot_xyz(const Win& w, int n, int cx, int cy, int cz) {
+  int lx = cx - w.ox, ly = cy - w.oy, lz = cz - w.oz;
+  lx += lx < 0 ? n : (lx >= n ? -n : 0);
+  ly += ly < 0 ? n : (ly >= n ? -n : 0);
+  lz += lz < 0 ? n : (lz >= n ? -n : 0);
+  if (lx >= w.wx || ly >= w.wy || lz >= w.wz) return -1;
+  return (lz * w.wy + ly) * w.wx + lx;
+}
+// Scratch key of a particle: its window slot with the top bit set when its new
+// cell lies in the block's window, else the new cell index itself.
+constexpr uint32_t kInWindow = 0x80000000u;
+
 __device__ __forceinline__ uint32_t window_cell(const Geo& g, const Win& w, int slot) {
   const int n = g.ncmp;
   int lx = slot % w.wx, ly = (slot / w.wx) % w.wy, lz = slot / (w.wx * w.wy);
@@ -895,14 +908,14 @@ __global__ void k_ikd_count(PCodes c0, PCodes c1, const int64_t* off0, const int
 #pragma unroll
         for (int d = 0; d < 3; ++d) encode_pos(x[d], inv_r, g.ncmp, cc[d], qq[d]);
         const uint32_t key = (uint32_t)(cc[0] + g.ncmp * (cc[1] + g.ncmp * cc[2]));
+        const int slot = window_slot_xyz(win, g.ncmp, cc[0], cc[1], cc[2]);
         const int64_t t = toff + p;
-        tkey[t] = key;
+        tkey[t] = slot >= 0 ? (kInWindow | (uint32_t)slot) : key;
         tpos[t] = (uint32_t)qq[0] | ((uint32_t)qq[1] << 8) | ((uint32_t)qq[2] << 16);
         tv[3 * t] = v[0];
         tv[3 * t + 1] = v[1];
         tv[3 * t + 2] = v[2];
         local_max = fmaxf(local_max, fmaxf(fabsf(v[0]), fmaxf(fabsf(v[1]), fabsf(v[2]))));
-        const int slot = window_slot(g, win, key);
         if (slot >= 0) atomicAdd(hs + slot, 1u);
         else atomicAdd(counts + key, 1u);
       }
@@ -945,8 +958,8 @@ __global__ void k_ikd_scatter(int64_t n0, int64_t n1, const int64_t* off0, const
       const int64_t* ro = roff + (s * nrow + row) * (bk.RX + 1);
       const int64_t p0 = ro[0] < n ? ro[0] : n, p1 = ro[bk.RX] < n ? ro[bk.RX] : n;
       for (int64_t p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
-        const int slot = window_slot(g, win, tkey[toff + p]);
-        if (slot >= 0) atomicAdd(hist + s * W + slot, 1u);
+        const uint32_t tk = tkey[toff + p];
+        if (tk & kInWindow) atomicAdd(hist + s * W + (tk & ~kInWindow), 1u);
       }
     }
   }
@@ -975,26 +988,42 @@ __global__ void k_ikd_scatter(int64_t n0, int64_t n1, const int64_t* off0, const
     for (int row = 0; row < nrow; ++row) {
       const int64_t* ro = roff + (s * nrow + row) * (bk.RX + 1);
       const int64_t p0 = ro[0] < n ? ro[0] : n, p1 = ro[bk.RX] < n ? ro[bk.RX] : n;
-      for (int64_t p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
-        const int64_t t = toff + p;
-        const uint32_t key = tkey[t];
-        const int slot = window_slot(g, win, key);
-        int64_t dst;
-        if (slot >= 0) {
-          dst = (int64_t)atomicAdd(base + s * W + slot, 1ull);
-        } else {
-          uint32_t top = atomicSub(counts + key, 1u);
-          dst = newoff[key] + (int64_t)top - 1;
-        }
-        if (dst < 0 || dst >= n) {
-          atomicOr(status, ST_CORRUPT);
-          continue;
-        }
-        o.pos[dst] = tpos[t];
-        int qv[3];
+      // Two particles per thread per iteration keep more independent loads in flight.
+      for (int64_t p = p0 + threadIdx.x; p < p1; p += 2 * blockDim.x) {
+        const int64_t pp[2] = {p, p + blockDim.x};
+        uint32_t tk[2], pq[2];
+        float vv[2][3];
 #pragma unroll
-        for (int d = 0; d < 3; ++d) qv[d] = encode_vel(tv[3 * t + d], sv, half, vzero);
-        store_vel(o.vel, o.vel16, dst, qv);
+        for (int u = 0; u < 2; ++u) {
+          if (pp[u] < p1) {
+            const int64_t t = toff + pp[u];
+            tk[u] = tkey[t];
+            pq[u] = tpos[t];
+            vv[u][0] = tv[3 * t];
+            vv[u][1] = tv[3 * t + 1];
+            vv[u][2] = tv[3 * t + 2];
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          if (pp[u] >= p1) continue;
+          int64_t dst;
+          if (tk[u] & kInWindow) {
+            dst = (int64_t)atomicAdd(base + s * W + (tk[u] & ~kInWindow), 1ull);
+          } else {
+            const uint32_t top = atomicSub(counts + tk[u], 1u);
+            dst = newoff[tk[u]] + (int64_t)top - 1;
+          }
+          if (dst < 0 || dst >= n) {
+            atomicOr(status, ST_CORRUPT);
+            continue;
+          }
+          o.pos[dst] = pq[u];
+          int qv[3];
+#pragma unroll
+          for (int d = 0; d < 3; ++d) qv[d] = encode_vel(vv[u][d], sv, half, vzero);
+          store_vel(o.vel, o.vel16, dst, qv);
+        }
       }
     }
   }
