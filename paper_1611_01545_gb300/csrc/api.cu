@@ -43,9 +43,7 @@ struct pm_handle {
   int64_t scratch_n = 0;
   uint32_t* tkey = nullptr;
   uint32_t* tpos = nullptr;
-  uint32_t* trank = nullptr;
   float* tv = nullptr;
-  uint32_t* blkbase = nullptr;  // [blocks][2 window cells] starting ranks
   std::vector<void*> allocs;
   Timer timer;
   // staging for pm_step_host
@@ -374,7 +372,6 @@ int pm_init(const pm_config_t* cfg, pm_handle_t** out) {
   A(&h->vmax_bits, 2 * 4);
   h->scratch_n = c.count[0] + c.count[1];
   A(&h->tkey, (size_t)h->scratch_n * 4);
-  A(&h->trank, (size_t)h->scratch_n * 4);
   A(&h->tpos, (size_t)h->scratch_n * 4);
   A(&h->tv, (size_t)h->scratch_n * 12);
   A(&h->partial, scan_partial_bytes((int64_t)ncell));
@@ -417,10 +414,6 @@ int pm_init(const pm_config_t* cfg, pm_handle_t** out) {
   }
   h->blk_dep = choose_blk(g, fixed, true);
   h->blk_ikd = choose_blk(g, fixed, false);
-  {
-    const Blk& b = h->blk_ikd;
-    A(&h->blkbase, (size_t)b.nbx * b.nby * b.nbz * 2 * window_cells(h->geo, b) * 4);
-  }
   if (rc != PM_OK) {
     fprintf(stderr, "pm_init: %s\n", h->err.c_str());
     pm_destroy(h);
@@ -597,7 +590,7 @@ int pm_step(pm_handle_t* h, const pm_codes_t in[2], pm_codes_t out[2], double c_
     for (int s = 0; s < 2; ++s) CK(h, cudaMemsetAsync(h->counts[s], 0, (size_t)ncell * 4, st));
     CK(h, launch_ikd_count(view(in[0], vel16), view(in[1], vel16), h->off[0], h->off[1], h->geo, h->blk_ikd,
                            h->acc_c, h->acc_f, ck, cd, h->counts[0], h->counts[1], h->vmax_bits, h->tkey, h->tpos,
-                           h->trank, h->tv, h->blkbase, st));
+                           h->tv, st));
   }
   {
     TimedScope ts(tm, "scan_out", st);
@@ -609,8 +602,8 @@ int pm_step(pm_handle_t* h, const pm_codes_t in[2], pm_codes_t out[2], double c_
   {
     TimedScope ts(tm, "ikd_scatter", st);
     PCodesOut o0 = oview(out[0], vel16), o1 = oview(out[1], vel16);
-    CK(h, launch_ikd_scatter(in[0].n, in[1].n, h->off[0], h->off[1], h->geo, h->blk_ikd, h->newoff[0], h->newoff[1],
-                             o0, o1, h->tkey, h->tpos, h->trank, h->tv, h->blkbase, h->status, st));
+    CK(h, launch_ikd_scatter(in[0].n, in[1].n, h->off[0], h->off[1], h->geo, h->blk_ikd, h->counts[0], h->counts[1],
+                             h->newoff[0], h->newoff[1], o0, o1, h->tkey, h->tpos, h->tv, h->status, st));
   }
   return PM_OK;
 }

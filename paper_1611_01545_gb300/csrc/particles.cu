@@ -809,16 +809,12 @@ __device__ __forceinline__ uint32_t window_cell(const Geo& g, const Win& w, int 
 // coarse: (RX + 1)(RY + 1)(RZ + 1), 3 components) is copied to shared memory
 // with coalesced row loads; every particle is decoded, gathered, kicked and
 // drifted; its new cell, in-cell position bytes and new velocity go to the
-// step's scratch arrays in stream order together with its rank among the
-// block's particles bound for the same cell (shared-memory histogram over the
-// block's window; far movers rank directly on the global count); each window
-// cell's block total is then added to the global count once, and the count
-// before the add -- the block's starting rank in that cell -- is kept per
-// (block, window cell); per-species max |v'_d| is reduced.
+// step's scratch arrays in stream order; new-cell counts are histogrammed in
+// shared memory over the block's window (far movers: global atomics) and
+// flushed once per window cell; per-species max |v'_d| is reduced.
 __global__ void k_ikd_count(PCodes c0, PCodes c1, const int64_t* off0, const int64_t* off1, Geo g, Blk bk,
                             const float* acc_c, const float* acc_f, float ck, float cd, uint32_t* counts0,
-                            uint32_t* counts1, uint32_t* vmax_bits, uint32_t* tkey, uint32_t* tpos, uint32_t* trank,
-                            float* tv, uint32_t* blkbase) {
+                            uint32_t* counts1, uint32_t* vmax_bits, uint32_t* tkey, uint32_t* tpos, float* tv) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const int r = g.rcmp;
   const int nrow = bk.RY * bk.RZ;
@@ -920,54 +916,71 @@ __global__ void k_ikd_count(PCodes c0, PCodes c1, const int64_t* off0, const int
         tv[3 * t + 1] = v[1];
         tv[3 * t + 2] = v[2];
         local_max = fmaxf(local_max, fmaxf(fabsf(v[0]), fmaxf(fabsf(v[1]), fabsf(v[2]))));
-        // rank among this block's particles bound for the same window cell, or
-        // (far movers) among all particles of the cell
-        trank[t] = slot >= 0 ? atomicAdd(hs + slot, 1u) : atomicAdd(counts + key, 1u);
+        if (slot >= 0) atomicAdd(hs + slot, 1u);
+        else atomicAdd(counts + key, 1u);
       }
     }
     block_vmax(local_max, vmax_bits + s);
   }
   __syncthreads();
-  // One reservation per window cell: the block's particles for that cell take
-  // the range [old, old + k) of the cell, old being the count before the add.
-  uint32_t* bb = blkbase + (int64_t)blockIdx.x * 2 * W;
   for (int i = threadIdx.x; i < 2 * W; i += blockDim.x) {
     uint32_t k = hist[i];
-    if (k) bb[i] = atomicAdd((i < W ? counts0 : counts1) + window_cell(g, win, i < W ? i : i - W), k);
+    if (k) atomicAdd((i < W ? counts0 : counts1) + window_cell(g, win, i < W ? i : i - W), k);
   }
 }
 
-// Pass 2: place every particle of a cell block.  After the scan of the counts,
-// a particle's slot is newoff[cell] + (its block's starting rank in the cell)
-// + (its rank within the block), all known from pass 1, so this pass does no
-// atomics: it reads the scratch, quantises the velocity with the new v_max
-// and writes the codes.
+// Pass 2: place every particle of a cell block in its new cell.  Phase 1
+// histograms the block's new cells over its window; phase 2 reserves one
+// contiguous range per window cell from the cell's global cursor (counts,
+// counted down to zero); phase 3 hands out slots from those ranges with
+// shared-memory atomics (far movers take single global slots), quantises the
+// velocity with the new v_max and writes the codes.
 __global__ void k_ikd_scatter(int64_t n0, int64_t n1, const int64_t* off0, const int64_t* off1, Geo g, Blk bk,
-                              const int64_t* newoff0, const int64_t* newoff1, PCodesOut o0, PCodesOut o1,
-                              const uint32_t* tkey, const uint32_t* tpos, const uint32_t* trank, const float* tv,
-                              const uint32_t* blkbase, int* status) {
+                              uint32_t* counts0, uint32_t* counts1, const int64_t* newoff0, const int64_t* newoff1,
+                              PCodesOut o0, PCodesOut o1, const uint32_t* tkey, const uint32_t* tpos, const float* tv,
+                              int* status) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const int nrow = bk.RY * bk.RZ;
   const CellBlock cb = block_of(bk, blockIdx.x);
   const Win win = window_of(g, bk, cb);
   const int W = win.wx * win.wy * win.wz;
   int64_t* roff = reinterpret_cast<int64_t*>(smraw);
-  int64_t* start = roff + 2 * nrow * (bk.RX + 1);
+  unsigned long long* base = reinterpret_cast<unsigned long long*>(roff + 2 * nrow * (bk.RX + 1));
+  uint32_t* hist = reinterpret_cast<uint32_t*>(base + 2 * W);
   load_row_offsets(off0, g, bk, cb, roff);
   load_row_offsets(off1, g, bk, cb, roff + nrow * (bk.RX + 1));
-  const uint32_t* bb = blkbase + (int64_t)blockIdx.x * 2 * W;
+  for (int i = threadIdx.x; i < 2 * W; i += blockDim.x) hist[i] = 0;
+  __syncthreads();
+  for (int s = 0; s < 2; ++s) {
+    const int64_t n = s ? n1 : n0;
+    const int64_t toff = s ? n0 : 0;
+    for (int row = 0; row < nrow; ++row) {
+      const int64_t* ro = roff + (s * nrow + row) * (bk.RX + 1);
+      const int64_t p0 = ro[0] < n ? ro[0] : n, p1 = ro[bk.RX] < n ? ro[bk.RX] : n;
+      for (int64_t p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
+        const uint32_t tk = tkey[toff + p];
+        if (tk & kInWindow) atomicAdd(hist + s * W + (tk & ~kInWindow), 1u);
+      }
+    }
+  }
+  __syncthreads();
   for (int i = threadIdx.x; i < 2 * W; i += blockDim.x) {
+    uint32_t k = hist[i];
+    if (!k) continue;
     const int s = i < W ? 0 : 1;
     const uint32_t cell = window_cell(g, win, i - s * W);
-    start[i] = (s ? newoff1 : newoff0)[cell] + (int64_t)bb[i];
+    uint32_t* counts = s ? counts1 : counts0;
+    const int64_t* newoff = s ? newoff1 : newoff0;
+    uint32_t top = atomicSub(counts + cell, k);
+    base[i] = (unsigned long long)(newoff[cell] + (int64_t)top - (int64_t)k);
   }
   __syncthreads();
   for (int s = 0; s < 2; ++s) {
     const int64_t n = s ? n1 : n0;
     const int64_t toff = s ? n0 : 0;
     const PCodesOut& o = s ? o1 : o0;
+    uint32_t* counts = s ? counts1 : counts0;
     const int64_t* newoff = s ? newoff1 : newoff0;
-    const int64_t* st = start + s * W;
     const int half = o.vel16 ? 32768 : 128;
     const float vm = *o.vmax;
     const bool vzero = !(vm > 0.f);
@@ -975,20 +988,42 @@ __global__ void k_ikd_scatter(int64_t n0, int64_t n1, const int64_t* off0, const
     for (int row = 0; row < nrow; ++row) {
       const int64_t* ro = roff + (s * nrow + row) * (bk.RX + 1);
       const int64_t p0 = ro[0] < n ? ro[0] : n, p1 = ro[bk.RX] < n ? ro[bk.RX] : n;
-      for (int64_t p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
-        const int64_t t = toff + p;
-        const uint32_t tk = tkey[t];
-        const uint32_t rk = trank[t];
-        const int64_t dst = (tk & kInWindow) ? st[tk & ~kInWindow] + (int64_t)rk : newoff[tk] + (int64_t)rk;
-        if (dst < 0 || dst >= n) {
-          atomicOr(status, ST_CORRUPT);
-          continue;
-        }
-        o.pos[dst] = tpos[t];
-        int qv[3];
+      // Two particles per thread per iteration keep more independent loads in flight.
+      for (int64_t p = p0 + threadIdx.x; p < p1; p += 2 * blockDim.x) {
+        const int64_t pp[2] = {p, p + blockDim.x};
+        uint32_t tk[2], pq[2];
+        float vv[2][3];
 #pragma unroll
-        for (int d = 0; d < 3; ++d) qv[d] = encode_vel(tv[3 * t + d], sv, half, vzero);
-        store_vel(o.vel, o.vel16, dst, qv);
+        for (int u = 0; u < 2; ++u) {
+          if (pp[u] < p1) {
+            const int64_t t = toff + pp[u];
+            tk[u] = tkey[t];
+            pq[u] = tpos[t];
+            vv[u][0] = tv[3 * t];
+            vv[u][1] = tv[3 * t + 1];
+            vv[u][2] = tv[3 * t + 2];
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          if (pp[u] >= p1) continue;
+          int64_t dst;
+          if (tk[u] & kInWindow) {
+            dst = (int64_t)atomicAdd(base + s * W + (tk[u] & ~kInWindow), 1ull);
+          } else {
+            const uint32_t top = atomicSub(counts + tk[u], 1u);
+            dst = newoff[tk[u]] + (int64_t)top - 1;
+          }
+          if (dst < 0 || dst >= n) {
+            atomicOr(status, ST_CORRUPT);
+            continue;
+          }
+          o.pos[dst] = pq[u];
+          int qv[3];
+#pragma unroll
+          for (int d = 0; d < 3; ++d) qv[d] = encode_vel(vv[u][d], sv, half, vzero);
+          store_vel(o.vel, o.vel16, dst, qv);
+        }
       }
     }
   }
@@ -1065,7 +1100,7 @@ size_t ikd_count_smem(const Geo& g, const Blk& bk) {
 
 size_t ikd_scatter_smem(const Geo& g, const Blk& bk) {
   size_t nrow = (size_t)bk.RY * bk.RZ;
-  return 2 * nrow * (bk.RX + 1) * sizeof(int64_t) + 2 * (size_t)window_cells(g, bk) * 8;
+  return 2 * nrow * (bk.RX + 1) * sizeof(int64_t) + 2 * (size_t)window_cells(g, bk) * (8 + 4);
 }
 
 int window_cells(const Geo& g, const Blk& bk) {
@@ -1104,25 +1139,25 @@ cudaError_t launch_deposit_codes(const PCodes& c0, const PCodes& c1, const int64
 cudaError_t launch_ikd_count(const PCodes& c0, const PCodes& c1, const int64_t* off0, const int64_t* off1,
                              const Geo& g, const Blk& bk, const float* acc_c, const float* acc_f, float ck, float cd,
                              uint32_t* counts0, uint32_t* counts1, uint32_t* vmax_bits, uint32_t* tkey,
-                             uint32_t* tpos, uint32_t* trank, float* tv, uint32_t* blkbase, cudaStream_t st) {
+                             uint32_t* tpos, float* tv, cudaStream_t st) {
   size_t smem = ikd_count_smem(g, bk);
   int nblk = bk.nbx * bk.nby * bk.nbz;
   cudaFuncSetAttribute(k_ikd_count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   k_ikd_count<<<nblk, 512, smem, st>>>(c0, c1, off0, off1, g, bk, acc_c, acc_f, ck, cd, counts0, counts1, vmax_bits,
-                                       tkey, tpos, trank, tv, blkbase);
+                                       tkey, tpos, tv);
   note_launches(1);
   return cudaGetLastError();
 }
 
 cudaError_t launch_ikd_scatter(int64_t n0, int64_t n1, const int64_t* off0, const int64_t* off1, const Geo& g,
-                               const Blk& bk, const int64_t* newoff0, const int64_t* newoff1, const PCodesOut& o0,
-                               const PCodesOut& o1, const uint32_t* tkey, const uint32_t* tpos, const uint32_t* trank,
-                               const float* tv, const uint32_t* blkbase, int* status, cudaStream_t st) {
+                               const Blk& bk, uint32_t* counts0, uint32_t* counts1, const int64_t* newoff0,
+                               const int64_t* newoff1, const PCodesOut& o0, const PCodesOut& o1, const uint32_t* tkey,
+                               const uint32_t* tpos, const float* tv, int* status, cudaStream_t st) {
   size_t smem = ikd_scatter_smem(g, bk);
   int nblk = bk.nbx * bk.nby * bk.nbz;
   cudaFuncSetAttribute(k_ikd_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k_ikd_scatter<<<nblk, 512, smem, st>>>(n0, n1, off0, off1, g, bk, newoff0, newoff1, o0, o1, tkey, tpos, trank, tv,
-                                         blkbase, status);
+  k_ikd_scatter<<<nblk, 512, smem, st>>>(n0, n1, off0, off1, g, bk, counts0, counts1, newoff0, newoff1, o0, o1, tkey,
+                                         tpos, tv, status);
   note_launches(1);
   return cudaGetLastError();
 }
