@@ -126,6 +126,35 @@ def algorithmic_bytes(cfg, counts, vel_bits):
     }
 
 
+def csrc_digest():
+    """Digest of the CUDA sources; ncu traffic figures apply only to the sources they were taken on."""
+    import glob
+    import hashlib
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_1611_01545_gb300", "csrc")
+    for f in sorted(glob.glob(os.path.join(d, "*.cu")) + glob.glob(os.path.join(d, "*.cuh"))):
+        h.update(os.path.basename(f).encode())
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kind):
+    """DRAM bytes per launch of a kernel kind from the committed ncu summary, or
+    None when the kernels changed since that capture."""
+    path = os.path.join(ROOT, "profiles", "step_kernels_two_level256_ncu.md")
+    try:
+        lines = open(path).read().splitlines()
+    except OSError:
+        return None
+    digest = csrc_digest()
+    for ln in lines:
+        parts = ln.split()
+        if len(parts) == 4 and parts[0] == "traffic" and parts[1] == kind and parts[3] == f"csrc={digest}":
+            return int(parts[2])
+    return None
+
+
 def build_state(pm, w, torch):
     import torch as _t  # noqa: F401
     codes = []
@@ -247,7 +276,8 @@ def run_gb300(args):
         avg_ms = stages[dom][0]
         achieved = alg[dom] / (avg_ms / 1e3) / 1e9
         roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": hbm,
-                    "peak_source": peak_src, "unit": "GB/s", "frac": round(achieved / hbm, 4), "traffic": None,
+                    "peak_source": peak_src, "unit": "GB/s", "frac": round(achieved / hbm, 4),
+                    "traffic": recorded_traffic(dom),
                     "alg_bytes_per_launch": alg[dom], "avg_launch_ms": round(avg_ms, 5)}
     step_ms = ms_max / args.steps
     result = {
