@@ -54,10 +54,20 @@ template <int P, int Q, int DIR, int I = 0>
 struct TwApply {
   static __device__ __forceinline__ void run(float2 (&b)[P][Q]) {
     constexpr int p = I / Q, k1 = I % Q;
+    constexpr int R = P * Q;
     if constexpr (p > 0 && k1 > 0) {
-      constexpr float c = (float)tcos(tw_angle(p * k1, P * Q, DIR));
-      constexpr float s = (float)tsin(tw_angle(p * k1, P * Q, DIR));
-      b[p][k1] = cmul(b[p][k1], make_float2(c, s));
+      if constexpr ((4 * p * k1) % R == 0) {
+        // quarter turns: exact swaps and sign flips, no multiplies
+        constexpr int quarter = ((4 * p * k1) / R) % 4;
+        const float2 a = b[p][k1];
+        if constexpr (quarter == 1) b[p][k1] = DIR < 0 ? make_float2(a.y, -a.x) : make_float2(-a.y, a.x);
+        else if constexpr (quarter == 2) b[p][k1] = make_float2(-a.x, -a.y);
+        else if constexpr (quarter == 3) b[p][k1] = DIR < 0 ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
+      } else {
+        constexpr float c = (float)tcos(tw_angle(p * k1, R, DIR));
+        constexpr float s = (float)tsin(tw_angle(p * k1, R, DIR));
+        b[p][k1] = cmul(b[p][k1], make_float2(c, s));
+      }
     }
     if constexpr (I + 1 < P * Q) TwApply<P, Q, DIR, I + 1>::run(b);
   }

@@ -418,6 +418,28 @@ __device__ __forceinline__ void gather_local(const float* S, int fx, int fy, int
   a[2] = s2;
 }
 
+// The same CIC gather when the lower corner's local index (lx, ly, lz) and the
+// upper weights w1 are already known; same weights and order as gather().
+__device__ __forceinline__ void gather_idx(const float* S, int fx, int fy, int fz, int lx, int ly, int lz,
+                                           const float w1[3], float a[3]) {
+  const float w0[3] = {__fsub_rn(1.0f, w1[0]), __fsub_rn(1.0f, w1[1]), __fsub_rn(1.0f, w1[2])};
+  const int plane = fx * fy * fz;
+  const float* base = S + (lz * fy + ly) * fx + lx;
+  float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const int dx = c & 1, dy = (c >> 1) & 1, dz = c >> 2;
+    const float w = __fmul_rn(__fmul_rn(dx ? w1[0] : w0[0], dy ? w1[1] : w0[1]), dz ? w1[2] : w0[2]);
+    const float* q = base + (dz * fy + dy) * fx + dx;
+    s0 = __fmaf_rn(w, q[0], s0);
+    s1 = __fmaf_rn(w, q[plane], s1);
+    s2 = __fmaf_rn(w, q[2 * plane], s2);
+  }
+  a[0] = s0;
+  a[1] = s1;
+  a[2] = s2;
+}
+
 __device__ __forceinline__ float wrap_pos(float x, float nf) {
   if (x < 0.f) x = __fadd_rn(x, nf);
   if (x >= nf) x = __fsub_rn(x, nf);
@@ -868,7 +890,6 @@ __global__ void k_ikd_count(PCodes c0, PCodes c1, const int64_t* off0, const int
   const float pscale = (float)r / 256.0f;
   const float inv_r = 1.0f / (float)r;
   const float nf = (float)g.nf;
-  const float cinv = g.two ? 1.0f / (float)g.rc : 1.0f;
   for (int s = 0; s < 2; ++s) {
     const PCodes& in = s ? c1 : c0;
     uint32_t* counts = s ? counts1 : counts0;
@@ -894,11 +915,23 @@ __global__ void k_ikd_count(PCodes c0, PCodes c1, const int64_t* off0, const int
         x[2] = decode_pos(iz, q[2], pscale);
 #pragma unroll
         for (int d = 0; d < 3; ++d) v[d] = decode_vel(qv[d], half, step);
-        gather_local(sf, fx, fy, fz, bxf, byf, bzf, x[0], x[1], x[2], a);
+        // Decoded positions are exact dyadics, so the CIC cell and weight come
+        // from the codes in integer arithmetic: x = c r + (2q + 1) r / 512.
+        const int ky = row % bk.RY, kz = row / bk.RY;
+        int num[3];
+        float w1[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          num[d] = (2 * q[d] + 1) * r;
+          w1[d] = __fmul_rn(__int2float_rn(num[d] & 511), 1.0f / 512.0f);
+        }
+        gather_idx(sf, fx, fy, fz, ixl * r + (num[0] >> 9), ky * r + (num[1] >> 9), kz * r + (num[2] >> 9), w1, a);
         if (g.two) {
-          float b[3];
-          gather_local(sc, cx, cy, cz, cb.ix0, cb.iy0, cb.iz0, __fmul_rn(x[0], cinv), __fmul_rn(x[1], cinv),
-                       __fmul_rn(x[2], cinv), b);
+          // coarse cell == compression cell: corner (ixl, ky, kz), weight (2q + 1) / 512
+          float b[3], u1[3];
+#pragma unroll
+          for (int d = 0; d < 3; ++d) u1[d] = __fmul_rn(__int2float_rn(2 * q[d] + 1), 1.0f / 512.0f);
+          gather_idx(sc, cx, cy, cz, ixl, ky, kz, u1, b);
           a[0] = __fadd_rn(b[0], a[0]);
           a[1] = __fadd_rn(b[1], a[1]);
           a[2] = __fadd_rn(b[2], a[2]);
