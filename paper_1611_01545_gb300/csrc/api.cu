@@ -206,8 +206,7 @@ Blk choose_blk(const Geom& g, bool fixed, bool deposit) {
   if (!deposit) {
     while (b.RX > 1 && b.RX % 2 == 0 && ikd_count_smem(geo, b) > 100 * 1024) b.RX /= 2;
   } else {
-    auto dep = [&](const Blk& x) { return g.rcmp >= 2 ? deposit_sorted_smem(geo, x, fixed) : deposit_codes_smem(geo, x, fixed); };
-    while (b.RX > 1 && b.RX % 2 == 0 && dep(b) > 72 * 1024) b.RX /= 2;
+    while (b.RX > 1 && b.RX % 2 == 0 && deposit_codes_smem(geo, b, fixed) > 64 * 1024) b.RX /= 2;
   }
   b.nbx = g.ncmp / b.RX;
   b.nby = g.ncmp / b.RY;

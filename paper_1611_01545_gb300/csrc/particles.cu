@@ -776,200 +776,6 @@ __global__ void k_deposit_codes(PCodes c0, PCodes c1, const int64_t* off0, const
   }
 }
 
-// Race-free deposit of one cell block, the GPU form of the paper's strided CIC
-// loop (Sec. 2.3: the outer loop is strided so that no two threads write the
-// same cells).  Particles of the block are sorted by fine cell with a
-// shared-memory counting sort (chunks of at most DEP_CAP particles); then, for
-// each of the 8 parity classes of fine cells in turn, one thread per cell adds
-// its particles' 8 CIC corners with plain shared-memory adds: cells of one
-// class are at least two apart in some dimension, so their 2x2x2 stencils
-// never overlap.  The coarse corners are summed per run of same-cell particles
-// as before.  Requires an even fine extent in every dimension (cmp_ratio >= 2).
-constexpr int DEP_CAP = 6144;
-
-// Sort record: species (bit 31) and the three 9-bit in-cell fractions
-// (2q + 1) r mod 512 of a decoded position; the fine cell is implied by the slot.
-__device__ __forceinline__ uint32_t dep_record(int s, const int num[3]) {
-  return ((uint32_t)s << 31) | (uint32_t)(num[0] & 511) | ((uint32_t)(num[1] & 511) << 9) |
-         ((uint32_t)(num[2] & 511) << 18);
-}
-
-template <typename Acc>
-__global__ void __launch_bounds__(256) k_deposit_sorted(PCodes c0, PCodes c1, const int64_t* off0, const int64_t* off1,
-                                                        Geo g, Blk bk, float m0, float m1, long long M0, long long M1,
-                                                        Acc* rho_c, Acc* rho_f) {
-  extern __shared__ __align__(16) unsigned char smraw[];
-  const int r = g.rcmp;
-  const int ex = bk.RX * r, ey = bk.RY * r, ez = bk.RZ * r;   // fine cells owned by the block
-  const int fx = ex + 1, fy = ey + 1, fz = ez + 1;            // region incl. the upper halo layer
-  const int cx = bk.RX + 1, cy = bk.RY + 1, cz = bk.RZ + 1;
-  const int nrow = bk.RY * bk.RZ;
-  const int nfc = ex * ey * ez;
-  int64_t* roff = reinterpret_cast<int64_t*>(smraw);
-  Acc* sf = reinterpret_cast<Acc*>(roff + 2 * nrow * (bk.RX + 1));
-  Acc* sc = sf + fx * fy * fz;
-  const int nsf = fx * fy * fz, nsc = g.two ? cx * cy * cz : 0;
-  uint32_t* fcnt = reinterpret_cast<uint32_t*>(sc + (g.two ? nsc : 0));   // [nfc + 1]
-  uint32_t* srec = fcnt + nfc + 1;                                         // [DEP_CAP]
-  __shared__ uint32_t warp_tot[32];
-  for (int i = threadIdx.x; i < nsf + nsc; i += blockDim.x) sf[i] = (Acc)0;
-  const CellBlock cb = block_of(bk, blockIdx.x);
-  load_row_offsets(off0, g, bk, cb, roff);
-  load_row_offsets(off1, g, bk, cb, roff + nrow * (bk.RX + 1));
-  __syncthreads();
-  // particles of the block, both species, enumerated as one sequence
-  int64_t seg_n[2], tot = 0;
-  for (int s = 0; s < 2; ++s) {
-    seg_n[s] = 0;
-    const PCodes& cs = s ? c1 : c0;
-    for (int row = 0; row < nrow; ++row) {
-      const int64_t* ro = roff + (s * nrow + row) * (bk.RX + 1);
-      const int64_t a = ro[0] < cs.n ? ro[0] : cs.n, b = ro[bk.RX] < cs.n ? ro[bk.RX] : cs.n;
-      seg_n[s] += b - a;
-    }
-    tot += seg_n[s];
-  }
-  const float pscale = (float)r / 256.0f;
-  (void)pscale;
-  for (int64_t chunk0 = 0; chunk0 < tot; chunk0 += DEP_CAP) {
-    const int64_t chunk1 = chunk0 + DEP_CAP < tot ? chunk0 + DEP_CAP : tot;
-    for (int i = threadIdx.x; i <= nfc; i += blockDim.x) fcnt[i] = 0;
-    __syncthreads();
-    // pass 1 over the chunk: count fine cells (+ coarse corners); pass 2: place records
-    for (int pass = 0; pass < 2; ++pass) {
-      const int64_t nround = (chunk1 - chunk0 + blockDim.x - 1) / blockDim.x;
-      for (int64_t it = 0; it < nround; ++it) {
-        const int64_t e = chunk0 + it * blockDim.x + threadIdx.x;   // index in the block's sequence
-        const bool live = e < chunk1;
-        int s = 0, row = 0, ixl = 0;
-        int q[3] = {0, 0, 0};
-        if (live) {
-          // locate (species, row, cell) of sequence element e
-          int64_t rem = e;
-          s = rem < seg_n[0] ? 0 : 1;
-          if (s) rem -= seg_n[0];
-          const PCodes& cs = s ? c1 : c0;
-          int64_t p = 0;
-          const int64_t* ro = roff + s * nrow * (bk.RX + 1);
-          for (row = 0; row < nrow; ++row, ro += bk.RX + 1) {
-            const int64_t a = ro[0] < cs.n ? ro[0] : cs.n, b = ro[bk.RX] < cs.n ? ro[bk.RX] : cs.n;
-            if (rem < b - a) { p = a + rem; break; }
-            rem -= b - a;
-          }
-          ixl = row_cell(ro, bk.RX, p);
-          unpack_pos(cs.pos[p], q);
-        }
-        int num[3];
-#pragma unroll
-        for (int d = 0; d < 3; ++d) num[d] = (2 * q[d] + 1) * r;
-        const int ky = row % bk.RY, kz = row / bk.RY;
-        const int fc = ((kz * r + (num[2] >> 9)) * ey + (ky * r + (num[1] >> 9))) * ex + ixl * r + (num[0] >> 9);
-        if (pass == 0) {
-          if (live) atomicAdd(fcnt + fc, 1u);
-          if (g.two) {
-            Acc cv[8];
-            if (live) {
-              float u1[3];
-#pragma unroll
-              for (int d = 0; d < 3; ++d) u1[d] = __fmul_rn(__int2float_rn(2 * q[d] + 1), 1.0f / 512.0f);
-              corner_masses(s ? m1 : m0, s ? M1 : M0, u1, cv);
-            } else {
-#pragma unroll
-              for (int c = 0; c < 8; ++c) cv[c] = (Acc)0;
-            }
-            const unsigned key = live ? (unsigned)((s * nrow + row) * bk.RX + ixl) : 0xffffffffu;
-            if (run_reduce<8, Acc>(key, cv) && live) {
-#pragma unroll
-              for (int c = 0; c < 8; ++c) {
-                int dx = c & 1, dy = (c >> 1) & 1, dz = c >> 2;
-                smem_acc(&sc[((kz + dz) * cy + (ky + dy)) * cx + (ixl + dx)], cv[c]);
-              }
-            }
-          }
-        } else if (live) {
-          const uint32_t slot = atomicAdd(fcnt + fc, 1u);
-          srec[slot] = dep_record(s, num);
-        }
-      }
-      __syncthreads();
-      if (pass == 0) {
-        // exclusive scan of fcnt[0..nfc) in place (fcnt[nfc] = chunk size)
-        const int per = (nfc + blockDim.x - 1) / blockDim.x;
-        const int i0 = threadIdx.x * per, i1 = i0 + per < nfc ? i0 + per : nfc;
-        uint32_t sum = 0;
-        for (int i = i0; i < i1; ++i) sum += fcnt[i];
-        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-        uint32_t inc = sum;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          uint32_t u = __shfl_up_sync(0xffffffffu, inc, o);
-          if (lane >= o) inc += u;
-        }
-        if (lane == 31) warp_tot[wid] = inc;
-        __syncthreads();
-        uint32_t wbase = 0;
-        for (int w = 0; w < wid; ++w) wbase += warp_tot[w];
-        uint32_t run = wbase + inc - sum;
-        for (int i = i0; i < i1; ++i) {
-          uint32_t k = fcnt[i];
-          fcnt[i] = run;
-          run += k;
-        }
-        __syncthreads();
-      }
-    }
-    // fcnt[c] now holds the end of cell c's records; cell c starts at fcnt[c - 1] (0 for c = 0)
-    const int hx = ex / 2, hy = ey / 2, hz = ez / 2;
-    for (int color = 0; color < 8; ++color) {
-      const int px = color & 1, py = (color >> 1) & 1, pz = color >> 2;
-      for (int i = threadIdx.x; i < hx * hy * hz; i += blockDim.x) {
-        const int x = 2 * (i % hx) + px, y = 2 * ((i / hx) % hy) + py, z = 2 * (i / (hx * hy)) + pz;
-        const int fc = (z * ey + y) * ex + x;
-        const uint32_t b0 = fc ? fcnt[fc - 1] : 0u, b1 = fcnt[fc];
-        Acc* tgt = sf + (z * fy + y) * fx + x;
-        for (uint32_t k = b0; k < b1; ++k) {
-          const uint32_t rec = srec[k];
-          const int s = (int)(rec >> 31);
-          float w1[3] = {__fmul_rn(__int2float_rn((int)(rec & 511u)), 1.0f / 512.0f),
-                         __fmul_rn(__int2float_rn((int)((rec >> 9) & 511u)), 1.0f / 512.0f),
-                         __fmul_rn(__int2float_rn((int)((rec >> 18) & 511u)), 1.0f / 512.0f)};
-          Acc t8[8];
-          corner_masses(s ? m1 : m0, s ? M1 : M0, w1, t8);
-#pragma unroll
-          for (int c = 0; c < 8; ++c) {
-            const int dx = c & 1, dy = (c >> 1) & 1, dz = c >> 2;
-            tgt[(dz * fy + dy) * fx + dx] += t8[c];
-          }
-        }
-      }
-      __syncthreads();
-    }
-  }
-  const int nf = g.nf;
-  const int bxf = cb.ix0 * r, byf = cb.iy0 * r, bzf = cb.iz0 * r;
-  for (int i = threadIdx.x; i < nsf; i += blockDim.x) {
-    Acc val = sf[i];
-    if (val == (Acc)0) continue;
-    int lx = i % fx, ly = (i / fx) % fy, lz = i / (fx * fy);
-    int gx = bxf + lx, gy = byf + ly, gz = bzf + lz;
-    if (gx >= nf) gx -= nf;
-    if (gy >= nf) gy -= nf;
-    if (gz >= nf) gz -= nf;
-    global_add(&rho_f[((int64_t)gz * nf + gy) * nf + gx], val);
-  }
-  const int nc = g.nc;
-  for (int i = threadIdx.x; i < nsc; i += blockDim.x) {
-    Acc val = sc[i];
-    if (val == (Acc)0) continue;
-    int lx = i % cx, ly = (i / cx) % cy, lz = i / (cx * cy);
-    int gx = cb.ix0 + lx, gy = cb.iy0 + ly, gz = cb.iz0 + lz;
-    if (gx >= nc) gx -= nc;
-    if (gy >= nc) gy -= nc;
-    if (gz >= nc) gz -= nc;
-    global_add(&rho_c[((int64_t)gz * nc + gy) * nc + gx], val);
-  }
-}
-
 // Window of destination compression cells owned by a cell block's histogram:
 // the block widened by D cells on each side (clamped to the mesh), periodic.
 struct Win {
@@ -1028,7 +834,7 @@ __device__ __forceinline__ uint32_t window_cell(const Geo& g, const Win& w, int 
 // step's scratch arrays in stream order; new-cell counts are histogrammed in
 // shared memory over the block's window (far movers: global atomics) and
 // flushed once per window cell; per-species max |v'_d| is reduced.
-__global__ void __launch_bounds__(512, 2) k_ikd_count(PCodes c0, PCodes c1, const int64_t* off0, const int64_t* off1, Geo g, Blk bk,
+__global__ void k_ikd_count(PCodes c0, PCodes c1, const int64_t* off0, const int64_t* off1, Geo g, Blk bk,
                             const float* acc_c, const float* acc_f, float ck, float cd, uint32_t* counts0,
                             uint32_t* counts1, uint32_t* vmax_bits, uint32_t* tkey, uint32_t* tpos, float* tv) {
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -1162,7 +968,7 @@ __global__ void __launch_bounds__(512, 2) k_ikd_count(PCodes c0, PCodes c1, cons
 // counted down to zero); phase 3 hands out slots from those ranges with
 // shared-memory atomics (far movers take single global slots), quantises the
 // velocity with the new v_max and writes the codes.
-__global__ void __launch_bounds__(512, 2) k_ikd_scatter(int64_t n0, int64_t n1, const int64_t* off0, const int64_t* off1, Geo g, Blk bk,
+__global__ void k_ikd_scatter(int64_t n0, int64_t n1, const int64_t* off0, const int64_t* off1, Geo g, Blk bk,
                               uint32_t* counts0, uint32_t* counts1, const int64_t* newoff0, const int64_t* newoff1,
                               PCodesOut o0, PCodesOut o1, const uint32_t* tkey, const uint32_t* tpos, const float* tv,
                               int* status) {
@@ -1338,15 +1144,6 @@ int window_cells(const Geo& g, const Blk& bk) {
   return wx * wy * wz;
 }
 
-size_t deposit_sorted_smem(const Geo& g, const Blk& bk, bool fixed) {
-  size_t nrow = (size_t)bk.RY * bk.RZ;
-  size_t fine = (size_t)(bk.RX * g.rcmp + 1) * (bk.RY * g.rcmp + 1) * (bk.RZ * g.rcmp + 1);
-  size_t coarse = g.two ? (size_t)(bk.RX + 1) * (bk.RY + 1) * (bk.RZ + 1) : 0;
-  size_t nfc = (size_t)bk.RX * g.rcmp * bk.RY * g.rcmp * bk.RZ * g.rcmp;
-  return 2 * nrow * (bk.RX + 1) * sizeof(int64_t) + (fine + coarse) * (fixed ? 8 : 4) + (nfc + 1) * 4 +
-         (size_t)DEP_CAP * 4 + 16;
-}
-
 size_t deposit_codes_smem(const Geo& g, const Blk& bk, bool fixed) {
   size_t nrow = (size_t)bk.RY * bk.RZ;
   size_t fine = (size_t)(bk.RX * g.rcmp + 1) * (bk.RY * g.rcmp + 1) * (bk.RZ * g.rcmp + 1);
@@ -1357,23 +1154,8 @@ size_t deposit_codes_smem(const Geo& g, const Blk& bk, bool fixed) {
 cudaError_t launch_deposit_codes(const PCodes& c0, const PCodes& c1, const int64_t* off0, const int64_t* off1,
                                  const Geo& g, const Blk& bk, float m0, float m1, long long M0, long long M1,
                                  void* rho_c, void* rho_f, bool fixed, cudaStream_t st) {
-  int nblk = bk.nbx * bk.nby * bk.nbz;
-  if (g.rcmp >= 2) {
-    size_t smem = deposit_sorted_smem(g, bk, fixed);
-    if (fixed) {
-      cudaFuncSetAttribute(k_deposit_sorted<long long>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      k_deposit_sorted<long long><<<nblk, 256, smem, st>>>(c0, c1, off0, off1, g, bk, m0, m1, M0, M1,
-                                                          static_cast<long long*>(rho_c),
-                                                          static_cast<long long*>(rho_f));
-    } else {
-      cudaFuncSetAttribute(k_deposit_sorted<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      k_deposit_sorted<float><<<nblk, 256, smem, st>>>(c0, c1, off0, off1, g, bk, m0, m1, M0, M1,
-                                                      static_cast<float*>(rho_c), static_cast<float*>(rho_f));
-    }
-    note_launches(1);
-    return cudaGetLastError();
-  }
   size_t smem = deposit_codes_smem(g, bk, fixed);
+  int nblk = bk.nbx * bk.nby * bk.nbz;
   if (fixed) {
     cudaFuncSetAttribute(k_deposit_codes<long long>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_deposit_codes<long long><<<nblk, 256, smem, st>>>(c0, c1, off0, off1, g, bk, m0, m1, M0, M1,

@@ -55,7 +55,6 @@ cudaError_t launch_compress(const float* x, const float* v, int64_t n, const Geo
                             uint32_t* vmax_bits, const float* vmax_in, int64_t* off, pm_codes_t& out, bool vel16,
                             void* partial, int* status, cudaStream_t st);
 size_t deposit_codes_smem(const Geo& g, const Blk& bk, bool fixed);
-size_t deposit_sorted_smem(const Geo& g, const Blk& bk, bool fixed);
 size_t ikd_count_smem(const Geo& g, const Blk& bk);
 size_t ikd_scatter_smem(const Geo& g, const Blk& bk);
 int window_cells(const Geo& g, const Blk& bk);
