@@ -834,7 +834,7 @@ __device__ __forceinline__ uint32_t window_cell(const Geo& g, const Win& w, int 
 // step's scratch arrays in stream order; new-cell counts are histogrammed in
 // shared memory over the block's window (far movers: global atomics) and
 // flushed once per window cell; per-species max |v'_d| is reduced.
-__global__ void k_ikd_count(PCodes c0, PCodes c1, const int64_t* off0, const int64_t* off1, Geo g, Blk bk,
+__global__ void __launch_bounds__(512, 2) k_ikd_count(PCodes c0, PCodes c1, const int64_t* off0, const int64_t* off1, Geo g, Blk bk,
                             const float* acc_c, const float* acc_f, float ck, float cd, uint32_t* counts0,
                             uint32_t* counts1, uint32_t* vmax_bits, uint32_t* tkey, uint32_t* tpos, float* tv) {
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -968,7 +968,7 @@ __global__ void k_ikd_count(PCodes c0, PCodes c1, const int64_t* off0, const int
 // counted down to zero); phase 3 hands out slots from those ranges with
 // shared-memory atomics (far movers take single global slots), quantises the
 // velocity with the new v_max and writes the codes.
-__global__ void k_ikd_scatter(int64_t n0, int64_t n1, const int64_t* off0, const int64_t* off1, Geo g, Blk bk,
+__global__ void __launch_bounds__(512, 2) k_ikd_scatter(int64_t n0, int64_t n1, const int64_t* off0, const int64_t* off1, Geo g, Blk bk,
                               uint32_t* counts0, uint32_t* counts1, const int64_t* newoff0, const int64_t* newoff1,
                               PCodesOut o0, PCodesOut o1, const uint32_t* tkey, const uint32_t* tpos, const float* tv,
                               int* status) {
