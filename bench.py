@@ -42,6 +42,17 @@ def dist_env():
     return rank, world, local
 
 
+def job_rate(local_seconds, units_per_rank, world, device="cpu", dist=None):
+    """Whole-job throughput of a weak-scaled replica run: the units of all ranks
+    divided by the slowest rank's time (max over ranks).  Returns (rate, max_s)."""
+    import torch
+    t = torch.tensor([float(local_seconds)], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    worst = float(t.item())
+    return units_per_rank * world / worst, worst
+
+
 class ClockSampler:
     """Samples nvidia-smi clocks and throttle reasons during the timed region."""
 
@@ -231,11 +242,8 @@ def run_gb300(args):
     pm.check()
     stages = pm.stage_times()
     pm.set_timing(False)
-    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
-    value = n_total * args.steps * world / (ms_max / 1e3)
+    value, worst_s = job_rate(ms / 1e3, n_total * args.steps, world, "cuda", dist)
+    ms_max = worst_s * 1e3
 
     # end-to-end through the C ABI with host buffers (pinned), copies in the timed region
     hin = [c.to("cpu", pin=True) for c in a]
@@ -250,10 +258,7 @@ def run_gb300(args):
         pm.step_host(hin, hout, 1.0, 1.0)
         hin, hout = hout, hin
     e2e_s = time.perf_counter() - t0
-    te = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e_value = n_total * k_e2e * world / float(te.item())
+    e2e_value, _ = job_rate(e2e_s, n_total * k_e2e, world, "cuda", dist)
     h2d = sum(codes_bytes(c, w.vel_bits) for c in a)
     d2h = h2d
 
