@@ -302,12 +302,56 @@ def run_gb300(args):
         "stage_launches": {k: v[1] for k, v in stages.items()},
         "clocks": sampler.summary(),
     }
+    if not args.no_adjoint:
+        result["adjoint"] = adjoint_ratio(args.adjoint_workload)
     if rank == 0 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline(w, 1.0 / 64)
     if world > 1:
         dist.destroy_process_group()
     pm.close()
     return result if rank == 0 else None
+
+
+def adjoint_ratio(workload: str, steps: int = 10, every: int = 2, reps: int = 3):
+    """Adjoint/forward time of the differentiable trajectory: `steps` PM steps of
+    a single-mesh workload from x0 = q + psi, loss sum (rho_K - target)^2, its
+    gradient in psi by the reverse mode with checkpoints every `every` steps."""
+    import numpy as np
+    import torch
+
+    from paper_1611_01545_gb300 import PM
+    from paper_1611_01545_gb300.diff import trajectory_loss
+    from synth import make_workload
+
+    w = make_workload(workload)
+    cfg = dict(w.config(), deposit_mode=1)
+    pm = PM(cfg)
+    q = torch.from_numpy(w.x[0]).cuda()
+    rng = np.random.default_rng(9)
+    psi = torch.from_numpy((rng.standard_normal(w.x[0].shape) * 0.2).astype(np.float32)).cuda()
+    xnu = torch.from_numpy(w.x[1]).cuda()
+    vnu = torch.from_numpy(w.v[1]).cuda()
+    target = torch.zeros((w.n_fine,) * 3, device="cuda")
+    fwd, bwd = [], []
+    for r in range(reps + 1):
+        p = psi.clone().requires_grad_(True)
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        torch.cuda.synchronize()
+        e0.record()
+        L = trajectory_loss(pm, p, q, xnu, vnu, target, 0.0, steps, every, 1.0, 1.0)
+        e1.record()
+        L.backward()
+        e2.record()
+        torch.cuda.synchronize()
+        if r:
+            fwd.append(e0.elapsed_time(e1))
+            bwd.append(e1.elapsed_time(e2))
+    pm.check()
+    pm.close()
+    f, b = statistics.median(fwd), statistics.median(bwd)
+    return {"workload": workload, "particles": sum(w.counts), "steps": steps, "checkpoint_every": every,
+            "forward_ms": round(f, 3), "adjoint_ms": round(b, 3), "ratio": round(b / f, 3),
+            "note": "adjoint time includes the checkpointed recompute of each segment"}
 
 
 def cpu_baseline(workload, frac: float = 1.0 / 64):
@@ -406,6 +450,8 @@ def main():
     p.add_argument("--workload", default="two_level256")
     p.add_argument("--tile-batch", type=int, default=0)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-adjoint", action="store_true")
+    p.add_argument("--adjoint-workload", default="diff128")
     args = p.parse_args()
     res = run_reference(args) if args.impl == "reference" else run_gb300(args)
     if res is not None:

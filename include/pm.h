@@ -122,6 +122,13 @@ typedef struct pm_codes {
   float* vmax;
 } pm_codes_t;
 
+/* Uncompressed particles of one species in device memory: x, v [n][3]. */
+typedef struct pm_particles {
+  int64_t n;
+  float* x;
+  float* v;
+} pm_particles_t;
+
 /* Host-memory twin of pm_codes_t for pm_step_host and the serializer: same
  * fields and layouts, every pointer is host memory (pinned for speed). */
 typedef pm_codes_t pm_host_codes_t;
@@ -244,6 +251,34 @@ int pm_step(pm_handle_t* h, const pm_codes_t in[2], pm_codes_t out[2], double c_
  * the handle (allocated on first use).  Returns the device status too. */
 int pm_step_host(pm_handle_t* h, const pm_host_codes_t in[2], pm_host_codes_t out[2], double c_kick,
                  double c_drift, void* stream);
+
+/* Reverse mode of the single-mesh step (coarse_ratio == 1), for gradients of
+ * losses of the final positions or density with respect to initial
+ * conditions.  The paper has no adjoint; these are the chain rule of the
+ * forward step above (Sec. 2.1 Eqs. 1-3, Sec. 2.3 CIC, kick-drift).  Two-level
+ * handles return PM_ERR_CONFIG.
+ *
+ * pm_deposit_adjoint:     lam_x[p] += m_s sum_c lam_rho(c) grad_x W(x_p - c)
+ *                          (W = CIC weight; lam_rho [n_fine^3] float32).
+ * pm_solve_adjoint:       lam_rho = A^T lam_acc for a = A rho of pm_solve
+ *                          (kernel conj(i k_d g)); lam_acc [3][n_fine^3].
+ * pm_interpolate_adjoint: the reverse of interpolate + kick + drift for one
+ *                          species: lam_v += c_drift lam_x; lam_a = c_kick lam_v;
+ *                          lam_acc(c) += lam_a W(x - c) (atomics, zero it
+ *                          first); lam_x += sum_c (lam_a . acc(c)) grad W.
+ * pm_step_adjoint:        one whole reverse step for both species: recomputes
+ *                          the step's acceleration at the pre-step positions
+ *                          state[s].x (cfg.deposit_mode as in the forward; use
+ *                          the fixed-point mode for a bit-exact recompute), then
+ *                          maps lam[s] = (dL/dx', dL/dv') after the step to
+ *                          (dL/dx, dL/dv) before it, in place. */
+int pm_deposit_adjoint(pm_handle_t* h, int species, const float* x, int64_t n, const float* lam_rho, float* lam_x,
+                       void* stream);
+int pm_solve_adjoint(pm_handle_t* h, const float* lam_acc, float* lam_rho, void* stream);
+int pm_interpolate_adjoint(pm_handle_t* h, const float* x, int64_t n, const float* acc_fine, double c_kick,
+                           double c_drift, float* lam_x, float* lam_v, float* lam_acc, void* stream);
+int pm_step_adjoint(pm_handle_t* h, const pm_particles_t state[2], pm_particles_t lam[2], double c_kick,
+                    double c_drift, void* stream);
 
 /* Synchronises `stream`, returns and clears the sticky device status
  * (PM_OK, PM_ERR_CORRUPT, PM_ERR_OVERFLOW, PM_ERR_RANGE, PM_ERR_TIMEOUT). */

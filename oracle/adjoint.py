@@ -132,16 +132,24 @@ def gradient(xs, vs, cfg: Dict, c_kick: float, c_drift: float, steps: int, targe
     lam_x: List[np.ndarray] = [m * cic_grad_gather(g_rho, xi, n) for xi, m in zip(xK, cfg["mass"])]
     lam_v: List[np.ndarray] = [np.zeros_like(xi) for xi in xK]
     for k in range(steps - 1, -1, -1):
-        x, v = states[k]
-        rho = density(x, cfg)
-        a_mesh = solve.accel_periodic(rho, 1.0, cfg["G"])
-        lam_A = np.zeros((3, n, n, n))
-        for s in range(len(x)):
-            lam_v[s] = lam_v[s] + c_drift * lam_x[s]
-            lam_a = c_kick * lam_v[s]
-            lam_A += cic_deposit_vector(lam_a, x[s], n)
-            lam_x[s] = lam_x[s] + interp_grad(a_mesh, lam_a, x[s], n)
-        lam_rho = accel_periodic_adjoint(lam_A, 1.0, cfg["G"])
-        for s in range(len(x)):
-            lam_x[s] = lam_x[s] + cfg["mass"][s] * cic_grad_gather(lam_rho, x[s], n)
+        lam_x, lam_v = reverse_step(states[k][0], cfg, lam_x, lam_v, c_kick, c_drift)
+    return lam_x, lam_v
+
+
+def reverse_step(x, cfg: Dict, lam_x, lam_v, c_kick: float, c_drift: float):
+    """Map (dL/dx', dL/dv') after one step to (dL/dx, dL/dv) before it, given
+    the pre-step positions x of every species."""
+    n = cfg["n_fine"]
+    a_mesh = solve.accel_periodic(density(x, cfg), 1.0, cfg["G"])
+    lam_x = [np.asarray(a, np.float64).copy() for a in lam_x]
+    lam_v = [np.asarray(a, np.float64).copy() for a in lam_v]
+    lam_A = np.zeros((3, n, n, n))
+    for s in range(len(x)):
+        lam_v[s] = lam_v[s] + c_drift * lam_x[s]
+        lam_a = c_kick * lam_v[s]
+        lam_A += cic_deposit_vector(lam_a, x[s], n)
+        lam_x[s] = lam_x[s] + interp_grad(a_mesh, lam_a, x[s], n)
+    lam_rho = accel_periodic_adjoint(lam_A, 1.0, cfg["G"])
+    for s in range(len(x)):
+        lam_x[s] = lam_x[s] + cfg["mass"][s] * cic_grad_gather(lam_rho, x[s], n)
     return lam_x, lam_v

@@ -32,6 +32,10 @@ class pm_config_t(ctypes.Structure):
                 ("r_cut", ctypes.c_double)]
 
 
+class pm_particles_t(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("x", ctypes.c_void_p), ("v", ctypes.c_void_p)]
+
+
 class pm_codes_t(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("cnt", ctypes.c_void_p), ("esc", ctypes.c_void_p),
                 ("esc_cap", ctypes.c_int64), ("n_esc", ctypes.c_void_p), ("pos", ctypes.c_void_p),
@@ -42,7 +46,8 @@ EXPORTED = ["pm_init", "pm_destroy", "pm_geometry", "pm_decompress", "pm_compres
             "pm_deposit_fixed", "pm_deposit_codes", "pm_tile_density", "pm_solve", "pm_solve_fixed", "pm_interpolate",
             "pm_kick_drift", "pm_step", "pm_step_host", "pm_check", "pm_last_error", "pm_set_timing",
             "pm_stage_times", "pm_serialize", "pm_deserialize", "pm_error_string", "pm_launch_count",
-            "pm_decompress_noalloc"]
+            "pm_decompress_noalloc", "pm_deposit_adjoint", "pm_solve_adjoint", "pm_interpolate_adjoint",
+            "pm_step_adjoint"]
 
 _P = ctypes.c_void_p
 _I64 = ctypes.c_int64
@@ -75,6 +80,11 @@ _PROTOS = {
                                       ctypes.POINTER(pm_codes_t)]),
     "pm_error_string": (ctypes.c_char_p, [ctypes.c_int]),
     "pm_launch_count": (ctypes.c_int64, []),
+    "pm_deposit_adjoint": (ctypes.c_int, [_P, ctypes.c_int, _P, _I64, _P, _P, _P]),
+    "pm_solve_adjoint": (ctypes.c_int, [_P, _P, _P, _P]),
+    "pm_interpolate_adjoint": (ctypes.c_int, [_P, _P, _I64, _P, _D, _D, _P, _P, _P, _P]),
+    "pm_step_adjoint": (ctypes.c_int, [_P, ctypes.POINTER(pm_particles_t), ctypes.POINTER(pm_particles_t), _D, _D,
+                                       _P]),
     "pm_decompress_noalloc": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                              ctypes.POINTER(pm_codes_t), _P, _P, _P]),
 }

@@ -46,6 +46,9 @@ struct pm_handle {
   float* tv = nullptr;
   std::vector<void*> allocs;
   Timer timer;
+  // adjoint workspace (single mesh): lam_acc [3][n^3], component spectra [3][N][N][N/2+1]
+  float* lam_acc = nullptr;
+  float2* adj_spec = nullptr;
   // staging for pm_step_host
   pm_codes_t stage_in[2]{}, stage_out[2]{};
   bool staged = false;
@@ -412,6 +415,10 @@ int pm_init(const pm_config_t* cfg, pm_handle_t** out) {
     if (cudaMemset(h->status, 0, 4) != cudaSuccess) rc = fail(h, PM_ERR_CUDA, "memset");
     if (cudaDeviceSynchronize() != cudaSuccess) rc = fail(h, PM_ERR_CUDA, "init sync");
   }
+  if (!g.two) {
+    A(&h->lam_acc, 3 * nf3 * 4);
+    A(&h->adj_spec, (size_t)3 * g.nf * g.nf * (g.nf / 2 + 1) * sizeof(float2));
+  }
   h->blk_dep = choose_blk(g, fixed, true);
   h->blk_ikd = choose_blk(g, fixed, false);
   if (rc != PM_OK) {
@@ -605,6 +612,66 @@ int pm_step(pm_handle_t* h, const pm_codes_t in[2], pm_codes_t out[2], double c_
     CK(h, launch_ikd_scatter(in[0].n, in[1].n, h->off[0], h->off[1], h->geo, h->blk_ikd, h->counts[0], h->counts[1],
                              h->newoff[0], h->newoff[1], o0, o1, h->tkey, h->tpos, h->tv, h->status, st));
   }
+  return PM_OK;
+}
+
+int pm_deposit_adjoint(pm_handle_t* h, int species, const float* x, int64_t n, const float* lam_rho, float* lam_x,
+                       void* stream) {
+  if (!h || (n && (!x || !lam_x)) || !lam_rho) return fail(h, PM_ERR_ARG, "null argument");
+  if (int r = check_species(h, species)) return r;
+  if (h->gm.two) return fail(h, PM_ERR_CONFIG, "adjoints are implemented for the single periodic mesh");
+  CK(h, launch_adj_deposit(x, n, (float)h->cfg.mass[species], h->gm.nf, lam_rho, lam_x, (cudaStream_t)stream));
+  return PM_OK;
+}
+
+int pm_solve_adjoint(pm_handle_t* h, const float* lam_acc, float* lam_rho, void* stream) {
+  if (!h || !lam_acc || !lam_rho) return fail(h, PM_ERR_ARG, "null argument");
+  if (h->gm.two) return fail(h, PM_ERR_CONFIG, "adjoints are implemented for the single periodic mesh");
+  CK(h, solve_adjoint_launch(h->plan_mesh, lam_acc, lam_rho, h->adj_spec, (cudaStream_t)stream));
+  return PM_OK;
+}
+
+int pm_interpolate_adjoint(pm_handle_t* h, const float* x, int64_t n, const float* acc_fine, double c_kick,
+                           double c_drift, float* lam_x, float* lam_v, float* lam_acc, void* stream) {
+  if (!h || (n && (!x || !lam_x || !lam_v)) || !acc_fine || !lam_acc) return fail(h, PM_ERR_ARG, "null argument");
+  if (h->gm.two) return fail(h, PM_ERR_CONFIG, "adjoints are implemented for the single periodic mesh");
+  CK(h, launch_adj_interp(x, n, h->gm.nf, acc_fine, (float)c_kick, (float)c_drift, lam_x, lam_v, lam_acc,
+                          (cudaStream_t)stream));
+  return PM_OK;
+}
+
+int pm_step_adjoint(pm_handle_t* h, const pm_particles_t state[2], pm_particles_t lam[2], double c_kick,
+                    double c_drift, void* stream) {
+  if (!h || !state || !lam) return fail(h, PM_ERR_ARG, "null argument");
+  if (h->gm.two) return fail(h, PM_ERR_CONFIG, "adjoints are implemented for the single periodic mesh");
+  for (int s = 0; s < 2; ++s)
+    if (state[s].n != lam[s].n || (state[s].n && (!state[s].x || !lam[s].x || !lam[s].v)))
+      return fail(h, PM_ERR_ARG, "state and adjoint particle arrays disagree");
+  cudaStream_t st = (cudaStream_t)stream;
+  const Geom& g = h->gm;
+  const bool fixed = h->cfg.deposit_mode == 1;
+  const size_t nf3 = (size_t)g.nfine3();
+  // recompute the step's acceleration mesh at the pre-step positions
+  if (fixed) {
+    CK(h, cudaMemsetAsync(h->rho_f_fix, 0, nf3 * 8, st));
+    for (int s = 0; s < 2; ++s) {
+      long long M = llrint(h->cfg.mass[s] * 4294967296.0);
+      CK(h, launch_deposit_fixed(state[s].x, state[s].n, M, h->geo, nullptr, h->rho_f_fix, st));
+    }
+    CK(h, solve_launch(h->plan_mesh, h->rho_f_fix, true, h->acc_f, st, nullptr));
+  } else {
+    CK(h, cudaMemsetAsync(h->rho_f, 0, nf3 * 4, st));
+    for (int s = 0; s < 2; ++s)
+      CK(h, launch_deposit(state[s].x, state[s].n, (float)h->cfg.mass[s], h->geo, nullptr, h->rho_f, st));
+    CK(h, solve_launch(h->plan_mesh, h->rho_f, false, h->acc_f, st, nullptr));
+  }
+  CK(h, cudaMemsetAsync(h->lam_acc, 0, 3 * nf3 * 4, st));
+  for (int s = 0; s < 2; ++s)
+    CK(h, launch_adj_interp(state[s].x, state[s].n, g.nf, h->acc_f, (float)c_kick, (float)c_drift, lam[s].x, lam[s].v,
+                            h->lam_acc, st));
+  CK(h, solve_adjoint_launch(h->plan_mesh, h->lam_acc, h->rho_f, h->adj_spec, st));   // rho_f holds lam_rho
+  for (int s = 0; s < 2; ++s)
+    CK(h, launch_adj_deposit(state[s].x, state[s].n, (float)h->cfg.mass[s], g.nf, h->rho_f, lam[s].x, st));
   return PM_OK;
 }
 

@@ -70,5 +70,9 @@ cudaError_t launch_ikd_scatter(int64_t n0, int64_t n1, const int64_t* off0, cons
                                const int64_t* newoff1, const PCodesOut& o0, const PCodesOut& o1, const uint32_t* tkey,
                                const uint32_t* tpos, const float* tv, int* status, cudaStream_t st);
 cudaError_t launch_set_vmax(const uint32_t* vmax_bits, float* out, cudaStream_t st);
+cudaError_t launch_adj_deposit(const float* x, int64_t n, float m, int nf, const float* lam_rho, float* lam_x,
+                               cudaStream_t st);
+cudaError_t launch_adj_interp(const float* x, int64_t n, int nf, const float* acc, float ck, float cd, float* lam_x,
+                              float* lam_v, float* lam_A, cudaStream_t st);
 
 }  // namespace pm

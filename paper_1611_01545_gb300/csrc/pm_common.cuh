@@ -50,6 +50,10 @@ void note_launches(int k);
 // Launch helpers implemented in solve.cu.
 cudaError_t solve_launch(const SolvePlan& p, const void* src, bool src_fixed, float* dst, cudaStream_t st,
                          struct Timer* timer);
+// Transpose of the periodic-mesh solve (adjoint): lam_rho = A^T lam_acc; spec3comp holds
+// the three component spectra [3][N][N][N/2+1].
+cudaError_t solve_adjoint_launch(const SolvePlan& p, const float* lam_acc, float* lam_rho, float2* spec3comp,
+                                 cudaStream_t st);
 cudaError_t tile_window_launch(const SolvePlan& p, const float* src, int64_t tile, float* out, cudaStream_t st);
 
 // Per-launch CUDA-event timing, accumulated by kind.

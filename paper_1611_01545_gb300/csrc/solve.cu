@@ -40,6 +40,7 @@ struct SolveArgs {
   const float* kern;
   const float2* tw;
   float* dst;
+  int comp_mode;   // pass A only: blockIdx.y selects component pb of a [3][n^3] source at origin 0
 };
 
 __device__ __forceinline__ int pmod(int a, int n) {
@@ -80,12 +81,17 @@ __global__ void __launch_bounds__(SolveCfg<N>::threads) k_solve_a(SolveArgs a) {
   int ox, oy, oz;
   problem_origin(a, a.p0 + pb, ox, oy, oz);
   const int n = a.src_n;
+  const void* src = a.src;
+  if (a.comp_mode) {
+    ox = oy = oz = 0;
+    src = static_cast<const float*>(a.src) + (size_t)pb * n * n * n;
+  }
   // origins lie in (-n, n) and N <= n, so one conditional wrap suffices
   const int gz = wrap1(oz + z, n);
   PM_ROWS(y, N) {
     const int64_t rowbase = ((int64_t)gz * n + wrap1(oy + y, n)) * n;
     float* w = reinterpret_cast<float*>(W + (y >> 1) * N) + (y & 1);
-    PM_COLS(x, N) w[2 * x] = src_value<FIXED>(a.src, rowbase + wrap1(ox + x, n));
+    PM_COLS(x, N) w[2 * x] = src_value<FIXED>(src, rowbase + wrap1(ox + x, n));
   }
   __syncthreads();
   fft_fwd<N, N / 2, N, 1>(W, tw);
@@ -167,6 +173,51 @@ __global__ void __launch_bounds__(PassB<N>::threads) k_solve_b(SolveArgs a) {
   }
 }
 
+// Transpose of the solve for one periodic mesh (the adjoint of a_d = K_d * rho):
+// the three component spectra (pass A with comp_mode) are z-transformed, each
+// multiplied by the conjugate kernel conj(i K_d) = -i K_d and summed, and the
+// sum is inverse z-transformed into component slot 0 of spec3; pass C then
+// gives the scalar result.
+template <int N>
+__global__ void __launch_bounds__(PassB<N>::threads) k_solve_b_adj(SolveArgs a) {
+  constexpr int NH = PassB<N>::NH, KC = PassB<N>::KC;
+  extern __shared__ float2 sm[];
+  float2* tw = sm;
+  float2* F = sm + N;             // [z][KC]
+  float2* G = F + N * KC;         // [z][KC]
+  for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = a.tw[i];
+  const int ys = blockIdx.x, half = blockIdx.y;
+  const int kx0 = half * KC;
+  const int ncol = (NH - kx0) < KC ? (NH - kx0) : KC;
+  const size_t kstride = (size_t)N * N * NH;
+  for (int i = threadIdx.x; i < N * KC; i += blockDim.x) G[i] = make_float2(0.f, 0.f);
+  for (int d = 0; d < 3; ++d) {
+    const float2* in = a.spec + (size_t)d * N * N * NH + (size_t)ys * NH + kx0;
+    for (int i = threadIdx.x; i < N * KC; i += blockDim.x) {
+      const int z = i / KC, c = i - z * KC;
+      F[i] = c < ncol ? in[(size_t)z * N * NH + c] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    fft_fwd<N, KC, 1, KC>(F, tw);
+    const float* K = a.kern + d * kstride + (size_t)ys * NH + kx0;
+    for (int i = threadIdx.x; i < N * KC; i += blockDim.x) {
+      const int zs = i / KC, c = i - zs * KC;
+      if (c < ncol) {
+        const float k = __ldg(K + (size_t)zs * N * NH + c);
+        const float2 f = F[i];
+        G[i] = make_float2(G[i].x + f.y * k, G[i].y - f.x * k);   // += -i K f
+      }
+    }
+    __syncthreads();
+  }
+  fft_inv<N, KC, 1, KC>(G, tw);
+  float2* out = a.spec3 + (size_t)ys * NH + kx0;
+  for (int i = threadIdx.x; i < N * KC; i += blockDim.x) {
+    const int z = i / KC, c = i - z * KC;
+    if (c < ncol) out[(size_t)z * N * NH + c] = G[i];
+  }
+}
+
 template <int N>
 __global__ void __launch_bounds__(SolveCfg<N>::threads) k_solve_c(SolveArgs a) {
   constexpr int NH = SolveCfg<N>::NH;
@@ -241,7 +292,7 @@ static cudaError_t solve_n(const SolvePlan& p, const void* src, bool fixed, floa
   const int nprob = p.nts * p.nts * p.nts;
   for (int p0 = 0; p0 < nprob; p0 += p.batch) {
     int nb = (nprob - p0 < p.batch) ? (nprob - p0) : p.batch;
-    SolveArgs a{src, fixed ? 1 : 0, p.src_n, p.nts, p.t, p.b, p0, p.spec, p.spec3, p.kern, p.tw, dst};
+    SolveArgs a{src, fixed ? 1 : 0, p.src_n, p.nts, p.t, p.b, p0, p.spec, p.spec3, p.kern, p.tw, dst, 0};
     {
       TimedScope ts(tm, N == p.src_n && p.b == 0 ? "fft_a_mesh" : "fft_a_tiles", st);
       if (fixed) k_solve_a<N, true><<<dim3(N, nb), C::threads, C::smem_a, st>>>(a);
@@ -270,6 +321,36 @@ cudaError_t solve_launch(const SolvePlan& p, const void* src, bool fixed, float*
     case 64: return solve_n<64>(p, src, fixed, dst, st, tm);
     case 96: return solve_n<96>(p, src, fixed, dst, st, tm);
     case 128: return solve_n<128>(p, src, fixed, dst, st, tm);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <int N>
+static cudaError_t solve_adjoint_n(const SolvePlan& p, const float* lam_acc, float* lam_rho, float2* spec3comp,
+                                   cudaStream_t st) {
+  using C = SolveCfg<N>;
+  cudaFuncSetAttribute(k_solve_a<N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem_a);
+  cudaFuncSetAttribute(k_solve_b_adj<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sizeof(float2) * (N + 2 * (size_t)N * PassB<N>::KC)));
+  cudaFuncSetAttribute(k_solve_c<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem_a);
+  SolveArgs a{lam_acc, 0, p.src_n, 1, N, 0, 0, spec3comp, p.spec3, p.kern, p.tw, lam_rho, 1};
+  k_solve_a<N, false><<<dim3(N, 3), C::threads, C::smem_a, st>>>(a);
+  a.comp_mode = 0;
+  k_solve_b_adj<N><<<dim3(N, 2, 1), PassB<N>::threads, sizeof(float2) * (N + 2 * (size_t)N * PassB<N>::KC), st>>>(a);
+  k_solve_c<N><<<dim3(N, 1, 1), C::threads, C::smem_a, st>>>(a);
+  note_launches(3);
+  return cudaGetLastError();
+}
+
+cudaError_t solve_adjoint_launch(const SolvePlan& p, const float* lam_acc, float* lam_rho, float2* spec3comp,
+                                 cudaStream_t st) {
+  if (p.nts != 1 || p.b != 0 || p.t != p.N) return cudaErrorInvalidValue;
+  switch (p.N) {
+    case 16: return solve_adjoint_n<16>(p, lam_acc, lam_rho, spec3comp, st);
+    case 32: return solve_adjoint_n<32>(p, lam_acc, lam_rho, spec3comp, st);
+    case 48: return solve_adjoint_n<48>(p, lam_acc, lam_rho, spec3comp, st);
+    case 64: return solve_adjoint_n<64>(p, lam_acc, lam_rho, spec3comp, st);
+    case 96: return solve_adjoint_n<96>(p, lam_acc, lam_rho, spec3comp, st);
+    case 128: return solve_adjoint_n<128>(p, lam_acc, lam_rho, spec3comp, st);
     default: return cudaErrorInvalidValue;
   }
 }

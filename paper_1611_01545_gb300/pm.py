@@ -13,7 +13,7 @@ from typing import Dict, Optional, Sequence, Tuple
 import torch
 
 from . import _lib
-from ._lib import pm_codes_t, pm_config_t
+from ._lib import pm_codes_t, pm_config_t, pm_particles_t
 
 
 class PMError(RuntimeError):
@@ -203,6 +203,41 @@ class PM:
         arr_in = (pm_codes_t * 2)(codes_in[0].struct(), codes_in[1].struct())
         arr_out = (pm_codes_t * 2)(codes_out[0].struct(), codes_out[1].struct())
         self._err(self.lib.pm_step_host(self.h, arr_in, arr_out, c_kick, c_drift, _stream(stream)))
+
+    # ---- uncompressed step and its reverse mode (single periodic mesh) -------
+    def density(self, xs: Sequence[torch.Tensor], fixed: bool, stream=None):
+        """Deposit both species; returns the mesh (int64 in 2^-32 mass units if fixed)."""
+        rc, rf = self.zeros_meshes(fixed=fixed)
+        for s, x in enumerate(xs):
+            (self.deposit_fixed if fixed else self.deposit)(s, x, rc, rf, stream)
+        return rc, rf
+
+    def step_plain(self, xs: Sequence[torch.Tensor], vs: Sequence[torch.Tensor], c_kick: float, c_drift: float,
+                   fixed: bool = True, stream=None):
+        """One uncompressed step in place: deposit, solve, interpolate + kick + drift."""
+        rc, rf = self.density(xs, fixed, stream)
+        ac, af = self.zeros_acc()
+        self.solve(rc, rf, ac, af, stream)
+        for x, v in zip(xs, vs):
+            self.kick_drift(x, v, ac, af, c_kick, c_drift, stream)
+
+    def deposit_adjoint(self, species: int, x: torch.Tensor, lam_rho: torch.Tensor, lam_x: torch.Tensor, stream=None):
+        self._err(self.lib.pm_deposit_adjoint(self.h, species, _ptr(x), x.shape[0], _ptr(lam_rho), _ptr(lam_x),
+                                              _stream(stream)))
+
+    def solve_adjoint(self, lam_acc: torch.Tensor, lam_rho: torch.Tensor, stream=None):
+        self._err(self.lib.pm_solve_adjoint(self.h, _ptr(lam_acc), _ptr(lam_rho), _stream(stream)))
+
+    def interpolate_adjoint(self, x, acc, c_kick, c_drift, lam_x, lam_v, lam_acc, stream=None):
+        self._err(self.lib.pm_interpolate_adjoint(self.h, _ptr(x), x.shape[0], _ptr(acc), c_kick, c_drift,
+                                                  _ptr(lam_x), _ptr(lam_v), _ptr(lam_acc), _stream(stream)))
+
+    def step_adjoint(self, xs: Sequence[torch.Tensor], lam_x: Sequence[torch.Tensor], lam_v: Sequence[torch.Tensor],
+                     c_kick: float, c_drift: float, stream=None):
+        st = (pm_particles_t * 2)(*[pm_particles_t(x.shape[0], x.data_ptr(), 0) for x in xs])
+        lam = (pm_particles_t * 2)(*[pm_particles_t(a.shape[0], a.data_ptr(), b.data_ptr())
+                                     for a, b in zip(lam_x, lam_v)])
+        self._err(self.lib.pm_step_adjoint(self.h, st, lam, c_kick, c_drift, _stream(stream)))
 
     def set_timing(self, on: bool):
         self._err(self.lib.pm_set_timing(self.h, 1 if on else 0))

@@ -1,0 +1,94 @@
+"""GPU reverse mode of the single-mesh step against the float64 oracle
+adjoint: the transposed solve, one reverse step, and the gradient of a
+final-density loss through a checkpointed multi-step trajectory."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import adjoint, solve
+from synth import make_workload
+from tests.helpers import rel_rms
+
+pytestmark = pytest.mark.gpu
+
+ADJ_TOL = 1e-3   # float32 adjoint vs float64 oracle, relative RMS
+
+
+def _pm(cfg):
+    from paper_1611_01545_gb300 import PM
+    return PM(cfg)
+
+
+def _cfg(n=32, counts=(512, 4096)):
+    return dict(n_fine=n, coarse_ratio=1, tile=n, buffer=0, cmp_ratio=4, vel_bits=16, G=1 / (4 * np.pi),
+                mass=(8.0, 0.04), count=counts, deposit_mode=1)
+
+
+def test_solve_adjoint_is_transpose_gpu():
+    pm = _pm(_cfg(32))
+    g = torch.Generator(device="cuda").manual_seed(3)
+    rho = torch.randn((32,) * 3, device="cuda", generator=g)
+    lam = torch.randn((3,) + (32,) * 3, device="cuda", generator=g)
+    _, af = pm.zeros_acc()
+    pm.solve(None, rho, None, af)
+    lr = torch.empty_like(rho)
+    pm.solve_adjoint(lam, lr)
+    pm.check()
+    lhs = float((af.double() * lam.double()).sum())
+    rhs = float((rho.double() * lr.double()).sum())
+    assert abs(lhs - rhs) <= 1e-5 * abs(lhs)
+    ref = adjoint.accel_periodic_adjoint(lam.cpu().numpy().astype(np.float64), 1.0, 1 / (4 * np.pi))
+    assert rel_rms(lr.cpu().numpy(), ref) < 1e-5
+
+
+def _particles(seed, n, n0, n1):
+    rng = np.random.default_rng(seed)
+    xs = [(rng.random((k, 3)) * n).astype(np.float32) for k in (n0, n1)]
+    vs = [(rng.standard_normal((k, 3)) * 0.3).astype(np.float32) for k in (n0, n1)]
+    return xs, vs
+
+
+def test_one_reverse_step_matches_oracle():
+    n = 32
+    cfg = _cfg(n)
+    pm = _pm(cfg)
+    xs, _ = _particles(5, n, 512, 4096)
+    rng = np.random.default_rng(6)
+    lx = [rng.standard_normal(x.shape).astype(np.float32) for x in xs]
+    lv = [rng.standard_normal(x.shape).astype(np.float32) for x in xs]
+    gx = [torch.from_numpy(a).cuda() for a in lx]
+    gv = [torch.from_numpy(a).cuda() for a in lv]
+    pm.step_adjoint([torch.from_numpy(x).cuda() for x in xs], gx, gv, 0.5, 0.5)
+    pm.check()
+    rx, rv = adjoint.reverse_step([x.astype(np.float64) for x in xs], cfg, lx, lv, 0.5, 0.5)
+    for s in range(2):
+        assert rel_rms(gv[s].cpu().numpy(), rv[s]) < ADJ_TOL
+        assert rel_rms(gx[s].cpu().numpy(), rx[s]) < ADJ_TOL, (s, rel_rms(gx[s].cpu().numpy(), rx[s]))
+
+
+@pytest.mark.parametrize("beta", [0.0, 0.3])
+def test_trajectory_gradient_matches_oracle(beta):
+    from paper_1611_01545_gb300.diff import trajectory_loss
+    w = make_workload("diff128", n_cdm=8, n_nu=16)
+    n = 32
+    w.x = [np.mod(x * (n / 128.0), n).astype(np.float32) for x in w.x]
+    cfg = _cfg(n, counts=(8 ** 3, 16 ** 3))
+    pm = _pm(cfg)
+    rng = np.random.default_rng(7)
+    q = w.x[0]
+    psi = (rng.standard_normal(q.shape) * 0.3).astype(np.float32)
+    vnu = (w.v[1] * 0.2).astype(np.float32)
+    target = (rng.random((n, n, n)) * 0.02).astype(np.float32)
+    steps, every, ck, cd = 4, 2, 0.5, 0.5
+    psi_t = torch.from_numpy(psi).cuda().requires_grad_(True)
+    L = trajectory_loss(pm, psi_t, torch.from_numpy(q).cuda(), torch.from_numpy(w.x[1]).cuda(),
+                        torch.from_numpy(vnu).cuda(), torch.from_numpy(target).cuda(), beta, steps, every, ck, cd)
+    L.backward()
+    pm.check()
+    x0 = [np.mod(q.astype(np.float64) + psi, n), w.x[1].astype(np.float64)]
+    v0 = [beta * psi.astype(np.float64), vnu.astype(np.float64)]
+    lx, lv = adjoint.gradient(x0, v0, cfg, ck, cd, steps, target.astype(np.float64))
+    ref_loss = adjoint.loss(adjoint.forward(x0, v0, cfg, ck, cd, steps)[-1][0], cfg, target)
+    assert abs(float(L) - ref_loss) <= 1e-4 * ref_loss
+    ref_grad = lx[0] + beta * lv[0]
+    assert rel_rms(psi_t.grad.cpu().numpy(), ref_grad) < ADJ_TOL
