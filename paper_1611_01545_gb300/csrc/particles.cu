@@ -42,6 +42,7 @@ __device__ __forceinline__ V2 warp_incl(V2 v) {
 // Exclusive block scan of one V2 per thread; returns the exclusive prefix and the block total.
 __device__ V2 block_excl(V2 v, V2* total) {
   __shared__ V2 warp_sums[32];
+  __shared__ V2 block_total;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   V2 inc = warp_incl(v);
   if (lane == 31) warp_sums[wid] = inc;
@@ -51,11 +52,11 @@ __device__ V2 block_excl(V2 v, V2* total) {
     V2 w = lane < nw ? warp_sums[lane] : V2{0, 0};
     V2 wi = warp_incl(w);
     if (lane < nw) warp_sums[lane] = V2{wi.a - w.a, wi.b - w.b};
-    if (lane == nw - 1) warp_sums[31] = wi;
+    if (lane == nw - 1) block_total = wi;
   }
   __syncthreads();
   V2 res = v2add(warp_sums[wid], V2{inc.a - v.a, inc.b - v.b});
-  *total = warp_sums[31];
+  *total = block_total;
   __syncthreads();
   return res;
 }

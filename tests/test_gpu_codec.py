@@ -145,3 +145,24 @@ def test_out_of_range_position_reported():
     with pytest.raises(PMError) as e:
         pm.check()
     assert e.value.code == 6
+
+
+def test_compress_parity_large_mesh():
+    # 128^3 compression cells: the count scan needs more than 992 partial sums,
+    # so the single-block scan of the partials runs all 32 of its warps.
+    rng = np.random.default_rng(43)
+    x = (rng.random((300000, 3)) * 512).astype(np.float32)
+    x[x >= 512] = 0
+    x[-1000:] = np.float32(511.5)              # the last cell, escaped
+    v = rng.standard_normal((300000, 3)).astype(np.float32)
+    pm = _pm(_cfg(512))
+    got = pm.compress(0, torch.from_numpy(x).cuda(), torch.from_numpy(v).cuda())
+    pm.check()
+    ref = codec.compress(x, v, 512, 128, 16)
+    g = oracle_codes_from_lib(got, 128, 16)
+    np.testing.assert_array_equal(g.cnt, ref.cnt)
+    np.testing.assert_array_equal(g.esc_count, ref.esc_count)
+    np.testing.assert_array_equal(records(g), records(ref))
+    xd, _ = pm.decompress(0, got)
+    pm.check()
+    np.testing.assert_array_equal(xd.cpu().numpy(), codec.decompress(g, 512)[0])
