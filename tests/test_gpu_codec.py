@@ -155,7 +155,7 @@ def test_compress_parity_large_mesh():
     x[x >= 512] = 0
     x[-1000:] = np.float32(511.5)              # the last cell, escaped
     v = rng.standard_normal((300000, 3)).astype(np.float32)
-    pm = _pm(_cfg(512))
+    pm = _pm(_cfg(512, coarse_ratio=4, tile=64, buffer=16, r_cut=14.0, r_split=14.0 / 4.5))
     got = pm.compress(0, torch.from_numpy(x).cuda(), torch.from_numpy(v).cuda())
     pm.check()
     ref = codec.compress(x, v, 512, 128, 16)
