@@ -188,6 +188,47 @@ def codes_bytes(c, vel_bits):
     return c.cnt.numel() + c.esc.numel() * 4 + 4 + c.n * 4 * (1 + vb) + 4
 
 
+def timed_loop(torch, stream, fn, steps: int) -> float:
+    """Milliseconds of `steps` calls of fn, CUDA events on the launching stream."""
+    fn()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def plain_step_ms(pm, w, codes, spare, torch, stream, steps: int) -> float:
+    """The plain form of one step, one library call per stage: decompress each
+    species, deposit (global float atomics), coarse + tile solve, interpolate +
+    kick + drift, compress.  Returns milliseconds per step."""
+    a, b = list(codes), list(spare)
+    ac, af = pm.zeros_acc()
+    rc, rf = pm.zeros_meshes()
+
+    def one():
+        nonlocal a, b
+        xv = [pm.decompress(s, a[s]) for s in range(2)]
+        rf.zero_()
+        if rc is not None:
+            rc.zero_()
+        for s in range(2):
+            pm.deposit(s, xv[s][0], rc, rf)
+        pm.solve(rc, rf, ac, af)
+        for s in range(2):
+            pm.kick_drift(xv[s][0], xv[s][1], ac, af, 1.0, 1.0)
+            pm.compress(s, xv[s][0], xv[s][1], out=b[s])
+        a, b = b, a
+
+    ms = timed_loop(torch, stream, one, steps) / steps
+    pm.check()
+    return ms
+
+
 def run_gb300(args):
     import torch
     import torch.distributed as dist
@@ -209,17 +250,29 @@ def run_gb300(args):
     lib = _lib.load()
     stream = torch.cuda.current_stream()
     a, b = codes, spare
+    # every timed region below starts from this state, so each one measures
+    # the same steps of the same evolving particle distribution
+    initial = [c.clone() for c in codes]
+
+    def reset():
+        nonlocal a, b
+        a, b = codes, spare
+        for s in range(2):
+            a[s].copy_(initial[s])
 
     def one_step():
         nonlocal a, b
         pm.step(a, b, 1.0, 1.0)
         a, b = b, a
 
-    for _ in range(args.warmup):
+    # headline: the step replayed from captured CUDA graphs (one per ping-pong direction)
+    pm.set_graphs(True)
+    for _ in range(max(args.warmup, 2)):
         one_step()
     pm.check()
-    # timed region: per-kernel CUDA events live, device time by events around the loop
-    pm.set_timing(True)
+    reset()
+    for _ in range(args.warmup):
+        one_step()
     sampler = ClockSampler(local)
     sampler.start()
     time.sleep(0.3)
@@ -240,14 +293,38 @@ def run_gb300(args):
     sampler.stop()
     ms = e0.elapsed_time(e1)
     pm.check()
-    stages = pm.stage_times()
-    pm.set_timing(False)
     value, worst_s = job_rate(ms / 1e3, n_total * args.steps, world, "cuda", dist)
     ms_max = worst_s * 1e3
+    pm.set_graphs(False)
+
+    # the same kernels launched directly, then with CUDA events around every
+    # stage on the launching stream (per-kernel durations for the roofline)
+    reset()
+    for _ in range(args.warmup - 1):
+        one_step()
+    direct_ms = timed_loop(torch, stream, one_step, args.steps) / args.steps
+    reset()
+    for _ in range(args.warmup):
+        one_step()
+    pm.set_timing(True)
+    for _ in range(args.steps):
+        one_step()
+    torch.cuda.synchronize()
+    pm.check()
+    stages = pm.stage_times()
+    pm.set_timing(False)
+    reset()
+    for _ in range(args.warmup):
+        one_step()
+    plain_ms = plain_step_ms(pm, w, a, b, torch, stream, max(3, args.steps // 4))
+    reset()
+    for _ in range(args.warmup):
+        one_step()
 
     # end-to-end through the C ABI with host buffers (pinned), copies in the timed region
     hin = [c.to("cpu", pin=True) for c in a]
     hout = [c.to("cpu", pin=True) for c in b]
+    pm.set_graphs(True)
     pm.step_host(hin, hout, 1.0, 1.0)     # first call allocates the library's staging buffers
     torch.cuda.synchronize()
     if world > 1:
@@ -258,6 +335,7 @@ def run_gb300(args):
         pm.step_host(hin, hout, 1.0, 1.0)
         hin, hout = hout, hin
     e2e_s = time.perf_counter() - t0
+    pm.set_graphs(False)
     e2e_value, _ = job_rate(e2e_s, n_total * k_e2e, world, "cuda", dist)
     h2d = sum(codes_bytes(c, w.vel_bits) for c in a)
     d2h = h2d
@@ -298,6 +376,11 @@ def run_gb300(args):
                 "steps": k_e2e},
         "gpu_launches": int(launches),
         "roofline": roofline,
+        "launch_forms": {"graph_ms_per_step": round(ms_max / args.steps, 5),
+                         "direct_ms_per_step": round(direct_ms, 5),
+                         "plain_ms_per_step": round(plain_ms, 5),
+                         "plain_value": n_total * world / (plain_ms / 1e3),
+                         "plain": "one call per stage: decompress, deposit, solve, kick_drift, compress"},
         "stages_ms": {k: round(v[0], 5) for k, v in stages.items()},
         "stage_launches": {k: v[1] for k, v in stages.items()},
         "clocks": sampler.summary(),

@@ -293,6 +293,19 @@ int pm_last_error(const pm_handle_t* h, char* buf, size_t n);
 int pm_set_timing(pm_handle_t* h, int on);
 int pm_stage_times(pm_handle_t* h, float* ms, int cap, int* n_stages, char* names, size_t names_cap);
 
+/* Graph replay of pm_step (and pm_step_host): with on = 1, the first pm_step
+ * with a given set of codes descriptors (in[2], out[2], every field) and
+ * (c_kick, c_drift) captures its launch sequence into a CUDA graph on a
+ * library-owned stream; later calls with the same set launch that graph on
+ * the caller's stream.  Up to 8 graphs are kept (oldest evicted), so a
+ * ping-pong pair of codes buffers replays two graphs.  The graph holds the
+ * device pointers it was captured with: the caller must not free or reuse
+ * those buffers for other data while graphs are on (turn them off, or
+ * destroy the handle, first).  on = 0 synchronises the device and drops every
+ * graph.  Per-stage timing (pm_set_timing) bypasses the graphs.  No
+ * counterpart in the paper (launch batching only; results are identical). */
+int pm_set_graphs(pm_handle_t* h, int on);
+
 /* Serializer for the Sec. 2.4 byte stream (host memory, not stream-ordered):
  * header "PMNU", u32 version 1, u32 n_cmp, u32 vel_bits, u64 n, f32 v_max,
  * u32 0; then per cell the count byte (255 + int32 count if >= 255) and the

@@ -44,7 +44,7 @@ class pm_codes_t(ctypes.Structure):
 
 EXPORTED = ["pm_init", "pm_destroy", "pm_geometry", "pm_decompress", "pm_compress", "pm_deposit",
             "pm_deposit_fixed", "pm_deposit_codes", "pm_tile_density", "pm_solve", "pm_solve_fixed", "pm_interpolate",
-            "pm_kick_drift", "pm_step", "pm_step_host", "pm_check", "pm_last_error", "pm_set_timing",
+            "pm_kick_drift", "pm_step", "pm_step_host", "pm_check", "pm_last_error", "pm_set_timing", "pm_set_graphs",
             "pm_stage_times", "pm_serialize", "pm_deserialize", "pm_error_string", "pm_launch_count",
             "pm_decompress_noalloc", "pm_deposit_adjoint", "pm_solve_adjoint", "pm_interpolate_adjoint",
             "pm_step_adjoint"]
@@ -72,6 +72,7 @@ _PROTOS = {
     "pm_check": (ctypes.c_int, [_P, _P]),
     "pm_last_error": (ctypes.c_int, [_P, ctypes.c_char_p, ctypes.c_size_t]),
     "pm_set_timing": (ctypes.c_int, [_P, ctypes.c_int]),
+    "pm_set_graphs": (ctypes.c_int, [_P, ctypes.c_int]),
     "pm_stage_times": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_float), ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                       ctypes.c_char_p, ctypes.c_size_t]),
     "pm_serialize": (ctypes.c_int, [ctypes.POINTER(pm_codes_t), ctypes.c_int32, ctypes.c_int32, _P, ctypes.c_size_t,

@@ -42,8 +42,7 @@ struct pm_handle {
   // per-particle scratch of the fused step (stream order, both species)
   int64_t scratch_n = 0;
   uint32_t* tkey = nullptr;
-  uint32_t* tpos = nullptr;
-  float* tv = nullptr;
+  uint4* tpv = nullptr;      // per particle: new in-cell position code, v'_x, v'_y, v'_z (float bits)
   std::vector<void*> allocs;
   Timer timer;
   // adjoint workspace (single mesh): lam_acc [3][n^3], component spectra [3][N][N][N/2+1]
@@ -52,6 +51,16 @@ struct pm_handle {
   // staging for pm_step_host
   pm_codes_t stage_in[2]{}, stage_out[2]{};
   bool staged = false;
+  // pm_step replay: one instantiated graph per (codes descriptors, c_k, c_d)
+  struct StepGraph {
+    pm_codes_t in[2], out[2];
+    double ck, cd;
+    cudaGraphExec_t exec;
+    long long launches;
+  };
+  bool graphs = false;
+  cudaStream_t capture_stream = nullptr;
+  std::vector<StepGraph> step_graphs;
 };
 
 namespace {
@@ -375,8 +384,7 @@ int pm_init(const pm_config_t* cfg, pm_handle_t** out) {
   A(&h->vmax_bits, 2 * 4);
   h->scratch_n = c.count[0] + c.count[1];
   A(&h->tkey, (size_t)h->scratch_n * 4);
-  A(&h->tpos, (size_t)h->scratch_n * 4);
-  A(&h->tv, (size_t)h->scratch_n * 12);
+  A(&h->tpv, (size_t)h->scratch_n * 16);
   A(&h->partial, scan_partial_bytes((int64_t)ncell));
   A(&h->status, 4);
   // plans and tables
@@ -433,6 +441,8 @@ int pm_init(const pm_config_t* cfg, pm_handle_t** out) {
 int pm_destroy(pm_handle_t* h) {
   if (!h) return PM_ERR_ARG;
   cudaDeviceSynchronize();
+  for (auto& g : h->step_graphs) cudaGraphExecDestroy(g.exec);
+  if (h->capture_stream) cudaStreamDestroy(h->capture_stream);
   h->timer.flush();
   for (auto e : h->timer.pool) cudaEventDestroy(e);
   for (void* p : h->allocs) cudaFree(p);
@@ -557,8 +567,81 @@ int pm_kick_drift(pm_handle_t* h, float* x, float* v, int64_t n, const float* ac
   return PM_OK;
 }
 
+namespace {
+int step_launch(pm_handle_t* h, const pm_codes_t in[2], pm_codes_t out[2], double c_kick, double c_drift,
+                cudaStream_t st);
+
+bool same_codes(const pm_codes_t& a, const pm_codes_t& b) { return memcmp(&a, &b, sizeof(pm_codes_t)) == 0; }
+
+// Replays (capturing on first use) the step's launch sequence as one graph.
+// Capture runs on a library stream, since the caller's stream may be the
+// legacy default stream, which cannot be captured.
+int step_graph(pm_handle_t* h, const pm_codes_t in[2], pm_codes_t out[2], double c_kick, double c_drift,
+               cudaStream_t st) {
+  for (auto& g : h->step_graphs) {
+    if (g.ck == c_kick && g.cd == c_drift && same_codes(g.in[0], in[0]) && same_codes(g.in[1], in[1]) &&
+        same_codes(g.out[0], out[0]) && same_codes(g.out[1], out[1])) {
+      CK(h, cudaGraphLaunch(g.exec, st));
+      note_launches((int)g.launches);
+      return PM_OK;
+    }
+  }
+  if (!h->capture_stream) CK(h, cudaStreamCreateWithFlags(&h->capture_stream, cudaStreamNonBlocking));
+  const long long before = pm_launch_count();
+  CK(h, cudaStreamBeginCapture(h->capture_stream, cudaStreamCaptureModeThreadLocal));
+  const int r = step_launch(h, in, out, c_kick, c_drift, h->capture_stream);
+  cudaGraph_t graph = nullptr;
+  const cudaError_t ec = cudaStreamEndCapture(h->capture_stream, &graph);
+  const long long captured = pm_launch_count() - before;
+  note_launches((int)-captured);   // captured launches run only when the graph is launched
+  if (r != PM_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return r;
+  }
+  if (ec != cudaSuccess) return fail(h, PM_ERR_CUDA, std::string("step capture: ") + cudaGetErrorString(ec));
+  pm_handle::StepGraph g{};
+  for (int s = 0; s < 2; ++s) {
+    g.in[s] = in[s];
+    g.out[s] = out[s];
+  }
+  g.ck = c_kick;
+  g.cd = c_drift;
+  g.launches = captured;
+  const cudaError_t ei = cudaGraphInstantiate(&g.exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (ei != cudaSuccess) return fail(h, PM_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(ei));
+  if (h->step_graphs.size() >= 8) {
+    cudaGraphExecDestroy(h->step_graphs.front().exec);
+    h->step_graphs.erase(h->step_graphs.begin());
+  }
+  h->step_graphs.push_back(g);
+  CK(h, cudaGraphLaunch(g.exec, st));
+  note_launches((int)captured);
+  return PM_OK;
+}
+}  // namespace
+
+int pm_set_graphs(pm_handle_t* h, int on) {
+  if (!h) return PM_ERR_ARG;
+  h->graphs = on != 0;
+  if (!h->graphs) {
+    cudaDeviceSynchronize();
+    for (auto& g : h->step_graphs) cudaGraphExecDestroy(g.exec);
+    h->step_graphs.clear();
+  }
+  return PM_OK;
+}
+
 int pm_step(pm_handle_t* h, const pm_codes_t in[2], pm_codes_t out[2], double c_kick, double c_drift, void* stream) {
   if (!h || !in || !out) return fail(h, PM_ERR_ARG, "null argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (h->graphs && !h->timer.on) return step_graph(h, in, out, c_kick, c_drift, st);
+  return step_launch(h, in, out, c_kick, c_drift, st);
+}
+
+namespace {
+int step_launch(pm_handle_t* h, const pm_codes_t in[2], pm_codes_t out[2], double c_kick, double c_drift,
+                cudaStream_t st) {
   for (int s = 0; s < 2; ++s) {
     if (in[s].n != out[s].n) return fail(h, PM_ERR_ARG, "out[s].n must equal in[s].n");
     if (!in[s].cnt || !in[s].vmax || !in[s].n_esc || !in[s].esc || !out[s].cnt || !out[s].vmax || !out[s].n_esc ||
@@ -568,7 +651,6 @@ int pm_step(pm_handle_t* h, const pm_codes_t in[2], pm_codes_t out[2], double c_
   }
   if (in[0].n + in[1].n > h->scratch_n)
     return fail(h, PM_ERR_ARG, "particle counts exceed the pm_config_t counts the handle was sized for");
-  cudaStream_t st = (cudaStream_t)stream;
   Timer* tm = h->timer.on ? &h->timer : nullptr;
   const Geom& g = h->gm;
   const bool fixed = h->cfg.deposit_mode == 1;
@@ -596,8 +678,8 @@ int pm_step(pm_handle_t* h, const pm_codes_t in[2], pm_codes_t out[2], double c_
     CK(h, cudaMemsetAsync(h->vmax_bits, 0, 8, st));
     for (int s = 0; s < 2; ++s) CK(h, cudaMemsetAsync(h->counts[s], 0, (size_t)ncell * 4, st));
     CK(h, launch_ikd_count(view(in[0], vel16), view(in[1], vel16), h->off[0], h->off[1], h->geo, h->blk_ikd,
-                           h->acc_c, h->acc_f, ck, cd, h->counts[0], h->counts[1], h->vmax_bits, h->tkey, h->tpos,
-                           h->tv, st));
+                           h->acc_c, h->acc_f, ck, cd, h->counts[0], h->counts[1], h->vmax_bits, h->tkey, h->tpv,
+                           st));
   }
   {
     TimedScope ts(tm, "scan_out", st);
@@ -610,10 +692,11 @@ int pm_step(pm_handle_t* h, const pm_codes_t in[2], pm_codes_t out[2], double c_
     TimedScope ts(tm, "ikd_scatter", st);
     PCodesOut o0 = oview(out[0], vel16), o1 = oview(out[1], vel16);
     CK(h, launch_ikd_scatter(in[0].n, in[1].n, h->off[0], h->off[1], h->geo, h->blk_ikd, h->counts[0], h->counts[1],
-                             h->newoff[0], h->newoff[1], o0, o1, h->tkey, h->tpos, h->tv, h->status, st));
+                             h->newoff[0], h->newoff[1], o0, o1, h->tkey, h->tpv, h->status, st));
   }
   return PM_OK;
 }
+}  // namespace
 
 int pm_deposit_adjoint(pm_handle_t* h, int species, const float* x, int64_t n, const float* lam_rho, float* lam_x,
                        void* stream) {

@@ -837,7 +837,7 @@ __device__ __forceinline__ uint32_t window_cell(const Geo& g, const Win& w, int 
 // flushed once per window cell; per-species max |v'_d| is reduced.
 __global__ void __launch_bounds__(512, 2) k_ikd_count(PCodes c0, PCodes c1, const int64_t* off0, const int64_t* off1, Geo g, Blk bk,
                             const float* acc_c, const float* acc_f, float ck, float cd, uint32_t* counts0,
-                            uint32_t* counts1, uint32_t* vmax_bits, uint32_t* tkey, uint32_t* tpos, float* tv) {
+                            uint32_t* counts1, uint32_t* vmax_bits, uint32_t* tkey, uint4* tpv) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const int r = g.rcmp;
   const int nrow = bk.RY * bk.RZ;
@@ -945,10 +945,8 @@ __global__ void __launch_bounds__(512, 2) k_ikd_count(PCodes c0, PCodes c1, cons
         const int slot = window_slot_xyz(win, g.ncmp, cc[0], cc[1], cc[2]);
         const int64_t t = toff + p;
         tkey[t] = slot >= 0 ? (kInWindow | (uint32_t)slot) : key;
-        tpos[t] = (uint32_t)qq[0] | ((uint32_t)qq[1] << 8) | ((uint32_t)qq[2] << 16);
-        tv[3 * t] = v[0];
-        tv[3 * t + 1] = v[1];
-        tv[3 * t + 2] = v[2];
+        tpv[t] = make_uint4((uint32_t)qq[0] | ((uint32_t)qq[1] << 8) | ((uint32_t)qq[2] << 16), __float_as_uint(v[0]),
+                            __float_as_uint(v[1]), __float_as_uint(v[2]));
         local_max = fmaxf(local_max, fmaxf(fabsf(v[0]), fmaxf(fabsf(v[1]), fabsf(v[2]))));
         if (slot >= 0) atomicAdd(hs + slot, 1u);
         else atomicAdd(counts + key, 1u);
@@ -971,7 +969,7 @@ __global__ void __launch_bounds__(512, 2) k_ikd_count(PCodes c0, PCodes c1, cons
 // velocity with the new v_max and writes the codes.
 __global__ void __launch_bounds__(512, 2) k_ikd_scatter(int64_t n0, int64_t n1, const int64_t* off0, const int64_t* off1, Geo g, Blk bk,
                               uint32_t* counts0, uint32_t* counts1, const int64_t* newoff0, const int64_t* newoff1,
-                              PCodesOut o0, PCodesOut o1, const uint32_t* tkey, const uint32_t* tpos, const float* tv,
+                              PCodesOut o0, PCodesOut o1, const uint32_t* tkey, const uint4* tpv,
                               int* status) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const int nrow = bk.RY * bk.RZ;
@@ -1025,17 +1023,13 @@ __global__ void __launch_bounds__(512, 2) k_ikd_scatter(int64_t n0, int64_t n1, 
       // Two particles per thread per iteration keep more independent loads in flight.
       for (int64_t p = p0 + threadIdx.x; p < p1; p += 2 * blockDim.x) {
         const int64_t pp[2] = {p, p + blockDim.x};
-        uint32_t tk[2], pq[2];
-        float vv[2][3];
+        uint32_t tk[2];
+        uint4 pv[2];
 #pragma unroll
         for (int u = 0; u < 2; ++u) {
           if (pp[u] < p1) {
-            const int64_t t = toff + pp[u];
-            tk[u] = tkey[t];
-            pq[u] = tpos[t];
-            vv[u][0] = tv[3 * t];
-            vv[u][1] = tv[3 * t + 1];
-            vv[u][2] = tv[3 * t + 2];
+            tk[u] = tkey[toff + pp[u]];
+            pv[u] = tpv[toff + pp[u]];
           }
         }
 #pragma unroll
@@ -1052,10 +1046,11 @@ __global__ void __launch_bounds__(512, 2) k_ikd_scatter(int64_t n0, int64_t n1, 
             atomicOr(status, ST_CORRUPT);
             continue;
           }
-          o.pos[dst] = pq[u];
+          o.pos[dst] = pv[u].x;
           int qv[3];
-#pragma unroll
-          for (int d = 0; d < 3; ++d) qv[d] = encode_vel(vv[u][d], sv, half, vzero);
+          qv[0] = encode_vel(__uint_as_float(pv[u].y), sv, half, vzero);
+          qv[1] = encode_vel(__uint_as_float(pv[u].z), sv, half, vzero);
+          qv[2] = encode_vel(__uint_as_float(pv[u].w), sv, half, vzero);
           store_vel(o.vel, o.vel16, dst, qv);
         }
       }
@@ -1173,12 +1168,12 @@ cudaError_t launch_deposit_codes(const PCodes& c0, const PCodes& c1, const int64
 cudaError_t launch_ikd_count(const PCodes& c0, const PCodes& c1, const int64_t* off0, const int64_t* off1,
                              const Geo& g, const Blk& bk, const float* acc_c, const float* acc_f, float ck, float cd,
                              uint32_t* counts0, uint32_t* counts1, uint32_t* vmax_bits, uint32_t* tkey,
-                             uint32_t* tpos, float* tv, cudaStream_t st) {
+                             uint4* tpv, cudaStream_t st) {
   size_t smem = ikd_count_smem(g, bk);
   int nblk = bk.nbx * bk.nby * bk.nbz;
   cudaFuncSetAttribute(k_ikd_count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   k_ikd_count<<<nblk, 512, smem, st>>>(c0, c1, off0, off1, g, bk, acc_c, acc_f, ck, cd, counts0, counts1, vmax_bits,
-                                       tkey, tpos, tv);
+                                       tkey, tpv);
   note_launches(1);
   return cudaGetLastError();
 }
@@ -1186,12 +1181,12 @@ cudaError_t launch_ikd_count(const PCodes& c0, const PCodes& c1, const int64_t* 
 cudaError_t launch_ikd_scatter(int64_t n0, int64_t n1, const int64_t* off0, const int64_t* off1, const Geo& g,
                                const Blk& bk, uint32_t* counts0, uint32_t* counts1, const int64_t* newoff0,
                                const int64_t* newoff1, const PCodesOut& o0, const PCodesOut& o1, const uint32_t* tkey,
-                               const uint32_t* tpos, const float* tv, int* status, cudaStream_t st) {
+                               const uint4* tpv, int* status, cudaStream_t st) {
   size_t smem = ikd_scatter_smem(g, bk);
   int nblk = bk.nbx * bk.nby * bk.nbz;
   cudaFuncSetAttribute(k_ikd_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   k_ikd_scatter<<<nblk, 512, smem, st>>>(n0, n1, off0, off1, g, bk, counts0, counts1, newoff0, newoff1, o0, o1, tkey,
-                                         tpos, tv, status);
+                                         tpv, status);
   note_launches(1);
   return cudaGetLastError();
 }

@@ -65,6 +65,16 @@ class Codes:
             return out.pin_memory() if pin and out.device.type == "cpu" else out
         return Codes(self.n, mv(self.cnt), mv(self.esc), mv(self.n_esc), mv(self.pos), mv(self.vel), mv(self.vmax))
 
+    def clone(self) -> "Codes":
+        return Codes(self.n, self.cnt.clone(), self.esc.clone(), self.n_esc.clone(), self.pos.clone(),
+                     self.vel.clone(), self.vmax.clone())
+
+    def copy_(self, src: "Codes") -> "Codes":
+        """Copy src's codes into this object's buffers (same shapes), stream-ordered."""
+        for name in ("cnt", "esc", "n_esc", "pos", "vel", "vmax"):
+            getattr(self, name).copy_(getattr(src, name))
+        return self
+
     def vel_u16(self) -> torch.Tensor:
         """Velocity codes [n, 3] as int64 values 0..65535 (or 0..255)."""
         v = self.vel[:, :3].to(torch.int64)
@@ -241,6 +251,10 @@ class PM:
 
     def set_timing(self, on: bool):
         self._err(self.lib.pm_set_timing(self.h, 1 if on else 0))
+
+    def set_graphs(self, on: bool):
+        """Replay step() as captured CUDA graphs (one per codes/c_k/c_d set)."""
+        self._err(self.lib.pm_set_graphs(self.h, 1 if on else 0))
 
     def stage_times(self) -> Dict[str, Tuple[float, int]]:
         ms = (ctypes.c_float * 64)()

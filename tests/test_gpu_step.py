@@ -145,3 +145,36 @@ def test_multi_step_invariants():
         assert g.counts().sum() == codes[s].n
         x, v = codec.decompress(g, w.n_fine)
         assert np.all((x >= 0) & (x < w.n_fine))
+
+
+def test_graph_replay_equals_direct_launches():
+    """pm_set_graphs: four ping-pong steps replayed from captured graphs give
+    the same codes as four directly launched steps (fixed-point deposits, so
+    both runs are deterministic up to the order within a cell), and the launch counter advances by the
+    captured kernels on every replay."""
+    from paper_1611_01545_gb300 import _lib
+    w, cfg, codes, xv = _setup("two_level64", 16, 40, deposit_mode=1)
+    lib = _lib.load()
+    results = []
+    for graphs in (False, True):
+        pm = _pm(cfg)
+        pm.set_graphs(graphs)
+        a = [lib_codes_from_oracle(c, esc_cap=64) for c in codes]
+        b = [pm.empty_codes(c.n, esc_cap=64) for c in codes]
+        per_step = []
+        for _ in range(4):
+            n0 = lib.pm_launch_count()
+            pm.step(a, b, 0.5, 0.5)
+            torch.cuda.synchronize()
+            per_step.append(lib.pm_launch_count() - n0)
+            pm.check()
+            a, b = b, a
+        assert len(set(per_step)) == 1 and per_step[0] > 0, per_step
+        results.append(([oracle_codes_from_lib(a[s], w.n_fine // 4, w.vel_bits) for s in range(2)], per_step[0]))
+        pm.set_graphs(False)
+    (direct, n_direct), (replayed, n_graph) = results
+    assert n_direct == n_graph
+    for s in range(2):
+        assert direct[s].vmax == replayed[s].vmax
+        np.testing.assert_array_equal(direct[s].cnt, replayed[s].cnt)
+        np.testing.assert_array_equal(records(direct[s]), records(replayed[s]))
