@@ -75,7 +75,18 @@ typedef struct pm_handle pm_handle_t;
  *  mass, count   per species (0 = CDM, 1 = neutrinos).
  *  r_split       Gaussian split scale r_s in fine cells (two-level).
  *  r_cut         short-range kernel radius R in fine cells, R <= b - 2.
- *  tile_batch    fine tiles solved per batch (0 = library default). */
+ *  tile_batch    fine tiles solved per batch (0 = library default).
+ *  vmax_mode     v_max' of the recompressed velocities (Sec. 2.4): 0 = the
+ *                exact max over particles and components of |v'_d| (the
+ *                paper's definition; needs the whole kicked population before
+ *                any velocity can be quantised); 1 = the bound
+ *                v_max + |c_kick| (max|a_coarse| + max|a_fine|) over the
+ *                force meshes, rounded up, known right after the solve, so
+ *                pm_step quantises velocities in the same pass that kicks
+ *                them.  Mode 1 is not the paper's definition: the codes
+ *                differ from mode 0 (coarser velocity bins), but every
+ *                |v'_d| is still <= v_max'.
+ *  reserved      must be 0. */
 typedef struct pm_config {
   int32_t n_fine;
   int32_t coarse_ratio;
@@ -85,6 +96,8 @@ typedef struct pm_config {
   int32_t vel_bits;
   int32_t deposit_mode;
   int32_t tile_batch;
+  int32_t vmax_mode;
+  int32_t reserved;
   double G;
   double mass[2];
   int64_t count[2];

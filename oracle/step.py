@@ -82,6 +82,47 @@ def fine_accel(xs: Sequence[np.ndarray], cfg: Dict) -> List[np.ndarray]:
     return out
 
 
+def fine_accel_mesh(xs: Sequence[np.ndarray], cfg: Dict) -> np.ndarray:
+    """[3, n, n, n] short-range acceleration assembled from the interiors of
+    all tiles (each tile solved as in fine_accel): the fine force values the
+    particles' home-tile interpolations draw on."""
+    n, t, b = cfg["n_fine"], cfg["tile"], cfg["buffer"]
+    T = t + 2 * b
+    K = solve.fine_kernel(T, cfg["G"], cfg["r_split"], cfg["r_cut"])
+    xs64 = [np.asarray(x, np.float64).reshape(-1, 3) for x in xs]
+    out = np.zeros((3, n, n, n))
+    for _, o in tile_origins(n, t):
+        rho = sum(mesh.tile_deposit(x, m, o - b, T, n) for x, m in zip(xs64, cfg["mass"]))
+        a_t = solve.accel_tile(rho, K)
+        x0, y0, z0 = (int(c) for c in o)
+        out[:, z0:z0 + t, y0:y0 + t, x0:x0 + t] = a_t[:, b:b + t, b:b + t, b:b + t]
+    return out
+
+
+def force_meshes(xs: Sequence[np.ndarray], cfg: Dict) -> List[np.ndarray]:
+    """The force meshes a step interpolates from: the periodic mesh (single
+    level), or the coarse long-range mesh and the assembled fine mesh."""
+    if cfg["coarse_ratio"] == 1:
+        return [solve.accel_periodic(density_fine(xs, cfg), 1.0, cfg["G"])]
+    return [coarse_accel_mesh(xs, cfg), fine_accel_mesh(xs, cfg)]
+
+
+def vmax_bound(vmax_in: float, meshes: Sequence[np.ndarray], c_kick: float) -> np.float32:
+    """Velocity scale of the bound mode (an option, not the paper's Sec. 2.4
+    definition, which is the exact max): a decoded velocity component lies
+    below v_max and a CIC-interpolated acceleration component never exceeds
+    the largest mesh value of each mesh it sums, so
+
+        |v'_d| <= v_max + |c_kick| * sum_meshes max |a|.
+
+    Returned as the smallest float32 not below that value."""
+    b = float(vmax_in) + abs(float(c_kick)) * sum(float(np.max(np.abs(m))) for m in meshes)
+    f = np.float32(b)
+    if float(f) < b:
+        f = np.nextafter(f, np.float32(np.inf))
+    return f
+
+
 def accel(xs: Sequence[np.ndarray], cfg: Dict) -> List[np.ndarray]:
     """Per-particle acceleration of each species (fine-cell units)."""
     if cfg["coarse_ratio"] == 1:
@@ -108,9 +149,11 @@ def to_f32_positions(x, n_fine: int) -> np.ndarray:
 
 
 def step(codes: Sequence[codec.Codes], cfg: Dict, c_kick: float, c_drift: float,
-         order: str = "stable"):
+         order: str = "stable", vmax_mode: int = 0):
     """One full PM step from compressed state to compressed state.
 
+    vmax_mode 0 quantises the new velocities with their exact max (Sec. 2.4);
+    1 with vmax_bound of each species' input v_max and the force meshes.
     Returns (new codes per species, float64 x', v' per species in input order).
     """
     n = cfg["n_fine"]
@@ -118,10 +161,14 @@ def step(codes: Sequence[codec.Codes], cfg: Dict, c_kick: float, c_drift: float,
     xv = [codec.decompress(c, n) for c in codes]
     xs = [p[0] for p in xv]
     a = accel(xs, cfg)
+    vm = [None, None]
+    if vmax_mode == 1:
+        meshes = force_meshes(xs, cfg)
+        vm = [vmax_bound(c.vmax, meshes, c_kick) for c in codes]
     new_codes, states = [], []
-    for (x, v), acc in zip(xv, a):
+    for (x, v), acc, vmax in zip(xv, a, vm):
         x1, v1 = kick_drift(x, v, acc, c_kick, c_drift, n)
         new_codes.append(codec.compress(to_f32_positions(x1, n), v1.astype(np.float32), n, n_cmp,
-                                        cfg["vel_bits"], order=order))
+                                        cfg["vel_bits"], vmax=vmax, order=order))
         states.append((x1, v1))
     return new_codes, states

@@ -27,7 +27,8 @@ ERROR_NAMES = {0: "PM_OK", 1: "PM_ERR_ARG", 2: "PM_ERR_CONFIG", 3: "PM_ERR_CUDA"
 class pm_config_t(ctypes.Structure):
     _fields_ = [("n_fine", ctypes.c_int32), ("coarse_ratio", ctypes.c_int32), ("tile", ctypes.c_int32),
                 ("buffer", ctypes.c_int32), ("cmp_ratio", ctypes.c_int32), ("vel_bits", ctypes.c_int32),
-                ("deposit_mode", ctypes.c_int32), ("tile_batch", ctypes.c_int32), ("G", ctypes.c_double),
+                ("deposit_mode", ctypes.c_int32), ("tile_batch", ctypes.c_int32), ("vmax_mode", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("G", ctypes.c_double),
                 ("mass", ctypes.c_double * 2), ("count", ctypes.c_int64 * 2), ("r_split", ctypes.c_double),
                 ("r_cut", ctypes.c_double)]
 

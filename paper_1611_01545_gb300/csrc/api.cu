@@ -36,6 +36,7 @@ struct pm_handle {
   int64_t* newoff[2] = {nullptr, nullptr};
   uint32_t* counts[2] = {nullptr, nullptr};
   uint32_t* vmax_bits = nullptr;  // [2]
+  uint32_t* amax = nullptr;       // [2] max |a| over the coarse / fine force meshes (float bits)
   void* partial = nullptr;
   int* status = nullptr;
   Blk blk_dep{}, blk_ikd{};
@@ -323,6 +324,8 @@ int pm_init(const pm_config_t* cfg, pm_handle_t** out) {
   if (c.n_fine <= 0 || c.cmp_ratio <= 0 || !pow2(c.cmp_ratio) || c.n_fine % c.cmp_ratio) return bad("cmp_ratio must be a power of two dividing n_fine");
   if (c.vel_bits != 8 && c.vel_bits != 16) return bad("vel_bits must be 8 or 16");
   if (c.deposit_mode != 0 && c.deposit_mode != 1) return bad("deposit_mode must be 0 or 1");
+  if (c.vmax_mode != 0 && c.vmax_mode != 1) return bad("vmax_mode must be 0 or 1");
+  if (c.reserved != 0) return bad("reserved must be 0");
   if (c.count[0] < 0 || c.count[1] < 0) return bad("negative particle count");
   g.nf = c.n_fine;
   g.rcmp = c.cmp_ratio;
@@ -382,6 +385,7 @@ int pm_init(const pm_config_t* cfg, pm_handle_t** out) {
     A(&h->counts[s], ncell * 4);
   }
   A(&h->vmax_bits, 2 * 4);
+  A(&h->amax, 2 * 4);
   h->scratch_n = c.count[0] + c.count[1];
   A(&h->tkey, (size_t)h->scratch_n * 4);
   A(&h->tpv, (size_t)h->scratch_n * 16);
@@ -525,16 +529,16 @@ int pm_tile_density(pm_handle_t* h, const float* rho_fine, int64_t tile, float* 
 }
 
 static int solve_impl(pm_handle_t* h, const void* rho_c, const void* rho_f, bool fixed, float* acc_c, float* acc_f,
-                      cudaStream_t st) {
+                      cudaStream_t st, uint32_t* amax = nullptr) {
   Timer* tm = h->timer.on ? &h->timer : nullptr;
   if (h->gm.two) {
     {
       TimedScope ts(tm, "solve_coarse", st);
-      CK(h, solve_launch(h->plan_mesh, rho_c, fixed, acc_c, st, nullptr));
+      CK(h, solve_launch(h->plan_mesh, rho_c, fixed, acc_c, st, nullptr, amax));
     }
-    CK(h, solve_launch(h->plan_tiles, rho_f, fixed, acc_f, st, tm));
+    CK(h, solve_launch(h->plan_tiles, rho_f, fixed, acc_f, st, tm, amax ? amax + 1 : nullptr));
   } else {
-    CK(h, solve_launch(h->plan_mesh, rho_f, fixed, acc_f, st, tm));
+    CK(h, solve_launch(h->plan_mesh, rho_f, fixed, acc_f, st, tm, amax ? amax + 1 : nullptr));
   }
   return PM_OK;
 }
@@ -671,20 +675,24 @@ int step_launch(pm_handle_t* h, const pm_codes_t in[2], pm_codes_t out[2], doubl
                                (float)h->cfg.mass[0], (float)h->cfg.mass[1], M0, M1, g.two ? rc : nullptr, rf, fixed,
                                st));
   }
-  if (int r = solve_impl(h, rc, rf, fixed, h->acc_c, h->acc_f, st)) return r;
+  const bool bound = h->cfg.vmax_mode == 1;
   const float ck = (float)c_kick, cd = (float)c_drift;
+  if (bound) CK(h, cudaMemsetAsync(h->amax, 0, 8, st));
+  if (int r = solve_impl(h, rc, rf, fixed, h->acc_c, h->acc_f, st, bound ? h->amax : nullptr)) return r;
+  // bound mode: v_max' from the mesh maxima, before any particle is kicked
+  if (bound) CK(h, launch_vmax_bound(in[0].vmax, in[1].vmax, h->amax, ck, out[0].vmax, out[1].vmax, st));
   {
     TimedScope ts(tm, "ikd_count", st);
-    CK(h, cudaMemsetAsync(h->vmax_bits, 0, 8, st));
+    if (!bound) CK(h, cudaMemsetAsync(h->vmax_bits, 0, 8, st));
     for (int s = 0; s < 2; ++s) CK(h, cudaMemsetAsync(h->counts[s], 0, (size_t)ncell * 4, st));
     CK(h, launch_ikd_count(view(in[0], vel16), view(in[1], vel16), h->off[0], h->off[1], h->geo, h->blk_ikd,
                            h->acc_c, h->acc_f, ck, cd, h->counts[0], h->counts[1], h->vmax_bits, h->tkey, h->tpv,
-                           st));
+                           bound ? out[0].vmax : nullptr, bound ? out[1].vmax : nullptr, st));
   }
   {
     TimedScope ts(tm, "scan_out", st);
     for (int s = 0; s < 2; ++s) {
-      CK(h, launch_set_vmax(h->vmax_bits + s, out[s].vmax, st));
+      if (!bound) CK(h, launch_set_vmax(h->vmax_bits + s, out[s].vmax, st));
       CK(h, scan_counts(h->counts[s], ncell, in[s].n, h->newoff[s], out[s], h->partial, h->status, st));
     }
   }
@@ -692,7 +700,7 @@ int step_launch(pm_handle_t* h, const pm_codes_t in[2], pm_codes_t out[2], doubl
     TimedScope ts(tm, "ikd_scatter", st);
     PCodesOut o0 = oview(out[0], vel16), o1 = oview(out[1], vel16);
     CK(h, launch_ikd_scatter(in[0].n, in[1].n, h->off[0], h->off[1], h->geo, h->blk_ikd, h->counts[0], h->counts[1],
-                             h->newoff[0], h->newoff[1], o0, o1, h->tkey, h->tpv, h->status, st));
+                             h->newoff[0], h->newoff[1], o0, o1, h->tkey, h->tpv, bound, h->status, st));
   }
   return PM_OK;
 }

@@ -505,10 +505,20 @@ __device__ __forceinline__ uint32_t take_rank(uint32_t* counts, uint32_t key) {
   return old - (unsigned)__popc(peers) + below;
 }
 
+// Block maximum of m into *vmax_bits (float bits of a value >= 0): one atomic
+// per block, and none when the block's maximum does not exceed the current
+// value.  Every thread of the block must call it.
 __device__ __forceinline__ void block_vmax(float m, uint32_t* vmax_bits) {
+  __shared__ float red[32];
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-  if ((threadIdx.x & 31) == 0 && m > 0.f) atomicMax(vmax_bits, __float_as_uint(m));
+  __syncthreads();   // red may still be read by a previous call
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = fmaxf(m, red[w]);
+    if (m > 0.f && m > __uint_as_float(*(volatile uint32_t*)vmax_bits)) atomicMax(vmax_bits, __float_as_uint(m));
+  }
 }
 
 __device__ __forceinline__ void write_codes(PCodesOut o, int64_t dst, const float x[3], const float v[3], float inv_r,
@@ -579,6 +589,18 @@ __global__ void k_compress_pass(const float* x, const float* v, int64_t n, Geo g
 
 __global__ void k_set_vmax(const uint32_t* vmax_bits, const float* vmax_in, float* out) {
   *out = vmax_in ? *vmax_in : __uint_as_float(*vmax_bits);
+}
+
+// Bound on |v'_d| = |v_d + c_k a_d(x)| before the kick: decoded |v_d| < v_max
+// (bin centres) and a CIC-interpolated component never exceeds the largest
+// mesh value, so v_max' = v_max + |c_k| (max|a_coarse| + max|a_fine|); every
+// operation rounds up, so the float result is not below the exact bound.
+__global__ void k_vmax_bound(const float* vin0, const float* vin1, const uint32_t* amax, float ck, float* vout0,
+                             float* vout1) {
+  const float a = __fadd_ru(__uint_as_float(amax[0]), __uint_as_float(amax[1]));
+  const float ka = __fmul_ru(fabsf(ck), a);
+  *vout0 = __fadd_ru(*vin0, ka);
+  *vout1 = __fadd_ru(*vin1, ka);
 }
 
 // --------------------------------------------- fused passes over codes ----
@@ -837,7 +859,8 @@ __device__ __forceinline__ uint32_t window_cell(const Geo& g, const Win& w, int 
 // flushed once per window cell; per-species max |v'_d| is reduced.
 __global__ void __launch_bounds__(512, 2) k_ikd_count(PCodes c0, PCodes c1, const int64_t* off0, const int64_t* off1, Geo g, Blk bk,
                             const float* acc_c, const float* acc_f, float ck, float cd, uint32_t* counts0,
-                            uint32_t* counts1, uint32_t* vmax_bits, uint32_t* tkey, uint4* tpv) {
+                            uint32_t* counts1, uint32_t* vmax_bits, uint32_t* tkey, uint4* tpv,
+                            const float* vq0, const float* vq1) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const int r = g.rcmp;
   const int nrow = bk.RY * bk.RZ;
@@ -899,6 +922,12 @@ __global__ void __launch_bounds__(512, 2) k_ikd_count(PCodes c0, PCodes c1, cons
     const int half = in.vel16 ? 32768 : 128;
     const float step = __fmul_rn(*in.vmax, 1.0f / (float)half);
     float local_max = 0.f;
+    // v_max' known before the pass (bound mode): quantise here, the scatter copies codes
+    const float* vq = s ? vq1 : vq0;
+    const bool coded = vq != nullptr;
+    const float vqm = coded ? *vq : 0.f;
+    const bool qzero = !(vqm > 0.f);
+    const float qs = (coded && !qzero) ? __fdiv_rn(in.vel16 ? 32768.0f : 128.0f, vqm) : 0.f;
     const int64_t* ro_s = roff + s * nrow * (bk.RX + 1);
     for (int row = 0; row < nrow; ++row) {
       const int64_t* ro = ro_s + row * (bk.RX + 1);
@@ -945,14 +974,22 @@ __global__ void __launch_bounds__(512, 2) k_ikd_count(PCodes c0, PCodes c1, cons
         const int slot = window_slot_xyz(win, g.ncmp, cc[0], cc[1], cc[2]);
         const int64_t t = toff + p;
         tkey[t] = slot >= 0 ? (kInWindow | (uint32_t)slot) : key;
-        tpv[t] = make_uint4((uint32_t)qq[0] | ((uint32_t)qq[1] << 8) | ((uint32_t)qq[2] << 16), __float_as_uint(v[0]),
-                            __float_as_uint(v[1]), __float_as_uint(v[2]));
-        local_max = fmaxf(local_max, fmaxf(fabsf(v[0]), fmaxf(fabsf(v[1]), fabsf(v[2]))));
+        const uint32_t pw = (uint32_t)qq[0] | ((uint32_t)qq[1] << 8) | ((uint32_t)qq[2] << 16);
+        if (coded) {
+          int c3[3];
+#pragma unroll
+          for (int d = 0; d < 3; ++d) c3[d] = encode_vel(v[d], qs, half, qzero);
+          tpv[t] = in.vel16 ? make_uint4(pw, (uint32_t)c3[0] | ((uint32_t)c3[1] << 16), (uint32_t)c3[2], 0u)
+                            : make_uint4(pw, (uint32_t)c3[0] | ((uint32_t)c3[1] << 8) | ((uint32_t)c3[2] << 16), 0u, 0u);
+        } else {
+          tpv[t] = make_uint4(pw, __float_as_uint(v[0]), __float_as_uint(v[1]), __float_as_uint(v[2]));
+          local_max = fmaxf(local_max, fmaxf(fabsf(v[0]), fmaxf(fabsf(v[1]), fabsf(v[2]))));
+        }
         if (slot >= 0) atomicAdd(hs + slot, 1u);
         else atomicAdd(counts + key, 1u);
       }
     }
-    block_vmax(local_max, vmax_bits + s);
+    if (!coded) block_vmax(local_max, vmax_bits + s);
   }
   __syncthreads();
   for (int i = threadIdx.x; i < 2 * W; i += blockDim.x) {
@@ -969,7 +1006,7 @@ __global__ void __launch_bounds__(512, 2) k_ikd_count(PCodes c0, PCodes c1, cons
 // velocity with the new v_max and writes the codes.
 __global__ void __launch_bounds__(512, 2) k_ikd_scatter(int64_t n0, int64_t n1, const int64_t* off0, const int64_t* off1, Geo g, Blk bk,
                               uint32_t* counts0, uint32_t* counts1, const int64_t* newoff0, const int64_t* newoff1,
-                              PCodesOut o0, PCodesOut o1, const uint32_t* tkey, const uint4* tpv,
+                              PCodesOut o0, PCodesOut o1, const uint32_t* tkey, const uint4* tpv, int coded,
                               int* status) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const int nrow = bk.RY * bk.RZ;
@@ -1047,6 +1084,14 @@ __global__ void __launch_bounds__(512, 2) k_ikd_scatter(int64_t n0, int64_t n1, 
             continue;
           }
           o.pos[dst] = pv[u].x;
+          if (coded) {
+            if (o.vel16)
+              reinterpret_cast<unsigned long long*>(o.vel)[dst] =
+                  (unsigned long long)pv[u].y | ((unsigned long long)pv[u].z << 32);
+            else
+              reinterpret_cast<uint32_t*>(o.vel)[dst] = pv[u].y;
+            continue;
+          }
           int qv[3];
           qv[0] = encode_vel(__uint_as_float(pv[u].y), sv, half, vzero);
           qv[1] = encode_vel(__uint_as_float(pv[u].z), sv, half, vzero);
@@ -1168,12 +1213,12 @@ cudaError_t launch_deposit_codes(const PCodes& c0, const PCodes& c1, const int64
 cudaError_t launch_ikd_count(const PCodes& c0, const PCodes& c1, const int64_t* off0, const int64_t* off1,
                              const Geo& g, const Blk& bk, const float* acc_c, const float* acc_f, float ck, float cd,
                              uint32_t* counts0, uint32_t* counts1, uint32_t* vmax_bits, uint32_t* tkey,
-                             uint4* tpv, cudaStream_t st) {
+                             uint4* tpv, const float* vq0, const float* vq1, cudaStream_t st) {
   size_t smem = ikd_count_smem(g, bk);
   int nblk = bk.nbx * bk.nby * bk.nbz;
   cudaFuncSetAttribute(k_ikd_count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   k_ikd_count<<<nblk, 512, smem, st>>>(c0, c1, off0, off1, g, bk, acc_c, acc_f, ck, cd, counts0, counts1, vmax_bits,
-                                       tkey, tpv);
+                                       tkey, tpv, vq0, vq1);
   note_launches(1);
   return cudaGetLastError();
 }
@@ -1181,12 +1226,19 @@ cudaError_t launch_ikd_count(const PCodes& c0, const PCodes& c1, const int64_t* 
 cudaError_t launch_ikd_scatter(int64_t n0, int64_t n1, const int64_t* off0, const int64_t* off1, const Geo& g,
                                const Blk& bk, uint32_t* counts0, uint32_t* counts1, const int64_t* newoff0,
                                const int64_t* newoff1, const PCodesOut& o0, const PCodesOut& o1, const uint32_t* tkey,
-                               const uint4* tpv, int* status, cudaStream_t st) {
+                               const uint4* tpv, bool coded, int* status, cudaStream_t st) {
   size_t smem = ikd_scatter_smem(g, bk);
   int nblk = bk.nbx * bk.nby * bk.nbz;
   cudaFuncSetAttribute(k_ikd_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   k_ikd_scatter<<<nblk, 512, smem, st>>>(n0, n1, off0, off1, g, bk, counts0, counts1, newoff0, newoff1, o0, o1, tkey,
-                                         tpv, status);
+                                         tpv, coded ? 1 : 0, status);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_vmax_bound(const float* vin0, const float* vin1, const uint32_t* amax, float ck, float* vout0,
+                              float* vout1, cudaStream_t st) {
+  k_vmax_bound<<<1, 1, 0, st>>>(vin0, vin1, amax, ck, vout0, vout1);
   note_launches(1);
   return cudaGetLastError();
 }

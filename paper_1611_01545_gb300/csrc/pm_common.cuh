@@ -48,8 +48,9 @@ struct SolvePlan {
 void note_launches(int k);
 
 // Launch helpers implemented in solve.cu.
+// amax (optional): atomicMax of max |a| over the written force values, as float bits.
 cudaError_t solve_launch(const SolvePlan& p, const void* src, bool src_fixed, float* dst, cudaStream_t st,
-                         struct Timer* timer);
+                         struct Timer* timer, unsigned int* amax = nullptr);
 // Transpose of the periodic-mesh solve (adjoint): lam_rho = A^T lam_acc; spec3comp holds
 // the three component spectra [3][N][N][N/2+1].
 cudaError_t solve_adjoint_launch(const SolvePlan& p, const float* lam_acc, float* lam_rho, float2* spec3comp,

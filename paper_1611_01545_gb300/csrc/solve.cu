@@ -41,6 +41,7 @@ struct SolveArgs {
   const float2* tw;
   float* dst;
   int comp_mode;   // pass A only: blockIdx.y selects component pb of a [3][n^3] source at origin 0
+  unsigned int* amax;   // pass C: if set, atomicMax of max |output| (float bits; values are >= 0)
 };
 
 __device__ __forceinline__ int pmod(int a, int n) {
@@ -259,10 +260,22 @@ __global__ void __launch_bounds__(SolveCfg<N>::threads) k_solve_c(SolveArgs a) {
   // Output cells are interior cells: origin + b + local lies inside [0, n) without wrap.
   const int gz = oz + a.b + zo;
   float* dst = a.dst + (size_t)d * n * n * n + ((int64_t)gz * n + oy + a.b) * n + ox + a.b;
+  float m = 0.f;
   PM_ROWS(yl, a.t) {
     const float* w = reinterpret_cast<const float*>(W + (yl >> 1) * N + a.b) + (yl & 1);
     float* drow = dst + (int64_t)yl * n;
-    PM_COLS(xl, a.t) drow[xl] = w[2 * xl];
+    PM_COLS(xl, a.t) {
+      const float val = w[2 * xl];
+      drow[xl] = val;
+      m = fmaxf(m, fabsf(val));
+    }
+  }
+  if (a.amax) {
+    // warp maximum; an atomic only when it raises the running maximum
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0 && m > __uint_as_float(*(volatile unsigned int*)a.amax))
+      atomicMax(a.amax, __float_as_uint(m));
   }
 }
 
@@ -279,7 +292,8 @@ __global__ void k_tile_window(const float* src, int src_n, int nts, int t, int b
 }
 
 template <int N>
-static cudaError_t solve_n(const SolvePlan& p, const void* src, bool fixed, float* dst, cudaStream_t st, Timer* tm) {
+static cudaError_t solve_n(const SolvePlan& p, const void* src, bool fixed, float* dst, cudaStream_t st, Timer* tm,
+                           unsigned int* amax) {
   using C = SolveCfg<N>;
   static bool attr_done = false;
   if (!attr_done) {
@@ -292,7 +306,7 @@ static cudaError_t solve_n(const SolvePlan& p, const void* src, bool fixed, floa
   const int nprob = p.nts * p.nts * p.nts;
   for (int p0 = 0; p0 < nprob; p0 += p.batch) {
     int nb = (nprob - p0 < p.batch) ? (nprob - p0) : p.batch;
-    SolveArgs a{src, fixed ? 1 : 0, p.src_n, p.nts, p.t, p.b, p0, p.spec, p.spec3, p.kern, p.tw, dst, 0};
+    SolveArgs a{src, fixed ? 1 : 0, p.src_n, p.nts, p.t, p.b, p0, p.spec, p.spec3, p.kern, p.tw, dst, 0, amax};
     {
       TimedScope ts(tm, N == p.src_n && p.b == 0 ? "fft_a_mesh" : "fft_a_tiles", st);
       if (fixed) k_solve_a<N, true><<<dim3(N, nb), C::threads, C::smem_a, st>>>(a);
@@ -313,14 +327,15 @@ static cudaError_t solve_n(const SolvePlan& p, const void* src, bool fixed, floa
   return cudaSuccess;
 }
 
-cudaError_t solve_launch(const SolvePlan& p, const void* src, bool fixed, float* dst, cudaStream_t st, Timer* tm) {
+cudaError_t solve_launch(const SolvePlan& p, const void* src, bool fixed, float* dst, cudaStream_t st, Timer* tm,
+                         unsigned int* amax) {
   switch (p.N) {
-    case 16: return solve_n<16>(p, src, fixed, dst, st, tm);
-    case 32: return solve_n<32>(p, src, fixed, dst, st, tm);
-    case 48: return solve_n<48>(p, src, fixed, dst, st, tm);
-    case 64: return solve_n<64>(p, src, fixed, dst, st, tm);
-    case 96: return solve_n<96>(p, src, fixed, dst, st, tm);
-    case 128: return solve_n<128>(p, src, fixed, dst, st, tm);
+    case 16: return solve_n<16>(p, src, fixed, dst, st, tm, amax);
+    case 32: return solve_n<32>(p, src, fixed, dst, st, tm, amax);
+    case 48: return solve_n<48>(p, src, fixed, dst, st, tm, amax);
+    case 64: return solve_n<64>(p, src, fixed, dst, st, tm, amax);
+    case 96: return solve_n<96>(p, src, fixed, dst, st, tm, amax);
+    case 128: return solve_n<128>(p, src, fixed, dst, st, tm, amax);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -91,6 +91,8 @@ def config_struct(cfg: Dict) -> pm_config_t:
     c.vel_bits = int(cfg.get("vel_bits", 16))
     c.deposit_mode = int(cfg.get("deposit_mode", 0))
     c.tile_batch = int(cfg.get("tile_batch", 0))
+    c.vmax_mode = int(cfg.get("vmax_mode", 0))
+    c.reserved = 0
     c.G = float(cfg["G"])
     c.mass[0], c.mass[1] = (float(m) for m in cfg["mass"])
     cnt = cfg.get("count", (0, 0))

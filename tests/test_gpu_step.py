@@ -178,3 +178,27 @@ def test_graph_replay_equals_direct_launches():
         assert direct[s].vmax == replayed[s].vmax
         np.testing.assert_array_equal(direct[s].cnt, replayed[s].cnt)
         np.testing.assert_array_equal(records(direct[s]), records(replayed[s]))
+
+
+@pytest.mark.parametrize("name,n_cdm,n_nu", CASES)
+def test_fused_step_vmax_bound_mode(name, n_cdm, n_nu):
+    """vmax_mode 1: v_max' is the rounded-up bound from the mesh maxima (GPU
+    float32 meshes vs the oracle's float64 ones: relative 1e-4), it covers
+    every kicked velocity, and the codes are the oracle codec's with that
+    v_max (up to records straddling a bin edge)."""
+    w, cfg, codes, xv = _setup(name, n_cdm, n_nu, vmax_mode=1)
+    pm = _pm(cfg)
+    din = [lib_codes_from_oracle(c) for c in codes]
+    dout = [pm.empty_codes(c.n, esc_cap=64) for c in codes]
+    pm.step(din, dout, 1.0, 1.0)
+    pm.check()
+    ref, states = step.step(codes, cfg, 1.0, 1.0, vmax_mode=1)
+    n, nc = w.n_fine, w.n_fine // 4
+    for s in range(2):
+        g = oracle_codes_from_lib(dout[s], nc, w.vel_bits)
+        assert abs(float(g.vmax) - float(ref[s].vmax)) <= 1e-4 * float(ref[s].vmax)
+        x1, v1 = states[s]
+        assert float(g.vmax) >= np.max(np.abs(v1)) * (1 - 1e-5)
+        mine = codec.compress(step.to_f32_positions(x1, n), v1.astype(np.float32), n, nc, w.vel_bits, vmax=g.vmax)
+        frac = multiset_overlap(records(g), records(mine)) / mine.n
+        assert frac > 0.98, frac
