@@ -257,7 +257,11 @@ def run_gb300(args):
     def one_step():
         pm.step(a, b, 1.0, 1.0)
 
-    # headline: the step replayed from captured CUDA graphs (one per ping-pong direction)
+    tuning = pm.get_tuning()
+    if not args.no_autotune:
+        # launch tuning picked by timing candidate cell blocks / launch forms / tile batches
+        tuning = pm.autotune(a, b, 1.0, 1.0, reps=2)
+    # headline: the step replayed from a captured CUDA graph
     pm.set_graphs(True)
     for _ in range(args.warmup):
         one_step()
@@ -353,6 +357,7 @@ def run_gb300(args):
                 "steps": k_e2e},
         "gpu_launches": int(launches),
         "roofline": roofline,
+        "tuning": tuning,
         "launch_forms": {"graph_ms_per_step": round(ms_max / args.steps, 5),
                          "direct_ms_per_step": round(direct_ms, 5),
                          "plain_ms_per_step": round(plain_ms, 5),
@@ -513,6 +518,7 @@ def main():
                    help="0: exact v_max' (the paper's definition); 1: bound from the force meshes")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-adjoint", action="store_true")
+    p.add_argument("--no-autotune", action="store_true")
     p.add_argument("--adjoint-workload", default="diff128")
     args = p.parse_args()
     res = run_reference(args) if args.impl == "reference" else run_gb300(args)

@@ -319,6 +319,47 @@ int pm_stage_times(pm_handle_t* h, float* ms, int cap, int* n_stages, char* name
  * counterpart in the paper (launch batching only; results are identical). */
 int pm_set_graphs(pm_handle_t* h, int on);
 
+/* Launch tuning of pm_step and pm_deposit_codes (no counterpart in the paper;
+ * results are the same for every tuning up to float summation order):
+ *  deposit_block[3]    compression cells per deposit CTA along x, y, z (its
+ *                      shared-memory bins cover them plus a one-cell halo);
+ *  deposit_persistent  0: one CTA per cell block; 1: as many CTAs as fit on
+ *                      the device, each drawing cell blocks from a device
+ *                      counter until none are left (uneven, clustered blocks
+ *                      then balance across the SMs);
+ *  kick_block[3]       compression cells per CTA of the interpolate + kick +
+ *                      drift + recompress passes;
+ *  kick_window         half-width in cells of the new-cell window whose
+ *                      counts a CTA keeps in shared memory (1..4; particles
+ *                      moving further use global counters);
+ *  kick_persistent     as deposit_persistent, for those passes;
+ *  tile_batch          fine tiles per solve launch, 1..the configured batch.
+ * Every block edge must divide n_cmp and the shared memory must fit one block
+ * of the device (PM_ERR_ARG otherwise).  pm_set_tuning drops captured step
+ * graphs (synchronising the device first). */
+typedef struct pm_tuning {
+  int32_t deposit_block[3];
+  int32_t deposit_persistent;
+  int32_t kick_block[3];
+  int32_t kick_window;
+  int32_t kick_persistent;
+  int32_t tile_batch;
+} pm_tuning_t;
+int pm_get_tuning(const pm_handle_t* h, pm_tuning_t* t);
+int pm_set_tuning(pm_handle_t* h, const pm_tuning_t* t);
+
+/* Autotuner: times pm_step(in -> out, c_kick, c_drift) on `stream` (one
+ * warm-up step, then `reps` timed steps per candidate, CUDA events) for the
+ * current tuning and for candidate deposit blocks and launch forms, then
+ * candidate kick blocks, windows and launch forms, then tile batches
+ * (coordinate search, each stage starting from the best so far), keeps the
+ * fastest and writes it to *chosen (may be NULL).  It writes `out` (any
+ * earlier content is lost) and never `in`; blocks the calling thread until
+ * the timing is done.  Per-stage timing and step graphs are suspended while
+ * it runs.  On error the previous tuning is restored. */
+int pm_autotune(pm_handle_t* h, const pm_codes_t in[2], pm_codes_t out[2], double c_kick, double c_drift, int32_t reps,
+                void* stream, pm_tuning_t* chosen);
+
 /* Serializer for the Sec. 2.4 byte stream (host memory, not stream-ordered):
  * header "PMNU", u32 version 1, u32 n_cmp, u32 vel_bits, u64 n, f32 v_max,
  * u32 0; then per cell the count byte (255 + int32 count if >= 255) and the

@@ -33,6 +33,12 @@ class pm_config_t(ctypes.Structure):
                 ("r_cut", ctypes.c_double)]
 
 
+class pm_tuning_t(ctypes.Structure):
+    _fields_ = [("deposit_block", ctypes.c_int32 * 3), ("deposit_persistent", ctypes.c_int32),
+                ("kick_block", ctypes.c_int32 * 3), ("kick_window", ctypes.c_int32),
+                ("kick_persistent", ctypes.c_int32), ("tile_batch", ctypes.c_int32)]
+
+
 class pm_particles_t(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("x", ctypes.c_void_p), ("v", ctypes.c_void_p)]
 
@@ -46,6 +52,7 @@ class pm_codes_t(ctypes.Structure):
 EXPORTED = ["pm_init", "pm_destroy", "pm_geometry", "pm_decompress", "pm_compress", "pm_deposit",
             "pm_deposit_fixed", "pm_deposit_codes", "pm_tile_density", "pm_solve", "pm_solve_fixed", "pm_interpolate",
             "pm_kick_drift", "pm_step", "pm_step_host", "pm_check", "pm_last_error", "pm_set_timing", "pm_set_graphs",
+            "pm_get_tuning", "pm_set_tuning", "pm_autotune",
             "pm_stage_times", "pm_serialize", "pm_deserialize", "pm_error_string", "pm_launch_count",
             "pm_decompress_noalloc", "pm_deposit_adjoint", "pm_solve_adjoint", "pm_interpolate_adjoint",
             "pm_step_adjoint"]
@@ -74,6 +81,10 @@ _PROTOS = {
     "pm_last_error": (ctypes.c_int, [_P, ctypes.c_char_p, ctypes.c_size_t]),
     "pm_set_timing": (ctypes.c_int, [_P, ctypes.c_int]),
     "pm_set_graphs": (ctypes.c_int, [_P, ctypes.c_int]),
+    "pm_get_tuning": (ctypes.c_int, [_P, ctypes.POINTER(pm_tuning_t)]),
+    "pm_set_tuning": (ctypes.c_int, [_P, ctypes.POINTER(pm_tuning_t)]),
+    "pm_autotune": (ctypes.c_int, [_P, ctypes.POINTER(pm_codes_t), ctypes.POINTER(pm_codes_t), ctypes.c_double,
+                                   ctypes.c_double, ctypes.c_int32, _P, ctypes.POINTER(pm_tuning_t)]),
     "pm_stage_times": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_float), ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                       ctypes.c_char_p, ctypes.c_size_t]),
     "pm_serialize": (ctypes.c_int, [ctypes.POINTER(pm_codes_t), ctypes.c_int32, ctypes.c_int32, _P, ctypes.c_size_t,

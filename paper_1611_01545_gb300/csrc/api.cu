@@ -40,6 +40,10 @@ struct pm_handle {
   void* partial = nullptr;
   int* status = nullptr;
   Blk blk_dep{}, blk_ikd{};
+  bool persist_dep = false, persist_ikd = false;   // persistent launches of the particle passes
+  int* work = nullptr;           // [4] device work counters of persistent launches
+  int tile_batch_alloc = 1;      // tile workspace capacity (problems per solve batch)
+  size_t smem_optin = 0;         // largest dynamic shared memory per block on this device
   // per-particle scratch of the fused step (stream order, both species)
   int64_t scratch_n = 0;
   uint32_t* tkey = nullptr;
@@ -229,6 +233,22 @@ Blk choose_blk(const Geom& g, bool fixed, bool deposit) {
 
 Geo to_geo(const Geom& g) { return Geo{g.nf, g.rc, g.nc, g.rcmp, g.ncmp, g.ncell(), g.two}; }
 
+// Launch copies of the handle's cell-block shapes with their work counters.
+Blk dep_blk(const pm_handle* h) {
+  Blk b = h->blk_dep;
+  b.work = h->persist_dep ? h->work : nullptr;
+  return b;
+}
+Blk ikd_blk(const pm_handle* h, int pass) {
+  Blk b = h->blk_ikd;
+  b.work = h->persist_ikd ? h->work + 1 + pass : nullptr;
+  return b;
+}
+cudaError_t zero_work(const pm_handle* h, cudaStream_t st) {
+  if (!h->persist_dep && !h->persist_ikd) return cudaSuccess;
+  return cudaMemsetAsync(h->work, 0, 4 * sizeof(int), st);
+}
+
 PCodes view(const pm_codes_t& c, bool vel16) {
   return PCodes{reinterpret_cast<const uint32_t*>(c.pos), c.vel, c.vmax, c.n, vel16};
 }
@@ -386,6 +406,7 @@ int pm_init(const pm_config_t* cfg, pm_handle_t** out) {
   }
   A(&h->vmax_bits, 2 * 4);
   A(&h->amax, 2 * 4);
+  A(&h->work, 4 * 4);
   h->scratch_n = c.count[0] + c.count[1];
   A(&h->tkey, (size_t)h->scratch_n * 4);
   A(&h->tpv, (size_t)h->scratch_n * 16);
@@ -433,6 +454,12 @@ int pm_init(const pm_config_t* cfg, pm_handle_t** out) {
   }
   h->blk_dep = choose_blk(g, fixed, true);
   h->blk_ikd = choose_blk(g, fixed, false);
+  h->tile_batch_alloc = g.two ? h->plan_tiles.batch : 1;
+  {
+    int optin = 0;
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
+    h->smem_optin = optin > 1024 ? (size_t)optin - 1024 : 0;   // room for the kernels' static shared memory
+  }
   if (rc != PM_OK) {
     fprintf(stderr, "pm_init: %s\n", h->err.c_str());
     pm_destroy(h);
@@ -515,7 +542,8 @@ int pm_deposit_codes(pm_handle_t* h, const pm_codes_t in[2], void* rho_coarse, v
   const bool vel16 = h->cfg.vel_bits == 16;
   for (int s = 0; s < 2; ++s) CK(h, scan_codes(in[s], h->gm.ncell(), h->off[s], h->partial, h->status, st));
   long long M0 = llrint(h->cfg.mass[0] * 4294967296.0), M1 = llrint(h->cfg.mass[1] * 4294967296.0);
-  CK(h, launch_deposit_codes(view(in[0], vel16), view(in[1], vel16), h->off[0], h->off[1], h->geo, h->blk_dep,
+  CK(h, zero_work(h, st));
+  CK(h, launch_deposit_codes(view(in[0], vel16), view(in[1], vel16), h->off[0], h->off[1], h->geo, dep_blk(h),
                              (float)h->cfg.mass[0], (float)h->cfg.mass[1], M0, M1, h->gm.two ? rho_coarse : nullptr,
                              rho_fine, fixed, st));
   return PM_OK;
@@ -636,6 +664,166 @@ int pm_set_graphs(pm_handle_t* h, int on) {
   return PM_OK;
 }
 
+namespace {
+// A cell-block shape is usable when it tiles the compression mesh and its
+// shared memory fits one block of this device.
+bool blk_fits(const pm_handle* h, const Blk& b, bool deposit) {
+  const int n = h->gm.ncmp;
+  if (b.RX < 1 || b.RY < 1 || b.RZ < 1 || n % b.RX || n % b.RY || n % b.RZ) return false;
+  if (b.D < 1 || b.D > 4) return false;
+  if (deposit) return deposit_codes_smem(h->geo, b, h->cfg.deposit_mode == 1) <= h->smem_optin;
+  return ikd_count_smem(h->geo, b) <= h->smem_optin && ikd_scatter_smem(h->geo, b) <= h->smem_optin;
+}
+
+Blk make_blk(const pm_handle* h, const int32_t r[3], int D) {
+  Blk b{};
+  b.RX = r[0];
+  b.RY = r[1];
+  b.RZ = r[2];
+  b.D = D;
+  if (b.RX > 0 && b.RY > 0 && b.RZ > 0) {
+    b.nbx = h->gm.ncmp / b.RX;
+    b.nby = h->gm.ncmp / b.RY;
+    b.nbz = h->gm.ncmp / b.RZ;
+  }
+  return b;
+}
+
+void drop_graphs(pm_handle* h) {
+  if (h->step_graphs.empty()) return;
+  cudaDeviceSynchronize();
+  for (auto& g : h->step_graphs) cudaGraphExecDestroy(g.exec);
+  h->step_graphs.clear();
+}
+
+int apply_tuning(pm_handle* h, const pm_tuning_t* t) {
+  const Blk bd = make_blk(h, t->deposit_block, 2);
+  const Blk bi = make_blk(h, t->kick_block, t->kick_window);
+  if (!blk_fits(h, bd, true)) return fail(h, PM_ERR_ARG, "deposit_block does not tile the mesh or exceeds shared memory");
+  if (!blk_fits(h, bi, false)) return fail(h, PM_ERR_ARG, "kick_block/kick_window invalid or exceeds shared memory");
+  if (t->tile_batch < 1 || t->tile_batch > h->tile_batch_alloc)
+    return fail(h, PM_ERR_ARG, "tile_batch must lie in [1, the configured tile batch]");
+  if ((t->deposit_persistent & ~1) || (t->kick_persistent & ~1)) return fail(h, PM_ERR_ARG, "persistent flags are 0 or 1");
+  drop_graphs(h);
+  h->blk_dep = bd;
+  h->blk_ikd = bi;
+  h->persist_dep = t->deposit_persistent != 0;
+  h->persist_ikd = t->kick_persistent != 0;
+  if (h->gm.two) h->plan_tiles.batch = t->tile_batch;
+  return PM_OK;
+}
+}  // namespace
+
+int pm_get_tuning(const pm_handle_t* h, pm_tuning_t* t) {
+  if (!h || !t) return PM_ERR_ARG;
+  t->deposit_block[0] = h->blk_dep.RX;
+  t->deposit_block[1] = h->blk_dep.RY;
+  t->deposit_block[2] = h->blk_dep.RZ;
+  t->deposit_persistent = h->persist_dep ? 1 : 0;
+  t->kick_block[0] = h->blk_ikd.RX;
+  t->kick_block[1] = h->blk_ikd.RY;
+  t->kick_block[2] = h->blk_ikd.RZ;
+  t->kick_window = h->blk_ikd.D;
+  t->kick_persistent = h->persist_ikd ? 1 : 0;
+  t->tile_batch = h->gm.two ? h->plan_tiles.batch : 1;
+  return PM_OK;
+}
+
+int pm_set_tuning(pm_handle_t* h, const pm_tuning_t* t) {
+  if (!h || !t) return fail(h, PM_ERR_ARG, "null argument");
+  return apply_tuning(h, t);
+}
+
+int pm_autotune(pm_handle_t* h, const pm_codes_t in[2], pm_codes_t out[2], double c_kick, double c_drift, int32_t reps,
+                void* stream, pm_tuning_t* chosen) {
+  if (!h || !in || !out) return fail(h, PM_ERR_ARG, "null argument");
+  if (reps < 1 || reps > 1000) return fail(h, PM_ERR_ARG, "reps must lie in [1, 1000]");
+  cudaStream_t st = (cudaStream_t)stream;
+  const bool timing = h->timer.on, graphs = h->graphs;
+  h->timer.on = false;
+  h->graphs = false;
+  pm_tuning_t best{};
+  pm_get_tuning(h, &best);
+  const pm_tuning_t start = best;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  int rc = PM_OK;
+  float best_ms = 0.f;
+  auto restore = [&](int code) {
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    h->timer.on = timing;
+    h->graphs = graphs;
+    return code;
+  };
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+    return restore(fail(h, PM_ERR_CUDA, "event create"));
+  // mean step time of a tuning: one untimed step, then reps steps between events
+  auto time_of = [&](const pm_tuning_t& t, float* ms) -> int {
+    if (int r = apply_tuning(h, &t)) return r;
+    if (int r = step_launch(h, in, out, c_kick, c_drift, st)) return r;
+    if (cudaEventRecord(e0, st) != cudaSuccess) return fail(h, PM_ERR_CUDA, "event record");
+    for (int i = 0; i < reps; ++i)
+      if (int r = step_launch(h, in, out, c_kick, c_drift, st)) return r;
+    if (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+        cudaEventElapsedTime(ms, e0, e1) != cudaSuccess)
+      return fail(h, PM_ERR_CUDA, "event timing");
+    *ms /= (float)reps;
+    return PM_OK;
+  };
+  if ((rc = time_of(best, &best_ms))) {
+    apply_tuning(h, &start);
+    return restore(rc);
+  }
+  auto consider = [&](const pm_tuning_t& t) -> int {
+    const Blk bd = make_blk(h, t.deposit_block, 2), bi = make_blk(h, t.kick_block, t.kick_window);
+    if (!blk_fits(h, bd, true) || !blk_fits(h, bi, false)) return PM_OK;   // not a candidate on this mesh
+    float ms = 0.f;
+    if (int r = time_of(t, &ms)) return r;
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = t;
+    }
+    return PM_OK;
+  };
+  const int n = h->gm.ncmp;
+  const int rx[4] = {n, n / 2, n / 4, n / 8};
+  const int ry[3] = {1, 2, 4}, rz[2] = {1, 2};
+  // coordinate search: deposit block and launch form, then the kick passes'
+  // block, window and launch form, then the tile batch
+  for (int pass = 0; pass < 2 && rc == PM_OK; ++pass)
+    for (int a = 0; a < 4 && rc == PM_OK; ++a)
+      for (int b = 0; b < 3 && rc == PM_OK; ++b)
+        for (int c = 0; c < 2 && rc == PM_OK; ++c)
+          for (int p = 0; p < 2 && rc == PM_OK; ++p)
+            for (int D = (pass ? 1 : 2); D <= 2 && rc == PM_OK; ++D) {
+              if (rx[a] < 1) continue;
+              pm_tuning_t t = best;
+              int32_t* blk = pass ? t.kick_block : t.deposit_block;
+              blk[0] = rx[a];
+              blk[1] = ry[b];
+              blk[2] = rz[c];
+              if (pass) {
+                t.kick_persistent = p;
+                t.kick_window = D;
+              } else {
+                t.deposit_persistent = p;
+              }
+              rc = consider(t);
+            }
+  for (int k = 1; k <= 4 && rc == PM_OK; k *= 2) {
+    pm_tuning_t t = best;
+    t.tile_batch = h->tile_batch_alloc / k > 0 ? h->tile_batch_alloc / k : 1;
+    rc = consider(t);
+  }
+  if (rc != PM_OK) {
+    apply_tuning(h, &start);
+    return restore(rc);
+  }
+  apply_tuning(h, &best);
+  if (chosen) *chosen = best;
+  return restore(PM_OK);
+}
+
 int pm_step(pm_handle_t* h, const pm_codes_t in[2], pm_codes_t out[2], double c_kick, double c_drift, void* stream) {
   if (!h || !in || !out) return fail(h, PM_ERR_ARG, "null argument");
   cudaStream_t st = (cudaStream_t)stream;
@@ -671,7 +859,8 @@ int step_launch(pm_handle_t* h, const pm_codes_t in[2], pm_codes_t out[2], doubl
     CK(h, cudaMemsetAsync(rf, 0, (size_t)g.nfine3() * (fixed ? 8 : 4), st));
     if (g.two) CK(h, cudaMemsetAsync(rc, 0, (size_t)g.ncoarse3() * (fixed ? 8 : 4), st));
     long long M0 = llrint(h->cfg.mass[0] * 4294967296.0), M1 = llrint(h->cfg.mass[1] * 4294967296.0);
-    CK(h, launch_deposit_codes(view(in[0], vel16), view(in[1], vel16), h->off[0], h->off[1], h->geo, h->blk_dep,
+    CK(h, zero_work(h, st));
+    CK(h, launch_deposit_codes(view(in[0], vel16), view(in[1], vel16), h->off[0], h->off[1], h->geo, dep_blk(h),
                                (float)h->cfg.mass[0], (float)h->cfg.mass[1], M0, M1, g.two ? rc : nullptr, rf, fixed,
                                st));
   }
@@ -685,7 +874,7 @@ int step_launch(pm_handle_t* h, const pm_codes_t in[2], pm_codes_t out[2], doubl
     TimedScope ts(tm, "ikd_count", st);
     if (!bound) CK(h, cudaMemsetAsync(h->vmax_bits, 0, 8, st));
     for (int s = 0; s < 2; ++s) CK(h, cudaMemsetAsync(h->counts[s], 0, (size_t)ncell * 4, st));
-    CK(h, launch_ikd_count(view(in[0], vel16), view(in[1], vel16), h->off[0], h->off[1], h->geo, h->blk_ikd,
+    CK(h, launch_ikd_count(view(in[0], vel16), view(in[1], vel16), h->off[0], h->off[1], h->geo, ikd_blk(h, 0),
                            h->acc_c, h->acc_f, ck, cd, h->counts[0], h->counts[1], h->vmax_bits, h->tkey, h->tpv,
                            bound ? out[0].vmax : nullptr, bound ? out[1].vmax : nullptr, st));
   }
@@ -699,7 +888,7 @@ int step_launch(pm_handle_t* h, const pm_codes_t in[2], pm_codes_t out[2], doubl
   {
     TimedScope ts(tm, "ikd_scatter", st);
     PCodesOut o0 = oview(out[0], vel16), o1 = oview(out[1], vel16);
-    CK(h, launch_ikd_scatter(in[0].n, in[1].n, h->off[0], h->off[1], h->geo, h->blk_ikd, h->counts[0], h->counts[1],
+    CK(h, launch_ikd_scatter(in[0].n, in[1].n, h->off[0], h->off[1], h->geo, ikd_blk(h, 1), h->counts[0], h->counts[1],
                              h->newoff[0], h->newoff[1], o0, o1, h->tkey, h->tpv, bound, h->status, st));
   }
   return PM_OK;

@@ -615,6 +615,30 @@ __device__ __forceinline__ CellBlock block_of(const Blk& bk, int bid) {
   return CellBlock{bx * bk.RX, by * bk.RY, bz * bk.RZ};
 }
 
+// Runs body(bid) for the cell blocks of this CTA: its own block (one CTA per
+// cell block), or, when bk.work is set (persistent launch), blocks drawn one
+// at a time from the device counter *bk.work until all are taken, so that
+// CTAs that drew light blocks take more of them.  body must use __syncthreads
+// uniformly; the barrier before each draw keeps the next block's shared-memory
+// set-up from overlapping the previous block's flush.
+template <class F>
+__device__ __forceinline__ void for_each_block(const Blk& bk, F&& body) {
+  if (!bk.work) {
+    body((int)blockIdx.x);
+    return;
+  }
+  __shared__ int s_bid;
+  const int nblk = bk.nbx * bk.nby * bk.nbz;
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) s_bid = atomicAdd(bk.work, 1);
+    __syncthreads();
+    const int bid = s_bid;
+    if (bid >= nblk) break;
+    body(bid);
+  }
+}
+
 // Loads the CSR offsets of the block's rows into smem: roff[r*(RX+1) + i], r = row (y fastest).
 __device__ __forceinline__ void load_row_offsets(const int64_t* off, const Geo& g, const Blk& bk, CellBlock cb,
                                                  int64_t* roff) {
@@ -695,108 +719,116 @@ template <typename Acc>
 __global__ void k_deposit_codes(PCodes c0, PCodes c1, const int64_t* off0, const int64_t* off1, Geo g, Blk bk,
                                 float m0, float m1, long long M0, long long M1, Acc* rho_c, Acc* rho_f) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  const int r = g.rcmp;
-  const int fx = bk.RX * r + 1, fy = bk.RY * r + 1, fz = bk.RZ * r + 1;
-  const int cx = bk.RX + 1, cy = bk.RY + 1, cz = bk.RZ + 1;
-  const int nrow = bk.RY * bk.RZ;
-  int64_t* roff = reinterpret_cast<int64_t*>(smraw);
-  Acc* sf = reinterpret_cast<Acc*>(roff + 2 * nrow * (bk.RX + 1));
-  Acc* sc = sf + fx * fy * fz;
-  const int nsf = fx * fy * fz, nsc = g.two ? cx * cy * cz : 0;
-  for (int i = threadIdx.x; i < nsf + nsc; i += blockDim.x) sf[i] = (Acc)0;
-  const CellBlock cb = block_of(bk, blockIdx.x);
-  load_row_offsets(off0, g, bk, cb, roff);
-  load_row_offsets(off1, g, bk, cb, roff + nrow * (bk.RX + 1));
-  __syncthreads();
-  const float pscale = (float)r / 256.0f;
-  const int bxf = cb.ix0 * r, byf = cb.iy0 * r, bzf = cb.iz0 * r;
-  for (int s = 0; s < 2; ++s) {
-    const PCodes& cs = s ? c1 : c0;
-    const float m = s ? m1 : m0;
-    const long long M = s ? M1 : M0;
-    const int64_t* ro_s = roff + s * nrow * (bk.RX + 1);
-    for (int row = 0; row < nrow; ++row) {
-      const int64_t* ro = ro_s + row * (bk.RX + 1);
-      const int iy = cb.iy0 + row % bk.RY, iz = cb.iz0 + row / bk.RY;
-      // A corrupt stream (flagged by the scan) may claim more particles than
-      // exist; never read past the caller's n records.
-      const int64_t p0 = ro[0] < cs.n ? ro[0] : cs.n;
-      const int64_t p1 = ro[bk.RX] < cs.n ? ro[bk.RX] : cs.n;
-      const int64_t rounds = (p1 - p0 + blockDim.x - 1) / blockDim.x;
-      for (int64_t it = 0; it < rounds; ++it) {
-        const int64_t p = p0 + it * blockDim.x + threadIdx.x;
-        const bool live = p < p1;
-        int ixl = 0;
-        float px = 0.f, py = 0.f, pz = 0.f;
-        if (live) {
-          ixl = row_cell(ro, bk.RX, p);
-          int q[3];
-          unpack_pos(cs.pos[p], q);
-          px = decode_pos(cb.ix0 + ixl, q[0], pscale);
-          py = decode_pos(iy, q[1], pscale);
-          pz = decode_pos(iz, q[2], pscale);
-          // fine CIC in local region coordinates (no wrap inside the block)
-          float flx = floorf(px), fly = floorf(py), flz = floorf(pz);
-          int lx = (int)flx - bxf, ly = (int)fly - byf, lz = (int)flz - bzf;
-          float w1[3] = {__fsub_rn(px, flx), __fsub_rn(py, fly), __fsub_rn(pz, flz)};
-          Acc t8[8];
-          corner_masses(m, M, w1, t8);
-#pragma unroll
-          for (int c = 0; c < 8; ++c) {
-            int dx = c & 1, dy = (c >> 1) & 1, dz = c >> 2;
-            smem_acc(&sf[((lz + dz) * fy + (ly + dy)) * fx + (lx + dx)], t8[c]);
-          }
-        }
-        if (g.two) {
-          // Coarse cell == compression cell (coarse_ratio == cmp_ratio), so every
-          // particle of a run shares its 8 coarse corners: sum the run in
-          // registers and let its last lane do 8 shared-memory adds.
-          Acc cv[8];
+  for_each_block(bk, [&](const int bid) {
+    const int r = g.rcmp;
+    const int fx = bk.RX * r + 1, fy = bk.RY * r + 1, fz = bk.RZ * r + 1;
+    const int cx = bk.RX + 1, cy = bk.RY + 1, cz = bk.RZ + 1;
+    const int nrow = bk.RY * bk.RZ;
+    int64_t* roff = reinterpret_cast<int64_t*>(smraw);
+    Acc* sf = reinterpret_cast<Acc*>(roff + 2 * nrow * (bk.RX + 1));
+    Acc* sc = sf + fx * fy * fz;
+    const int nsf = fx * fy * fz, nsc = g.two ? cx * cy * cz : 0;
+    for (int i = threadIdx.x; i < nsf + nsc; i += blockDim.x) sf[i] = (Acc)0;
+    const CellBlock cb = block_of(bk, bid);
+    load_row_offsets(off0, g, bk, cb, roff);
+    load_row_offsets(off1, g, bk, cb, roff + nrow * (bk.RX + 1));
+    __syncthreads();
+    const float pscale = (float)r / 256.0f;
+    const int bxf = cb.ix0 * r, byf = cb.iy0 * r, bzf = cb.iz0 * r;
+    for (int s = 0; s < 2; ++s) {
+      const PCodes& cs = s ? c1 : c0;
+      const float m = s ? m1 : m0;
+      const long long M = s ? M1 : M0;
+      const int64_t* ro_s = roff + s * nrow * (bk.RX + 1);
+      for (int row = 0; row < nrow; ++row) {
+        const int64_t* ro = ro_s + row * (bk.RX + 1);
+        const int iy = cb.iy0 + row % bk.RY, iz = cb.iz0 + row / bk.RY;
+        // A corrupt stream (flagged by the scan) may claim more particles than
+        // exist; never read past the caller's n records.
+        const int64_t p0 = ro[0] < cs.n ? ro[0] : cs.n;
+        const int64_t p1 = ro[bk.RX] < cs.n ? ro[bk.RX] : cs.n;
+        const int64_t rounds = (p1 - p0 + blockDim.x - 1) / blockDim.x;
+        for (int64_t it = 0; it < rounds; ++it) {
+          const int64_t p = p0 + it * blockDim.x + threadIdx.x;
+          const bool live = p < p1;
+          int ixl = 0;
+          float px = 0.f, py = 0.f, pz = 0.f;
           if (live) {
-            const float sc_inv = 1.0f / (float)g.rc;
-            float ux = __fmul_rn(px, sc_inv), uy = __fmul_rn(py, sc_inv), uz = __fmul_rn(pz, sc_inv);
-            float v1[3] = {__fsub_rn(ux, floorf(ux)), __fsub_rn(uy, floorf(uy)), __fsub_rn(uz, floorf(uz))};
-            corner_masses(m, M, v1, cv);
-          } else {
-#pragma unroll
-            for (int c = 0; c < 8; ++c) cv[c] = (Acc)0;
-          }
-          const unsigned key = live ? (unsigned)ixl : 0xffffffffu;
-          if (run_reduce<8, Acc>(key, cv) && live) {
-            const int kx = ixl, ky = row % bk.RY, kz = row / bk.RY;
+            ixl = row_cell(ro, bk.RX, p);
+            int q[3];
+            unpack_pos(cs.pos[p], q);
+            px = decode_pos(cb.ix0 + ixl, q[0], pscale);
+            py = decode_pos(iy, q[1], pscale);
+            pz = decode_pos(iz, q[2], pscale);
+            // fine CIC in local region coordinates (no wrap inside the block)
+            float flx = floorf(px), fly = floorf(py), flz = floorf(pz);
+            int lx = (int)flx - bxf, ly = (int)fly - byf, lz = (int)flz - bzf;
+            float w1[3] = {__fsub_rn(px, flx), __fsub_rn(py, fly), __fsub_rn(pz, flz)};
+            Acc t8[8];
+            corner_masses(m, M, w1, t8);
 #pragma unroll
             for (int c = 0; c < 8; ++c) {
               int dx = c & 1, dy = (c >> 1) & 1, dz = c >> 2;
-              smem_acc(&sc[((kz + dz) * cy + (ky + dy)) * cx + (kx + dx)], cv[c]);
+              smem_acc(&sf[((lz + dz) * fy + (ly + dy)) * fx + (lx + dx)], t8[c]);
+            }
+          }
+          if (g.two) {
+            // Coarse cell == compression cell (coarse_ratio == cmp_ratio), so every
+            // particle of a run shares its 8 coarse corners: sum the run in
+            // registers and let its last lane do 8 shared-memory adds.
+            Acc cv[8];
+            if (live) {
+              const float sc_inv = 1.0f / (float)g.rc;
+              float ux = __fmul_rn(px, sc_inv), uy = __fmul_rn(py, sc_inv), uz = __fmul_rn(pz, sc_inv);
+              float v1[3] = {__fsub_rn(ux, floorf(ux)), __fsub_rn(uy, floorf(uy)), __fsub_rn(uz, floorf(uz))};
+              corner_masses(m, M, v1, cv);
+            } else {
+#pragma unroll
+              for (int c = 0; c < 8; ++c) cv[c] = (Acc)0;
+            }
+            const unsigned key = live ? (unsigned)ixl : 0xffffffffu;
+            if (run_reduce<8, Acc>(key, cv) && live) {
+              const int kx = ixl, ky = row % bk.RY, kz = row / bk.RY;
+#pragma unroll
+              for (int c = 0; c < 8; ++c) {
+                int dx = c & 1, dy = (c >> 1) & 1, dz = c >> 2;
+                smem_acc(&sc[((kz + dz) * cy + (ky + dy)) * cx + (kx + dx)], cv[c]);
+              }
             }
           }
         }
       }
     }
-  }
-  __syncthreads();
-  const int nf = g.nf;
-  for (int i = threadIdx.x; i < nsf; i += blockDim.x) {
-    Acc val = sf[i];
-    if (val == (Acc)0) continue;
-    int lx = i % fx, ly = (i / fx) % fy, lz = i / (fx * fy);
-    int gx = bxf + lx, gy = byf + ly, gz = bzf + lz;
-    if (gx >= nf) gx -= nf;
-    if (gy >= nf) gy -= nf;
-    if (gz >= nf) gz -= nf;
-    global_add(&rho_f[((int64_t)gz * nf + gy) * nf + gx], val);
-  }
-  const int nc = g.nc;
-  for (int i = threadIdx.x; i < nsc; i += blockDim.x) {
-    Acc val = sc[i];
-    if (val == (Acc)0) continue;
-    int lx = i % cx, ly = (i / cx) % cy, lz = i / (cx * cy);
-    int gx = cb.ix0 + lx, gy = cb.iy0 + ly, gz = cb.iz0 + lz;
-    if (gx >= nc) gx -= nc;
-    if (gy >= nc) gy -= nc;
-    if (gz >= nc) gz -= nc;
-    global_add(&rho_c[((int64_t)gz * nc + gy) * nc + gx], val);
-  }
+    __syncthreads();
+    const int nf = g.nf;
+    // flush: one warp per region row (z, y), lanes along x
+    for (int line = threadIdx.x >> 5; line < fy * fz; line += blockDim.x >> 5) {
+      const int lz = line / fy, ly = line - lz * fy;
+      int gy = byf + ly, gz = bzf + lz;
+      if (gy >= nf) gy -= nf;
+      if (gz >= nf) gz -= nf;
+      Acc* grow = rho_f + ((int64_t)gz * nf + gy) * nf;
+      const Acc* srow = sf + line * fx;
+      for (int lx = threadIdx.x & 31; lx < fx; lx += 32) {
+        const Acc val = srow[lx];
+        if (val == (Acc)0) continue;
+        int gx = bxf + lx;
+        if (gx >= nf) gx -= nf;
+        global_add(grow + gx, val);
+      }
+    }
+    const int nc = g.nc;
+    for (int i = threadIdx.x; i < nsc; i += blockDim.x) {
+      Acc val = sc[i];
+      if (val == (Acc)0) continue;
+      int lx = i % cx, ly = (i / cx) % cy, lz = i / (cx * cy);
+      int gx = cb.ix0 + lx, gy = cb.iy0 + ly, gz = cb.iz0 + lz;
+      if (gx >= nc) gx -= nc;
+      if (gy >= nc) gy -= nc;
+      if (gz >= nc) gz -= nc;
+      global_add(&rho_c[((int64_t)gz * nc + gy) * nc + gx], val);
+    }
+  });
 }
 
 // Window of destination compression cells owned by a cell block's histogram:
@@ -839,14 +871,19 @@ __device__ __forceinline__ int window_slot_xyz(const Win& w, int n, int cx, int 
 // cell lies in the block's window, else the new cell index itself.
 constexpr uint32_t kInWindow = 0x80000000u;
 
-__device__ __forceinline__ uint32_t window_cell(const Geo& g, const Win& w, int slot) {
+// Cell index of window row r = lz wy + ly at x = 0 (add window_x for the column).
+__device__ __forceinline__ uint32_t window_row(const Geo& g, const Win& w, int r) {
   const int n = g.ncmp;
-  int lx = slot % w.wx, ly = (slot / w.wx) % w.wy, lz = slot / (w.wx * w.wy);
-  int cx = w.ox + lx, cy = w.oy + ly, cz = w.oz + lz;
-  if (cx < 0) cx += n; else if (cx >= n) cx -= n;
+  const int lz = r / w.wy, ly = r - lz * w.wy;
+  int cy = w.oy + ly, cz = w.oz + lz;
   if (cy < 0) cy += n; else if (cy >= n) cy -= n;
   if (cz < 0) cz += n; else if (cz >= n) cz -= n;
-  return (uint32_t)(cx + n * (cy + n * cz));
+  return (uint32_t)(n * (cy + n * cz));
+}
+__device__ __forceinline__ uint32_t window_x(const Geo& g, const Win& w, int lx) {
+  int cx = w.ox + lx;
+  if (cx < 0) cx += g.ncmp; else if (cx >= g.ncmp) cx -= g.ncmp;
+  return (uint32_t)cx;
 }
 
 // Pass 1 of interpolate + kick + drift + recompress, both species of one cell
@@ -862,140 +899,150 @@ __global__ void __launch_bounds__(512, 2) k_ikd_count(PCodes c0, PCodes c1, cons
                             uint32_t* counts1, uint32_t* vmax_bits, uint32_t* tkey, uint4* tpv,
                             const float* vq0, const float* vq1) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  const int r = g.rcmp;
-  const int nrow = bk.RY * bk.RZ;
-  const int fx = bk.RX * r + 1, fy = bk.RY * r + 1, fz = bk.RZ * r + 1;
-  const int cx = bk.RX + 1, cy = bk.RY + 1, cz = bk.RZ + 1;
-  const CellBlock cb = block_of(bk, blockIdx.x);
-  const Win win = window_of(g, bk, cb);
-  const int W = win.wx * win.wy * win.wz;
-  int64_t* roff = reinterpret_cast<int64_t*>(smraw);
-  uint32_t* hist = reinterpret_cast<uint32_t*>(roff + 2 * nrow * (bk.RX + 1));
-  float* sf = reinterpret_cast<float*>(hist + 2 * W);
-  float* sc = sf + 3 * fx * fy * fz;
-  load_row_offsets(off0, g, bk, cb, roff);
-  load_row_offsets(off1, g, bk, cb, roff + nrow * (bk.RX + 1));
-  for (int i = threadIdx.x; i < 2 * W; i += blockDim.x) hist[i] = 0;
-  const int bxf = cb.ix0 * r, byf = cb.iy0 * r, bzf = cb.iz0 * r;
-  {
-    const int nf = g.nf;
-    const int64_t nf3 = (int64_t)nf * nf * nf;
-    const int lines = 3 * fz * fy;
-    for (int li = threadIdx.x >> 5; li < lines; li += blockDim.x >> 5) {
-      int comp = li / (fz * fy), rem = li - comp * fz * fy;
-      int lz = rem / fy, ly = rem - lz * fy;
-      int gz = bzf + lz, gy = byf + ly;
-      if (gz >= nf) gz -= nf;
-      if (gy >= nf) gy -= nf;
-      const float* src = acc_f + comp * nf3 + ((int64_t)gz * nf + gy) * nf;
-      float* dst = sf + (int64_t)li * fx;
-      for (int lx = threadIdx.x & 31; lx < fx; lx += 32) {
-        int gx = bxf + lx;
-        if (gx >= nf) gx -= nf;
-        dst[lx] = __ldg(src + gx);
+  for_each_block(bk, [&](const int bid) {
+    const int r = g.rcmp;
+    const int nrow = bk.RY * bk.RZ;
+    const int fx = bk.RX * r + 1, fy = bk.RY * r + 1, fz = bk.RZ * r + 1;
+    const int cx = bk.RX + 1, cy = bk.RY + 1, cz = bk.RZ + 1;
+    const CellBlock cb = block_of(bk, bid);
+    const Win win = window_of(g, bk, cb);
+    const int W = win.wx * win.wy * win.wz;
+    int64_t* roff = reinterpret_cast<int64_t*>(smraw);
+    uint32_t* hist = reinterpret_cast<uint32_t*>(roff + 2 * nrow * (bk.RX + 1));
+    float* sf = reinterpret_cast<float*>(hist + 2 * W);
+    float* sc = sf + 3 * fx * fy * fz;
+    load_row_offsets(off0, g, bk, cb, roff);
+    load_row_offsets(off1, g, bk, cb, roff + nrow * (bk.RX + 1));
+    for (int i = threadIdx.x; i < 2 * W; i += blockDim.x) hist[i] = 0;
+    const int bxf = cb.ix0 * r, byf = cb.iy0 * r, bzf = cb.iz0 * r;
+    {
+      const int nf = g.nf;
+      const int64_t nf3 = (int64_t)nf * nf * nf;
+      const int lines = 3 * fz * fy;
+      for (int li = threadIdx.x >> 5; li < lines; li += blockDim.x >> 5) {
+        int comp = li / (fz * fy), rem = li - comp * fz * fy;
+        int lz = rem / fy, ly = rem - lz * fy;
+        int gz = bzf + lz, gy = byf + ly;
+        if (gz >= nf) gz -= nf;
+        if (gy >= nf) gy -= nf;
+        const float* src = acc_f + comp * nf3 + ((int64_t)gz * nf + gy) * nf;
+        float* dst = sf + (int64_t)li * fx;
+        for (int lx = threadIdx.x & 31; lx < fx; lx += 32) {
+          int gx = bxf + lx;
+          if (gx >= nf) gx -= nf;
+          dst[lx] = __ldg(src + gx);
+        }
+      }
+      if (g.two) {
+        const int nc = g.nc;
+        const int64_t nc3 = (int64_t)nc * nc * nc;
+        for (int i = threadIdx.x; i < 3 * cx * cy * cz; i += blockDim.x) {
+          int comp = i / (cx * cy * cz), rem = i - comp * cx * cy * cz;
+          int lz = rem / (cx * cy), rem2 = rem - lz * cx * cy;
+          int ly = rem2 / cx, lx = rem2 - ly * cx;
+          int gx = cb.ix0 + lx, gy = cb.iy0 + ly, gz = cb.iz0 + lz;
+          if (gx >= nc) gx -= nc;
+          if (gy >= nc) gy -= nc;
+          if (gz >= nc) gz -= nc;
+          sc[i] = __ldg(acc_c + comp * nc3 + ((int64_t)gz * nc + gy) * nc + gx);
+        }
       }
     }
-    if (g.two) {
-      const int nc = g.nc;
-      const int64_t nc3 = (int64_t)nc * nc * nc;
-      for (int i = threadIdx.x; i < 3 * cx * cy * cz; i += blockDim.x) {
-        int comp = i / (cx * cy * cz), rem = i - comp * cx * cy * cz;
-        int lz = rem / (cx * cy), rem2 = rem - lz * cx * cy;
-        int ly = rem2 / cx, lx = rem2 - ly * cx;
-        int gx = cb.ix0 + lx, gy = cb.iy0 + ly, gz = cb.iz0 + lz;
-        if (gx >= nc) gx -= nc;
-        if (gy >= nc) gy -= nc;
-        if (gz >= nc) gz -= nc;
-        sc[i] = __ldg(acc_c + comp * nc3 + ((int64_t)gz * nc + gy) * nc + gx);
+    __syncthreads();
+    const float pscale = (float)r / 256.0f;
+    const float inv_r = 1.0f / (float)r;
+    const float nf = (float)g.nf;
+    for (int s = 0; s < 2; ++s) {
+      const PCodes& in = s ? c1 : c0;
+      uint32_t* counts = s ? counts1 : counts0;
+      uint32_t* hs = hist + s * W;
+      const int64_t toff = s ? c0.n : 0;
+      const int half = in.vel16 ? 32768 : 128;
+      const float step = __fmul_rn(*in.vmax, 1.0f / (float)half);
+      float local_max = 0.f;
+      // v_max' known before the pass (bound mode): quantise here, the scatter copies codes
+      const float* vq = s ? vq1 : vq0;
+      const bool coded = vq != nullptr;
+      const float vqm = coded ? *vq : 0.f;
+      const bool qzero = !(vqm > 0.f);
+      const float qs = (coded && !qzero) ? __fdiv_rn(in.vel16 ? 32768.0f : 128.0f, vqm) : 0.f;
+      const int64_t* ro_s = roff + s * nrow * (bk.RX + 1);
+      for (int row = 0; row < nrow; ++row) {
+        const int64_t* ro = ro_s + row * (bk.RX + 1);
+        const int iy = cb.iy0 + row % bk.RY, iz = cb.iz0 + row / bk.RY;
+        const int64_t p0 = ro[0] < in.n ? ro[0] : in.n;
+        const int64_t p1 = ro[bk.RX] < in.n ? ro[bk.RX] : in.n;
+        for (int64_t p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
+          const int ixl = row_cell(ro, bk.RX, p);
+          int q[3], qv[3];
+          unpack_pos(in.pos[p], q);
+          load_vel(in.vel, in.vel16, p, qv);
+          float x[3], v[3], a[3];
+          x[0] = decode_pos(cb.ix0 + ixl, q[0], pscale);
+          x[1] = decode_pos(iy, q[1], pscale);
+          x[2] = decode_pos(iz, q[2], pscale);
+#pragma unroll
+          for (int d = 0; d < 3; ++d) v[d] = decode_vel(qv[d], half, step);
+          // Decoded positions are exact dyadics, so the CIC cell and weight come
+          // from the codes in integer arithmetic: x = c r + (2q + 1) r / 512.
+          const int ky = row % bk.RY, kz = row / bk.RY;
+          int num[3];
+          float w1[3];
+#pragma unroll
+          for (int d = 0; d < 3; ++d) {
+            num[d] = (2 * q[d] + 1) * r;
+            w1[d] = __fmul_rn(__int2float_rn(num[d] & 511), 1.0f / 512.0f);
+          }
+          gather_idx(sf, fx, fy, fz, ixl * r + (num[0] >> 9), ky * r + (num[1] >> 9), kz * r + (num[2] >> 9), w1, a);
+          if (g.two) {
+            // coarse cell == compression cell: corner (ixl, ky, kz), weight (2q + 1) / 512
+            float b[3], u1[3];
+#pragma unroll
+            for (int d = 0; d < 3; ++d) u1[d] = __fmul_rn(__int2float_rn(2 * q[d] + 1), 1.0f / 512.0f);
+            gather_idx(sc, cx, cy, cz, ixl, ky, kz, u1, b);
+            a[0] = __fadd_rn(b[0], a[0]);
+            a[1] = __fadd_rn(b[1], a[1]);
+            a[2] = __fadd_rn(b[2], a[2]);
+          }
+          kick_drift(x, v, a, ck, cd, nf);
+          int cc[3], qq[3];
+#pragma unroll
+          for (int d = 0; d < 3; ++d) encode_pos(x[d], inv_r, g.ncmp, cc[d], qq[d]);
+          const uint32_t key = (uint32_t)(cc[0] + g.ncmp * (cc[1] + g.ncmp * cc[2]));
+          const int slot = window_slot_xyz(win, g.ncmp, cc[0], cc[1], cc[2]);
+          const int64_t t = toff + p;
+          tkey[t] = slot >= 0 ? (kInWindow | (uint32_t)slot) : key;
+          const uint32_t pw = (uint32_t)qq[0] | ((uint32_t)qq[1] << 8) | ((uint32_t)qq[2] << 16);
+          if (coded) {
+            int c3[3];
+#pragma unroll
+            for (int d = 0; d < 3; ++d) c3[d] = encode_vel(v[d], qs, half, qzero);
+            tpv[t] = in.vel16 ? make_uint4(pw, (uint32_t)c3[0] | ((uint32_t)c3[1] << 16), (uint32_t)c3[2], 0u)
+                              : make_uint4(pw, (uint32_t)c3[0] | ((uint32_t)c3[1] << 8) | ((uint32_t)c3[2] << 16), 0u, 0u);
+          } else {
+            tpv[t] = make_uint4(pw, __float_as_uint(v[0]), __float_as_uint(v[1]), __float_as_uint(v[2]));
+            local_max = fmaxf(local_max, fmaxf(fabsf(v[0]), fmaxf(fabsf(v[1]), fabsf(v[2]))));
+          }
+          if (slot >= 0) atomicAdd(hs + slot, 1u);
+          else atomicAdd(counts + key, 1u);
+        }
+      }
+      if (!coded) block_vmax(local_max, vmax_bits + s);
+    }
+    __syncthreads();
+    // flush: one warp per window row (species, z, y), lanes along x
+    const int wyz = win.wy * win.wz;
+    for (int rw = threadIdx.x >> 5; rw < 2 * wyz; rw += blockDim.x >> 5) {
+      const int sp = rw >= wyz ? 1 : 0;
+      const uint32_t rowcell = window_row(g, win, rw - sp * wyz);
+      const uint32_t* hrow = hist + sp * W + (rw - sp * wyz) * win.wx;
+      uint32_t* cnt = sp ? counts1 : counts0;
+      for (int lx = threadIdx.x & 31; lx < win.wx; lx += 32) {
+        const uint32_t k = hrow[lx];
+        if (k) atomicAdd(cnt + rowcell + window_x(g, win, lx), k);
       }
     }
-  }
-  __syncthreads();
-  const float pscale = (float)r / 256.0f;
-  const float inv_r = 1.0f / (float)r;
-  const float nf = (float)g.nf;
-  for (int s = 0; s < 2; ++s) {
-    const PCodes& in = s ? c1 : c0;
-    uint32_t* counts = s ? counts1 : counts0;
-    uint32_t* hs = hist + s * W;
-    const int64_t toff = s ? c0.n : 0;
-    const int half = in.vel16 ? 32768 : 128;
-    const float step = __fmul_rn(*in.vmax, 1.0f / (float)half);
-    float local_max = 0.f;
-    // v_max' known before the pass (bound mode): quantise here, the scatter copies codes
-    const float* vq = s ? vq1 : vq0;
-    const bool coded = vq != nullptr;
-    const float vqm = coded ? *vq : 0.f;
-    const bool qzero = !(vqm > 0.f);
-    const float qs = (coded && !qzero) ? __fdiv_rn(in.vel16 ? 32768.0f : 128.0f, vqm) : 0.f;
-    const int64_t* ro_s = roff + s * nrow * (bk.RX + 1);
-    for (int row = 0; row < nrow; ++row) {
-      const int64_t* ro = ro_s + row * (bk.RX + 1);
-      const int iy = cb.iy0 + row % bk.RY, iz = cb.iz0 + row / bk.RY;
-      const int64_t p0 = ro[0] < in.n ? ro[0] : in.n;
-      const int64_t p1 = ro[bk.RX] < in.n ? ro[bk.RX] : in.n;
-      for (int64_t p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
-        const int ixl = row_cell(ro, bk.RX, p);
-        int q[3], qv[3];
-        unpack_pos(in.pos[p], q);
-        load_vel(in.vel, in.vel16, p, qv);
-        float x[3], v[3], a[3];
-        x[0] = decode_pos(cb.ix0 + ixl, q[0], pscale);
-        x[1] = decode_pos(iy, q[1], pscale);
-        x[2] = decode_pos(iz, q[2], pscale);
-#pragma unroll
-        for (int d = 0; d < 3; ++d) v[d] = decode_vel(qv[d], half, step);
-        // Decoded positions are exact dyadics, so the CIC cell and weight come
-        // from the codes in integer arithmetic: x = c r + (2q + 1) r / 512.
-        const int ky = row % bk.RY, kz = row / bk.RY;
-        int num[3];
-        float w1[3];
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-          num[d] = (2 * q[d] + 1) * r;
-          w1[d] = __fmul_rn(__int2float_rn(num[d] & 511), 1.0f / 512.0f);
-        }
-        gather_idx(sf, fx, fy, fz, ixl * r + (num[0] >> 9), ky * r + (num[1] >> 9), kz * r + (num[2] >> 9), w1, a);
-        if (g.two) {
-          // coarse cell == compression cell: corner (ixl, ky, kz), weight (2q + 1) / 512
-          float b[3], u1[3];
-#pragma unroll
-          for (int d = 0; d < 3; ++d) u1[d] = __fmul_rn(__int2float_rn(2 * q[d] + 1), 1.0f / 512.0f);
-          gather_idx(sc, cx, cy, cz, ixl, ky, kz, u1, b);
-          a[0] = __fadd_rn(b[0], a[0]);
-          a[1] = __fadd_rn(b[1], a[1]);
-          a[2] = __fadd_rn(b[2], a[2]);
-        }
-        kick_drift(x, v, a, ck, cd, nf);
-        int cc[3], qq[3];
-#pragma unroll
-        for (int d = 0; d < 3; ++d) encode_pos(x[d], inv_r, g.ncmp, cc[d], qq[d]);
-        const uint32_t key = (uint32_t)(cc[0] + g.ncmp * (cc[1] + g.ncmp * cc[2]));
-        const int slot = window_slot_xyz(win, g.ncmp, cc[0], cc[1], cc[2]);
-        const int64_t t = toff + p;
-        tkey[t] = slot >= 0 ? (kInWindow | (uint32_t)slot) : key;
-        const uint32_t pw = (uint32_t)qq[0] | ((uint32_t)qq[1] << 8) | ((uint32_t)qq[2] << 16);
-        if (coded) {
-          int c3[3];
-#pragma unroll
-          for (int d = 0; d < 3; ++d) c3[d] = encode_vel(v[d], qs, half, qzero);
-          tpv[t] = in.vel16 ? make_uint4(pw, (uint32_t)c3[0] | ((uint32_t)c3[1] << 16), (uint32_t)c3[2], 0u)
-                            : make_uint4(pw, (uint32_t)c3[0] | ((uint32_t)c3[1] << 8) | ((uint32_t)c3[2] << 16), 0u, 0u);
-        } else {
-          tpv[t] = make_uint4(pw, __float_as_uint(v[0]), __float_as_uint(v[1]), __float_as_uint(v[2]));
-          local_max = fmaxf(local_max, fmaxf(fabsf(v[0]), fmaxf(fabsf(v[1]), fabsf(v[2]))));
-        }
-        if (slot >= 0) atomicAdd(hs + slot, 1u);
-        else atomicAdd(counts + key, 1u);
-      }
-    }
-    if (!coded) block_vmax(local_max, vmax_bits + s);
-  }
-  __syncthreads();
-  for (int i = threadIdx.x; i < 2 * W; i += blockDim.x) {
-    uint32_t k = hist[i];
-    if (k) atomicAdd((i < W ? counts0 : counts1) + window_cell(g, win, i < W ? i : i - W), k);
-  }
+  });
 }
 
 // Pass 2: place every particle of a cell block in its new cell.  Phase 1
@@ -1009,98 +1056,105 @@ __global__ void __launch_bounds__(512, 2) k_ikd_scatter(int64_t n0, int64_t n1, 
                               PCodesOut o0, PCodesOut o1, const uint32_t* tkey, const uint4* tpv, int coded,
                               int* status) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  const int nrow = bk.RY * bk.RZ;
-  const CellBlock cb = block_of(bk, blockIdx.x);
-  const Win win = window_of(g, bk, cb);
-  const int W = win.wx * win.wy * win.wz;
-  int64_t* roff = reinterpret_cast<int64_t*>(smraw);
-  unsigned long long* base = reinterpret_cast<unsigned long long*>(roff + 2 * nrow * (bk.RX + 1));
-  uint32_t* hist = reinterpret_cast<uint32_t*>(base + 2 * W);
-  load_row_offsets(off0, g, bk, cb, roff);
-  load_row_offsets(off1, g, bk, cb, roff + nrow * (bk.RX + 1));
-  for (int i = threadIdx.x; i < 2 * W; i += blockDim.x) hist[i] = 0;
-  __syncthreads();
-  for (int s = 0; s < 2; ++s) {
-    const int64_t n = s ? n1 : n0;
-    const int64_t toff = s ? n0 : 0;
-    for (int row = 0; row < nrow; ++row) {
-      const int64_t* ro = roff + (s * nrow + row) * (bk.RX + 1);
-      const int64_t p0 = ro[0] < n ? ro[0] : n, p1 = ro[bk.RX] < n ? ro[bk.RX] : n;
-      for (int64_t p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
-        const uint32_t tk = tkey[toff + p];
-        if (tk & kInWindow) atomicAdd(hist + s * W + (tk & ~kInWindow), 1u);
-      }
-    }
-  }
-  __syncthreads();
-  for (int i = threadIdx.x; i < 2 * W; i += blockDim.x) {
-    uint32_t k = hist[i];
-    if (!k) continue;
-    const int s = i < W ? 0 : 1;
-    const uint32_t cell = window_cell(g, win, i - s * W);
-    uint32_t* counts = s ? counts1 : counts0;
-    const int64_t* newoff = s ? newoff1 : newoff0;
-    uint32_t top = atomicSub(counts + cell, k);
-    base[i] = (unsigned long long)(newoff[cell] + (int64_t)top - (int64_t)k);
-  }
-  __syncthreads();
-  for (int s = 0; s < 2; ++s) {
-    const int64_t n = s ? n1 : n0;
-    const int64_t toff = s ? n0 : 0;
-    const PCodesOut& o = s ? o1 : o0;
-    uint32_t* counts = s ? counts1 : counts0;
-    const int64_t* newoff = s ? newoff1 : newoff0;
-    const int half = o.vel16 ? 32768 : 128;
-    const float vm = *o.vmax;
-    const bool vzero = !(vm > 0.f);
-    const float sv = vzero ? 0.f : __fdiv_rn(o.vel16 ? 32768.0f : 128.0f, vm);
-    for (int row = 0; row < nrow; ++row) {
-      const int64_t* ro = roff + (s * nrow + row) * (bk.RX + 1);
-      const int64_t p0 = ro[0] < n ? ro[0] : n, p1 = ro[bk.RX] < n ? ro[bk.RX] : n;
-      // Two particles per thread per iteration keep more independent loads in flight.
-      for (int64_t p = p0 + threadIdx.x; p < p1; p += 2 * blockDim.x) {
-        const int64_t pp[2] = {p, p + blockDim.x};
-        uint32_t tk[2];
-        uint4 pv[2];
-#pragma unroll
-        for (int u = 0; u < 2; ++u) {
-          if (pp[u] < p1) {
-            tk[u] = tkey[toff + pp[u]];
-            pv[u] = tpv[toff + pp[u]];
-          }
-        }
-#pragma unroll
-        for (int u = 0; u < 2; ++u) {
-          if (pp[u] >= p1) continue;
-          int64_t dst;
-          if (tk[u] & kInWindow) {
-            dst = (int64_t)atomicAdd(base + s * W + (tk[u] & ~kInWindow), 1ull);
-          } else {
-            const uint32_t top = atomicSub(counts + tk[u], 1u);
-            dst = newoff[tk[u]] + (int64_t)top - 1;
-          }
-          if (dst < 0 || dst >= n) {
-            atomicOr(status, ST_CORRUPT);
-            continue;
-          }
-          o.pos[dst] = pv[u].x;
-          if (coded) {
-            if (o.vel16)
-              reinterpret_cast<unsigned long long*>(o.vel)[dst] =
-                  (unsigned long long)pv[u].y | ((unsigned long long)pv[u].z << 32);
-            else
-              reinterpret_cast<uint32_t*>(o.vel)[dst] = pv[u].y;
-            continue;
-          }
-          int qv[3];
-          qv[0] = encode_vel(__uint_as_float(pv[u].y), sv, half, vzero);
-          qv[1] = encode_vel(__uint_as_float(pv[u].z), sv, half, vzero);
-          qv[2] = encode_vel(__uint_as_float(pv[u].w), sv, half, vzero);
-          store_vel(o.vel, o.vel16, dst, qv);
+  for_each_block(bk, [&](const int bid) {
+    const int nrow = bk.RY * bk.RZ;
+    const CellBlock cb = block_of(bk, bid);
+    const Win win = window_of(g, bk, cb);
+    const int W = win.wx * win.wy * win.wz;
+    int64_t* roff = reinterpret_cast<int64_t*>(smraw);
+    unsigned long long* base = reinterpret_cast<unsigned long long*>(roff + 2 * nrow * (bk.RX + 1));
+    uint32_t* hist = reinterpret_cast<uint32_t*>(base + 2 * W);
+    load_row_offsets(off0, g, bk, cb, roff);
+    load_row_offsets(off1, g, bk, cb, roff + nrow * (bk.RX + 1));
+    for (int i = threadIdx.x; i < 2 * W; i += blockDim.x) hist[i] = 0;
+    __syncthreads();
+    for (int s = 0; s < 2; ++s) {
+      const int64_t n = s ? n1 : n0;
+      const int64_t toff = s ? n0 : 0;
+      for (int row = 0; row < nrow; ++row) {
+        const int64_t* ro = roff + (s * nrow + row) * (bk.RX + 1);
+        const int64_t p0 = ro[0] < n ? ro[0] : n, p1 = ro[bk.RX] < n ? ro[bk.RX] : n;
+        for (int64_t p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
+          const uint32_t tk = tkey[toff + p];
+          if (tk & kInWindow) atomicAdd(hist + s * W + (tk & ~kInWindow), 1u);
         }
       }
     }
-  }
+    __syncthreads();
+    const int wyz = win.wy * win.wz;
+    for (int rw = threadIdx.x >> 5; rw < 2 * wyz; rw += blockDim.x >> 5) {
+      const int sp = rw >= wyz ? 1 : 0;
+      const uint32_t rowcell = window_row(g, win, rw - sp * wyz);
+      const int i0 = sp * W + (rw - sp * wyz) * win.wx;
+      uint32_t* counts = sp ? counts1 : counts0;
+      const int64_t* newoff = sp ? newoff1 : newoff0;
+      for (int lx = threadIdx.x & 31; lx < win.wx; lx += 32) {
+        const uint32_t k = hist[i0 + lx];
+        if (!k) continue;
+        const uint32_t cell = rowcell + window_x(g, win, lx);
+        const uint32_t top = atomicSub(counts + cell, k);
+        base[i0 + lx] = (unsigned long long)(newoff[cell] + (int64_t)top - (int64_t)k);
+      }
+    }
+    __syncthreads();
+    for (int s = 0; s < 2; ++s) {
+      const int64_t n = s ? n1 : n0;
+      const int64_t toff = s ? n0 : 0;
+      const PCodesOut& o = s ? o1 : o0;
+      uint32_t* counts = s ? counts1 : counts0;
+      const int64_t* newoff = s ? newoff1 : newoff0;
+      const int half = o.vel16 ? 32768 : 128;
+      const float vm = *o.vmax;
+      const bool vzero = !(vm > 0.f);
+      const float sv = vzero ? 0.f : __fdiv_rn(o.vel16 ? 32768.0f : 128.0f, vm);
+      for (int row = 0; row < nrow; ++row) {
+        const int64_t* ro = roff + (s * nrow + row) * (bk.RX + 1);
+        const int64_t p0 = ro[0] < n ? ro[0] : n, p1 = ro[bk.RX] < n ? ro[bk.RX] : n;
+        // Two particles per thread per iteration keep more independent loads in flight.
+        for (int64_t p = p0 + threadIdx.x; p < p1; p += 2 * blockDim.x) {
+          const int64_t pp[2] = {p, p + blockDim.x};
+          uint32_t tk[2];
+          uint4 pv[2];
+#pragma unroll
+          for (int u = 0; u < 2; ++u) {
+            if (pp[u] < p1) {
+              tk[u] = tkey[toff + pp[u]];
+              pv[u] = tpv[toff + pp[u]];
+            }
+          }
+#pragma unroll
+          for (int u = 0; u < 2; ++u) {
+            if (pp[u] >= p1) continue;
+            int64_t dst;
+            if (tk[u] & kInWindow) {
+              dst = (int64_t)atomicAdd(base + s * W + (tk[u] & ~kInWindow), 1ull);
+            } else {
+              const uint32_t top = atomicSub(counts + tk[u], 1u);
+              dst = newoff[tk[u]] + (int64_t)top - 1;
+            }
+            if (dst < 0 || dst >= n) {
+              atomicOr(status, ST_CORRUPT);
+              continue;
+            }
+            o.pos[dst] = pv[u].x;
+            if (coded) {
+              if (o.vel16)
+                reinterpret_cast<unsigned long long*>(o.vel)[dst] =
+                    (unsigned long long)pv[u].y | ((unsigned long long)pv[u].z << 32);
+              else
+                reinterpret_cast<uint32_t*>(o.vel)[dst] = pv[u].y;
+              continue;
+            }
+            int qv[3];
+            qv[0] = encode_vel(__uint_as_float(pv[u].y), sv, half, vzero);
+            qv[1] = encode_vel(__uint_as_float(pv[u].z), sv, half, vzero);
+            qv[2] = encode_vel(__uint_as_float(pv[u].w), sv, half, vzero);
+            store_vel(o.vel, o.vel16, dst, qv);
+          }
+        }
+      }
+    }
+  });
 }
 
 // ------------------------------------------------------------ launchers --
@@ -1192,6 +1246,20 @@ size_t deposit_codes_smem(const Geo& g, const Blk& bk, bool fixed) {
   return 2 * nrow * (bk.RX + 1) * sizeof(int64_t) + (fine + coarse) * (fixed ? 8 : 4);
 }
 
+// Grid of a cell-block launch: one CTA per block, or (bk.work set) as many
+// CTAs as fit on the device at once, capped by the block count.
+template <class K>
+static int block_grid(K kernel, const Blk& bk, int threads, size_t smem) {
+  const int nblk = bk.nbx * bk.nby * bk.nbz;
+  if (!bk.work) return nblk;
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem);
+  const long long resident = (long long)(per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
+  return (int)(resident < nblk ? resident : nblk);
+}
+
 cudaError_t launch_deposit_codes(const PCodes& c0, const PCodes& c1, const int64_t* off0, const int64_t* off1,
                                  const Geo& g, const Blk& bk, float m0, float m1, long long M0, long long M1,
                                  void* rho_c, void* rho_f, bool fixed, cudaStream_t st) {
@@ -1199,10 +1267,12 @@ cudaError_t launch_deposit_codes(const PCodes& c0, const PCodes& c1, const int64
   int nblk = bk.nbx * bk.nby * bk.nbz;
   if (fixed) {
     cudaFuncSetAttribute(k_deposit_codes<long long>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    nblk = block_grid(k_deposit_codes<long long>, bk, 256, smem);
     k_deposit_codes<long long><<<nblk, 256, smem, st>>>(c0, c1, off0, off1, g, bk, m0, m1, M0, M1,
                                                        static_cast<long long*>(rho_c), static_cast<long long*>(rho_f));
   } else {
     cudaFuncSetAttribute(k_deposit_codes<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    nblk = block_grid(k_deposit_codes<float>, bk, 256, smem);
     k_deposit_codes<float><<<nblk, 256, smem, st>>>(c0, c1, off0, off1, g, bk, m0, m1, M0, M1,
                                                    static_cast<float*>(rho_c), static_cast<float*>(rho_f));
   }
@@ -1217,6 +1287,7 @@ cudaError_t launch_ikd_count(const PCodes& c0, const PCodes& c1, const int64_t* 
   size_t smem = ikd_count_smem(g, bk);
   int nblk = bk.nbx * bk.nby * bk.nbz;
   cudaFuncSetAttribute(k_ikd_count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  nblk = block_grid(k_ikd_count, bk, 512, smem);
   k_ikd_count<<<nblk, 512, smem, st>>>(c0, c1, off0, off1, g, bk, acc_c, acc_f, ck, cd, counts0, counts1, vmax_bits,
                                        tkey, tpv, vq0, vq1);
   note_launches(1);
@@ -1230,6 +1301,7 @@ cudaError_t launch_ikd_scatter(int64_t n0, int64_t n1, const int64_t* off0, cons
   size_t smem = ikd_scatter_smem(g, bk);
   int nblk = bk.nbx * bk.nby * bk.nbz;
   cudaFuncSetAttribute(k_ikd_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  nblk = block_grid(k_ikd_scatter, bk, 512, smem);
   k_ikd_scatter<<<nblk, 512, smem, st>>>(n0, n1, off0, off1, g, bk, counts0, counts1, newoff0, newoff1, o0, o1, tkey,
                                          tpv, coded ? 1 : 0, status);
   note_launches(1);

@@ -19,6 +19,7 @@ struct Blk {
   int RX, RY, RZ;     // cells per block along x, y, z
   int nbx, nby, nbz;  // blocks along x, y, z
   int D;              // half-width (cells) of the new-cell histogram window
+  int* work;          // persistent launch: device counter of cell blocks taken (zeroed before the launch); null: one CTA per block
 };
 
 struct PCodes {

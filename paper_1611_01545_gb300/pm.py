@@ -13,7 +13,7 @@ from typing import Dict, Optional, Sequence, Tuple
 import torch
 
 from . import _lib
-from ._lib import pm_codes_t, pm_config_t, pm_particles_t
+from ._lib import pm_codes_t, pm_config_t, pm_particles_t, pm_tuning_t
 
 
 class PMError(RuntimeError):
@@ -253,6 +253,37 @@ class PM:
 
     def set_timing(self, on: bool):
         self._err(self.lib.pm_set_timing(self.h, 1 if on else 0))
+
+    @staticmethod
+    def _tuning_dict(t: pm_tuning_t) -> Dict:
+        return {"deposit_block": tuple(t.deposit_block), "deposit_persistent": t.deposit_persistent,
+                "kick_block": tuple(t.kick_block), "kick_window": t.kick_window,
+                "kick_persistent": t.kick_persistent, "tile_batch": t.tile_batch}
+
+    def get_tuning(self) -> Dict:
+        t = pm_tuning_t()
+        self._err(self.lib.pm_get_tuning(self.h, ctypes.byref(t)))
+        return self._tuning_dict(t)
+
+    def set_tuning(self, tuning: Dict):
+        t = pm_tuning_t()
+        self.lib.pm_get_tuning(self.h, ctypes.byref(t))
+        for k, v in tuning.items():
+            if k in ("deposit_block", "kick_block"):
+                getattr(t, k)[:] = [int(a) for a in v]
+            else:
+                setattr(t, k, int(v))
+        self._err(self.lib.pm_set_tuning(self.h, ctypes.byref(t)))
+
+    def autotune(self, codes_in: Sequence[Codes], codes_out: Sequence[Codes], c_kick: float, c_drift: float,
+                 reps: int = 2, stream=None) -> Dict:
+        """Time candidate launch tunings of step(codes_in -> codes_out) and keep the fastest."""
+        arr_in = (pm_codes_t * 2)(codes_in[0].struct(), codes_in[1].struct())
+        arr_out = (pm_codes_t * 2)(codes_out[0].struct(), codes_out[1].struct())
+        t = pm_tuning_t()
+        self._err(self.lib.pm_autotune(self.h, arr_in, arr_out, c_kick, c_drift, reps, _stream(stream),
+                                       ctypes.byref(t)))
+        return self._tuning_dict(t)
 
     def set_graphs(self, on: bool):
         """Replay step() as captured CUDA graphs (one per codes/c_k/c_d set)."""
