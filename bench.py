@@ -257,8 +257,10 @@ def run_gb300(args):
     def one_step():
         pm.step(a, b, 1.0, 1.0)
 
+    if args.tuning:
+        pm.set_tuning(json.loads(args.tuning))
     tuning = pm.get_tuning()
-    if not args.no_autotune:
+    if not args.no_autotune and not args.tuning:
         # launch tuning picked by timing candidate cell blocks / launch forms / tile batches
         tuning = pm.autotune(a, b, 1.0, 1.0, reps=2)
     # headline: the step replayed from a captured CUDA graph
@@ -519,6 +521,7 @@ def main():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-adjoint", action="store_true")
     p.add_argument("--no-autotune", action="store_true")
+    p.add_argument("--tuning", default="", help="launch tuning as JSON (as printed under 'tuning'); skips the autotuner")
     p.add_argument("--adjoint-workload", default="diff128")
     args = p.parse_args()
     res = run_reference(args) if args.impl == "reference" else run_gb300(args)
