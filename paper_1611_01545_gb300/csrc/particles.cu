@@ -1074,27 +1074,50 @@ __global__ void __launch_bounds__(512, 2) k_ikd_scatter(int64_t n0, int64_t n1, 
       for (int row = 0; row < nrow; ++row) {
         const int64_t* ro = roff + (s * nrow + row) * (bk.RX + 1);
         const int64_t p0 = ro[0] < n ? ro[0] : n, p1 = ro[bk.RX] < n ? ro[bk.RX] : n;
-        for (int64_t p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
-          const uint32_t tk = tkey[toff + p];
-          if (tk & kInWindow) atomicAdd(hist + s * W + (tk & ~kInWindow), 1u);
+        // four keys per thread loaded before any is counted
+        for (int64_t p = p0 + threadIdx.x; p < p1; p += 4 * (int64_t)blockDim.x) {
+          uint32_t tk[4];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const int64_t q = p + j * (int64_t)blockDim.x;
+            tk[j] = q < p1 ? tkey[toff + q] : 0u;
+          }
+#pragma unroll
+          for (int j = 0; j < 4; ++j)
+            if (tk[j] & kInWindow) atomicAdd(hist + s * W + (tk[j] & ~kInWindow), 1u);
         }
       }
     }
     __syncthreads();
-    const int wyz = win.wy * win.wz;
-    for (int rw = threadIdx.x >> 5; rw < 2 * wyz; rw += blockDim.x >> 5) {
-      const int sp = rw >= wyz ? 1 : 0;
-      const uint32_t rowcell = window_row(g, win, rw - sp * wyz);
-      const int i0 = sp * W + (rw - sp * wyz) * win.wx;
-      uint32_t* counts = sp ? counts1 : counts0;
-      const int64_t* newoff = sp ? newoff1 : newoff0;
-      for (int lx = threadIdx.x & 31; lx < win.wx; lx += 32) {
-        const uint32_t k = hist[i0 + lx];
-        if (!k) continue;
-        const uint32_t cell = rowcell + window_x(g, win, lx);
-        const uint32_t top = atomicSub(counts + cell, k);
-        base[i0 + lx] = (unsigned long long)(newoff[cell] + (int64_t)top - (int64_t)k);
+    // Reserve the block's range in each window cell.  A thread takes up to
+    // RJ slots at a time and issues all their cursor atomics and offset loads
+    // before using any result, so their round trips overlap.
+    constexpr int RJ = 4;
+    for (int i0 = threadIdx.x; i0 < 2 * W; i0 += RJ * blockDim.x) {
+      uint32_t cell[RJ], k[RJ], top[RJ];
+      int64_t no[RJ];
+#pragma unroll
+      for (int j = 0; j < RJ; ++j) {
+        const int i = i0 + j * blockDim.x;
+        k[j] = i < 2 * W ? hist[i] : 0u;
+        cell[j] = 0;
+        if (k[j]) {
+          const int sp = i >= W ? 1 : 0, r = i - sp * W;
+          const int row = r / win.wx, lx = r - row * win.wx;
+          cell[j] = window_row(g, win, row) + window_x(g, win, lx);
+        }
       }
+#pragma unroll
+      for (int j = 0; j < RJ; ++j) {
+        const int i = i0 + j * blockDim.x;
+        if (!k[j]) continue;
+        const bool sp = i >= W;
+        top[j] = atomicSub((sp ? counts1 : counts0) + cell[j], k[j]);
+        no[j] = (sp ? newoff1 : newoff0)[cell[j]];
+      }
+#pragma unroll
+      for (int j = 0; j < RJ; ++j)
+        if (k[j]) base[i0 + j * blockDim.x] = (unsigned long long)(no[j] + (int64_t)top[j] - (int64_t)k[j]);
     }
     __syncthreads();
     for (int s = 0; s < 2; ++s) {
