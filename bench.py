@@ -134,6 +134,8 @@ def algorithmic_bytes(cfg, counts, vel_bits):
         "ikd_count": N * 3 * (1 + vb) + 12 * (nf ** 3 + nc ** 3),
         # position + velocity codes written
         "ikd_scatter": N * 3 * (1 + vb),
+        # position codes read, one float32 acceleration triple written per particle
+        "pp": N * 15,
     }
 
 
@@ -242,6 +244,10 @@ def run_gb300(args):
     cfg = w.config()
     cfg["tile_batch"] = args.tile_batch
     cfg["vmax_mode"] = args.vmax_mode
+    if args.pp:
+        # Eq. 4 softening: 0.05 of the mean CDM inter-particle spacing, L / (20 n_p)
+        n_p = round(w.counts[0] ** (1.0 / 3.0))
+        cfg["pp"], cfg["r_soft"] = 1, w.n_fine / (20.0 * n_p)
     pm = PM(cfg)
     codes, spare = build_state(pm, w, torch)
     counts = w.counts
@@ -322,7 +328,7 @@ def run_gb300(args):
     h2d = sum(codes_bytes(c, w.vel_bits) for c in a)
     d2h = h2d
 
-    alg = algorithmic_bytes(cfg, counts, w.vel_bits)
+    alg = algorithmic_bytes(dict(cfg, tile_batch=tuning["tile_batch"]), counts, w.vel_bits)
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -351,7 +357,7 @@ def run_gb300(args):
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": args.workload, "n_fine": w.n_fine, "coarse_ratio": w.coarse_ratio,
                    "tile": w.tile, "buffer": w.buffer, "tile_batch": args.tile_batch,
-                   "vmax_mode": args.vmax_mode,
+                   "vmax_mode": args.vmax_mode, "pp": int(args.pp),
                    "particles": {"cdm": counts[0], "nu": counts[1]}, "vel_bits": w.vel_bits,
                    "global_batch": n_total * world, "parallelism": f"replicas{world}",
                    "l2": "working set > L2 (126 MB): codes 113 MB + meshes > 400 MB per step"},
@@ -521,6 +527,7 @@ def main():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-adjoint", action="store_true")
     p.add_argument("--no-autotune", action="store_true")
+    p.add_argument("--pp", action="store_true", help="add the particle-particle force of Eq. 4 to the step")
     p.add_argument("--tuning", default="", help="launch tuning as JSON (as printed under 'tuning'); skips the autotuner")
     p.add_argument("--adjoint-workload", default="diff128")
     args = p.parse_args()

@@ -85,8 +85,14 @@ typedef struct pm_handle pm_handle_t;
  *                pm_step quantises velocities in the same pass that kicks
  *                them.  Mode 1 is not the paper's definition: the codes
  *                differ from mode 0 (coarser velocity bins), but every
- *                |v'_d| is still <= v_max'.
- *  reserved      must be 0. */
+ *                |v'_d| is still <= v_max'.  With pp = 1 the bound adds
+ *                |c_kick| max_i |a_pp,i|.
+ *  pp            1: add the particle-particle force of Eq. 4 (direct sum over
+ *                the particles sharing a fine-mesh cell [i, i+1)^3, both
+ *                species, pairs closer than r_soft dropped) to every
+ *                particle's acceleration in pm_step; 0: PM force only.
+ *  r_soft        PP softening length in fine cells (Sec. 2.1: 0.05 of the
+ *                mean inter-particle spacing); used when pp = 1. */
 typedef struct pm_config {
   int32_t n_fine;
   int32_t coarse_ratio;
@@ -97,12 +103,13 @@ typedef struct pm_config {
   int32_t deposit_mode;
   int32_t tile_batch;
   int32_t vmax_mode;
-  int32_t reserved;
+  int32_t pp;
   double G;
   double mass[2];
   int64_t count[2];
   double r_split;
   double r_cut;
+  double r_soft;
 } pm_config_t;
 
 /* One species' compressed state (Sec. 2.4) in device memory, SoA layout:
@@ -299,6 +306,14 @@ int pm_check(pm_handle_t* h, void* stream);
 
 /* Copies the last error message (NUL-terminated, truncated to n). */
 int pm_last_error(const pm_handle_t* h, char* buf, size_t n);
+
+/* Particle-particle acceleration of Eq. 4 (Sec. 2.1) for every particle of
+ * the compressed state in[2]: a_i = G sum m_j (x_j - x_i)/|x_j - x_i|^3 over
+ * the particles of both species in particle i's fine-mesh cell, pairs closer
+ * than cfg.r_soft dropped.  acc: device float32 [n0 + n1][4] (16-byte
+ * aligned), row t = stream index (species 0 first), components x, y, z, 0.
+ * The step adds the same values when cfg.pp = 1. */
+int pm_pp_accel(pm_handle_t* h, const pm_codes_t in[2], float* acc, void* stream);
 
 /* Per-stage timing of pm_step with CUDA events on its stream: enable (1) or
  * disable (0); pm_stage_times writes up to cap averages in ms over the

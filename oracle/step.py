@@ -25,7 +25,7 @@ from typing import Dict, List, Sequence
 
 import numpy as np
 
-from . import codec, mesh, solve
+from . import codec, mesh, pp, solve
 
 
 def tile_origins(n_fine: int, t: int):
@@ -154,6 +154,9 @@ def step(codes: Sequence[codec.Codes], cfg: Dict, c_kick: float, c_drift: float,
 
     vmax_mode 0 quantises the new velocities with their exact max (Sec. 2.4);
     1 with vmax_bound of each species' input v_max and the force meshes.
+    cfg["pp"] = 1 adds the particle-particle acceleration of Eq. 4 (oracle/pp.py,
+    softening cfg["r_soft"]) to the PM acceleration before the kick; the bound
+    then also covers its largest component.
     Returns (new codes per species, float64 x', v' per species in input order).
     """
     n = cfg["n_fine"]
@@ -161,9 +164,14 @@ def step(codes: Sequence[codec.Codes], cfg: Dict, c_kick: float, c_drift: float,
     xv = [codec.decompress(c, n) for c in codes]
     xs = [p[0] for p in xv]
     a = accel(xs, cfg)
+    extra = []
+    if cfg.get("pp", 0):
+        a_pp = pp.pp_accel(xs, cfg["mass"], cfg["G"], cfg["r_soft"])
+        a = [ai + pi for ai, pi in zip(a, a_pp)]
+        extra = [np.concatenate(a_pp)]
     vm = [None, None]
     if vmax_mode == 1:
-        meshes = force_meshes(xs, cfg)
+        meshes = force_meshes(xs, cfg) + extra
         vm = [vmax_bound(c.vmax, meshes, c_kick) for c in codes]
     new_codes, states = [], []
     for (x, v), acc, vmax in zip(xv, a, vm):

@@ -28,9 +28,9 @@ class pm_config_t(ctypes.Structure):
     _fields_ = [("n_fine", ctypes.c_int32), ("coarse_ratio", ctypes.c_int32), ("tile", ctypes.c_int32),
                 ("buffer", ctypes.c_int32), ("cmp_ratio", ctypes.c_int32), ("vel_bits", ctypes.c_int32),
                 ("deposit_mode", ctypes.c_int32), ("tile_batch", ctypes.c_int32), ("vmax_mode", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("G", ctypes.c_double),
+                ("pp", ctypes.c_int32), ("G", ctypes.c_double),
                 ("mass", ctypes.c_double * 2), ("count", ctypes.c_int64 * 2), ("r_split", ctypes.c_double),
-                ("r_cut", ctypes.c_double)]
+                ("r_cut", ctypes.c_double), ("r_soft", ctypes.c_double)]
 
 
 class pm_tuning_t(ctypes.Structure):
@@ -52,7 +52,7 @@ class pm_codes_t(ctypes.Structure):
 EXPORTED = ["pm_init", "pm_destroy", "pm_geometry", "pm_decompress", "pm_compress", "pm_deposit",
             "pm_deposit_fixed", "pm_deposit_codes", "pm_tile_density", "pm_solve", "pm_solve_fixed", "pm_interpolate",
             "pm_kick_drift", "pm_step", "pm_step_host", "pm_check", "pm_last_error", "pm_set_timing", "pm_set_graphs",
-            "pm_get_tuning", "pm_set_tuning", "pm_autotune",
+            "pm_get_tuning", "pm_set_tuning", "pm_autotune", "pm_pp_accel",
             "pm_stage_times", "pm_serialize", "pm_deserialize", "pm_error_string", "pm_launch_count",
             "pm_decompress_noalloc", "pm_deposit_adjoint", "pm_solve_adjoint", "pm_interpolate_adjoint",
             "pm_step_adjoint"]
@@ -81,6 +81,7 @@ _PROTOS = {
     "pm_last_error": (ctypes.c_int, [_P, ctypes.c_char_p, ctypes.c_size_t]),
     "pm_set_timing": (ctypes.c_int, [_P, ctypes.c_int]),
     "pm_set_graphs": (ctypes.c_int, [_P, ctypes.c_int]),
+    "pm_pp_accel": (ctypes.c_int, [_P, ctypes.POINTER(pm_codes_t), _P, _P]),
     "pm_get_tuning": (ctypes.c_int, [_P, ctypes.POINTER(pm_tuning_t)]),
     "pm_set_tuning": (ctypes.c_int, [_P, ctypes.POINTER(pm_tuning_t)]),
     "pm_autotune": (ctypes.c_int, [_P, ctypes.POINTER(pm_codes_t), ctypes.POINTER(pm_codes_t), ctypes.c_double,

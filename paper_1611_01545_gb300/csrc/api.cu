@@ -36,7 +36,8 @@ struct pm_handle {
   int64_t* newoff[2] = {nullptr, nullptr};
   uint32_t* counts[2] = {nullptr, nullptr};
   uint32_t* vmax_bits = nullptr;  // [2]
-  uint32_t* amax = nullptr;       // [2] max |a| over the coarse / fine force meshes (float bits)
+  uint32_t* amax = nullptr;       // [3] max |a| over the coarse / fine force meshes and the PP accelerations (float bits)
+  float4* app = nullptr;          // per particle PP acceleration (pp = 1), stream order, species 0 first
   void* partial = nullptr;
   int* status = nullptr;
   Blk blk_dep{}, blk_ikd{};
@@ -345,7 +346,8 @@ int pm_init(const pm_config_t* cfg, pm_handle_t** out) {
   if (c.vel_bits != 8 && c.vel_bits != 16) return bad("vel_bits must be 8 or 16");
   if (c.deposit_mode != 0 && c.deposit_mode != 1) return bad("deposit_mode must be 0 or 1");
   if (c.vmax_mode != 0 && c.vmax_mode != 1) return bad("vmax_mode must be 0 or 1");
-  if (c.reserved != 0) return bad("reserved must be 0");
+  if (c.pp != 0 && c.pp != 1) return bad("pp must be 0 or 1");
+  if (c.pp && !(c.r_soft >= 0.0 && c.r_soft < 1.0)) return bad("r_soft must lie in [0, 1) fine cells");
   if (c.count[0] < 0 || c.count[1] < 0) return bad("negative particle count");
   g.nf = c.n_fine;
   g.rcmp = c.cmp_ratio;
@@ -405,7 +407,8 @@ int pm_init(const pm_config_t* cfg, pm_handle_t** out) {
     A(&h->counts[s], ncell * 4);
   }
   A(&h->vmax_bits, 2 * 4);
-  A(&h->amax, 2 * 4);
+  A(&h->amax, 3 * 4);
+  if (c.pp) A(&h->app, (size_t)(c.count[0] + c.count[1]) * sizeof(float4));
   A(&h->work, 4 * 4);
   h->scratch_n = c.count[0] + c.count[1];
   A(&h->tkey, (size_t)h->scratch_n * 4);
@@ -546,6 +549,23 @@ int pm_deposit_codes(pm_handle_t* h, const pm_codes_t in[2], void* rho_coarse, v
   CK(h, launch_deposit_codes(view(in[0], vel16), view(in[1], vel16), h->off[0], h->off[1], h->geo, dep_blk(h),
                              (float)h->cfg.mass[0], (float)h->cfg.mass[1], M0, M1, h->gm.two ? rho_coarse : nullptr,
                              rho_fine, fixed, st));
+  return PM_OK;
+}
+
+int pm_pp_accel(pm_handle_t* h, const pm_codes_t in[2], float* acc, void* stream) {
+  if (!h || !in) return fail(h, PM_ERR_ARG, "null argument");
+  for (int s = 0; s < 2; ++s)
+    if (!in[s].cnt || !in[s].vmax || !in[s].n_esc || !in[s].esc || (in[s].n > 0 && (!in[s].pos || !in[s].vel)))
+      return fail(h, PM_ERR_ARG, "null codes pointer");
+  if (in[0].n + in[1].n > 0 && !acc) return fail(h, PM_ERR_ARG, "null acc");
+  if ((reinterpret_cast<uintptr_t>(acc) & 15) != 0) return fail(h, PM_ERR_ARG, "acc must be 16-byte aligned");
+  if (!(h->cfg.r_soft >= 0.0 && h->cfg.r_soft < 1.0)) return fail(h, PM_ERR_ARG, "r_soft must lie in [0, 1)");
+  cudaStream_t st = (cudaStream_t)stream;
+  const bool vel16 = h->cfg.vel_bits == 16;
+  for (int s = 0; s < 2; ++s) CK(h, scan_codes(in[s], h->gm.ncell(), h->off[s], h->partial, h->status, st));
+  CK(h, launch_pp(view(in[0], vel16), view(in[1], vel16), h->off[0], h->off[1], h->geo, (float)h->cfg.mass[0],
+                  (float)h->cfg.mass[1], (float)h->cfg.G, (float)h->cfg.r_soft, reinterpret_cast<float4*>(acc), nullptr,
+                  st));
   return PM_OK;
 }
 
@@ -866,8 +886,14 @@ int step_launch(pm_handle_t* h, const pm_codes_t in[2], pm_codes_t out[2], doubl
   }
   const bool bound = h->cfg.vmax_mode == 1;
   const float ck = (float)c_kick, cd = (float)c_drift;
-  if (bound) CK(h, cudaMemsetAsync(h->amax, 0, 8, st));
+  if (bound) CK(h, cudaMemsetAsync(h->amax, 0, 12, st));
   if (int r = solve_impl(h, rc, rf, fixed, h->acc_c, h->acc_f, st, bound ? h->amax : nullptr)) return r;
+  if (h->cfg.pp) {
+    TimedScope ts(tm, "pp", st);
+    CK(h, launch_pp(view(in[0], vel16), view(in[1], vel16), h->off[0], h->off[1], h->geo, (float)h->cfg.mass[0],
+                    (float)h->cfg.mass[1], (float)h->cfg.G, (float)h->cfg.r_soft, h->app, bound ? h->amax + 2 : nullptr,
+                    st));
+  }
   // bound mode: v_max' from the mesh maxima, before any particle is kicked
   if (bound) CK(h, launch_vmax_bound(in[0].vmax, in[1].vmax, h->amax, ck, out[0].vmax, out[1].vmax, st));
   {
@@ -876,7 +902,8 @@ int step_launch(pm_handle_t* h, const pm_codes_t in[2], pm_codes_t out[2], doubl
     for (int s = 0; s < 2; ++s) CK(h, cudaMemsetAsync(h->counts[s], 0, (size_t)ncell * 4, st));
     CK(h, launch_ikd_count(view(in[0], vel16), view(in[1], vel16), h->off[0], h->off[1], h->geo, ikd_blk(h, 0),
                            h->acc_c, h->acc_f, ck, cd, h->counts[0], h->counts[1], h->vmax_bits, h->tkey, h->tpv,
-                           bound ? out[0].vmax : nullptr, bound ? out[1].vmax : nullptr, st));
+                           bound ? out[0].vmax : nullptr, bound ? out[1].vmax : nullptr, h->cfg.pp ? h->app : nullptr,
+                           st));
   }
   {
     TimedScope ts(tm, "scan_out", st);

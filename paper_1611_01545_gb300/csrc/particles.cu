@@ -597,7 +597,7 @@ __global__ void k_set_vmax(const uint32_t* vmax_bits, const float* vmax_in, floa
 // operation rounds up, so the float result is not below the exact bound.
 __global__ void k_vmax_bound(const float* vin0, const float* vin1, const uint32_t* amax, float ck, float* vout0,
                              float* vout1) {
-  const float a = __fadd_ru(__uint_as_float(amax[0]), __uint_as_float(amax[1]));
+  const float a = __fadd_ru(__fadd_ru(__uint_as_float(amax[0]), __uint_as_float(amax[1])), __uint_as_float(amax[2]));
   const float ka = __fmul_ru(fabsf(ck), a);
   *vout0 = __fadd_ru(*vin0, ka);
   *vout1 = __fadd_ru(*vin1, ka);
@@ -897,7 +897,7 @@ __device__ __forceinline__ uint32_t window_x(const Geo& g, const Win& w, int lx)
 __global__ void __launch_bounds__(512, 2) k_ikd_count(PCodes c0, PCodes c1, const int64_t* off0, const int64_t* off1, Geo g, Blk bk,
                             const float* acc_c, const float* acc_f, float ck, float cd, uint32_t* counts0,
                             uint32_t* counts1, uint32_t* vmax_bits, uint32_t* tkey, uint4* tpv,
-                            const float* vq0, const float* vq1) {
+                            const float* vq0, const float* vq1, const float4* app) {
   extern __shared__ __align__(16) unsigned char smraw[];
   for_each_block(bk, [&](const int bid) {
     const int r = g.rcmp;
@@ -1003,6 +1003,12 @@ __global__ void __launch_bounds__(512, 2) k_ikd_count(PCodes c0, PCodes c1, cons
             a[0] = __fadd_rn(b[0], a[0]);
             a[1] = __fadd_rn(b[1], a[1]);
             a[2] = __fadd_rn(b[2], a[2]);
+          }
+          if (app) {   // particle-particle term (Eq. 4), precomputed per particle
+            const float4 q4 = app[toff + p];
+            a[0] = __fadd_rn(a[0], q4.x);
+            a[1] = __fadd_rn(a[1], q4.y);
+            a[2] = __fadd_rn(a[2], q4.z);
           }
           kick_drift(x, v, a, ck, cd, nf);
           int cc[3], qq[3];
@@ -1306,13 +1312,13 @@ cudaError_t launch_deposit_codes(const PCodes& c0, const PCodes& c1, const int64
 cudaError_t launch_ikd_count(const PCodes& c0, const PCodes& c1, const int64_t* off0, const int64_t* off1,
                              const Geo& g, const Blk& bk, const float* acc_c, const float* acc_f, float ck, float cd,
                              uint32_t* counts0, uint32_t* counts1, uint32_t* vmax_bits, uint32_t* tkey,
-                             uint4* tpv, const float* vq0, const float* vq1, cudaStream_t st) {
+                             uint4* tpv, const float* vq0, const float* vq1, const float4* app, cudaStream_t st) {
   size_t smem = ikd_count_smem(g, bk);
   int nblk = bk.nbx * bk.nby * bk.nbz;
   cudaFuncSetAttribute(k_ikd_count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   nblk = block_grid(k_ikd_count, bk, 512, smem);
   k_ikd_count<<<nblk, 512, smem, st>>>(c0, c1, off0, off1, g, bk, acc_c, acc_f, ck, cd, counts0, counts1, vmax_bits,
-                                       tkey, tpv, vq0, vq1);
+                                       tkey, tpv, vq0, vq1, app);
   note_launches(1);
   return cudaGetLastError();
 }

@@ -65,13 +65,19 @@ cudaError_t launch_deposit_codes(const PCodes& c0, const PCodes& c1, const int64
 cudaError_t launch_ikd_count(const PCodes& c0, const PCodes& c1, const int64_t* off0, const int64_t* off1,
                              const Geo& g, const Blk& bk, const float* acc_c, const float* acc_f, float ck, float cd,
                              uint32_t* counts0, uint32_t* counts1, uint32_t* vmax_bits, uint32_t* tkey,
-                             uint4* tpv, const float* vq0, const float* vq1, cudaStream_t st);
+                             uint4* tpv, const float* vq0, const float* vq1, const float4* app, cudaStream_t st);
 cudaError_t launch_ikd_scatter(int64_t n0, int64_t n1, const int64_t* off0, const int64_t* off1, const Geo& g,
                                const Blk& bk, uint32_t* counts0, uint32_t* counts1, const int64_t* newoff0,
                                const int64_t* newoff1, const PCodesOut& o0, const PCodesOut& o1, const uint32_t* tkey,
                                const uint4* tpv, bool coded, int* status, cudaStream_t st);
 cudaError_t launch_set_vmax(const uint32_t* vmax_bits, float* out, cudaStream_t st);
-// v_max' bound of both species from v_max and the mesh maxima amax[2] (float bits).
+// v_max' bound of both species from v_max and the maxima amax[3] (coarse mesh,
+// fine mesh, PP accelerations; float bits).
+// PP acceleration (Eq. 4) of every particle of both species into acc[t] (stream index t,
+// species 0 first; float4, w = 0); max |a_d| into *amax when set.  pp.cu.
+size_t pp_smem(const Geo& g);
+cudaError_t launch_pp(const PCodes& c0, const PCodes& c1, const int64_t* off0, const int64_t* off1, const Geo& g,
+                      float m0, float m1, float G, float r_soft, float4* acc, uint32_t* amax, cudaStream_t st);
 cudaError_t launch_vmax_bound(const float* vin0, const float* vin1, const uint32_t* amax, float ck, float* vout0,
                               float* vout1, cudaStream_t st);
 cudaError_t launch_adj_deposit(const float* x, int64_t n, float m, int nf, const float* lam_rho, float* lam_x,

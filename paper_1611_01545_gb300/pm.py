@@ -92,13 +92,14 @@ def config_struct(cfg: Dict) -> pm_config_t:
     c.deposit_mode = int(cfg.get("deposit_mode", 0))
     c.tile_batch = int(cfg.get("tile_batch", 0))
     c.vmax_mode = int(cfg.get("vmax_mode", 0))
-    c.reserved = 0
+    c.pp = int(cfg.get("pp", 0))
     c.G = float(cfg["G"])
     c.mass[0], c.mass[1] = (float(m) for m in cfg["mass"])
     cnt = cfg.get("count", (0, 0))
     c.count[0], c.count[1] = (int(k) for k in cnt)
     c.r_split = float(cfg.get("r_split", 0.0))
     c.r_cut = float(cfg.get("r_cut", 0.0))
+    c.r_soft = float(cfg.get("r_soft", 0.0))
     return c
 
 
@@ -250,6 +251,13 @@ class PM:
         lam = (pm_particles_t * 2)(*[pm_particles_t(a.shape[0], a.data_ptr(), b.data_ptr())
                                      for a, b in zip(lam_x, lam_v)])
         self._err(self.lib.pm_step_adjoint(self.h, st, lam, c_kick, c_drift, _stream(stream)))
+
+    def pp_accel(self, codes: Sequence[Codes], stream=None) -> torch.Tensor:
+        """Eq. 4 accelerations [n0 + n1, 4] (x, y, z, 0), stream order, species 0 first."""
+        acc = torch.empty((codes[0].n + codes[1].n, 4), dtype=torch.float32, device="cuda")
+        arr = (pm_codes_t * 2)(codes[0].struct(), codes[1].struct())
+        self._err(self.lib.pm_pp_accel(self.h, arr, _ptr(acc), _stream(stream)))
+        return acc
 
     def set_timing(self, on: bool):
         self._err(self.lib.pm_set_timing(self.h, 1 if on else 0))
