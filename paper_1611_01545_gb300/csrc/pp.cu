@@ -30,7 +30,7 @@ namespace pm {
 namespace {
 
 constexpr int PP_RX = 16;        // compression cells per CTA row segment
-constexpr int PP_CAP = 4096;     // particles per chunk held in shared memory
+constexpr int PP_CAP = 2048;     // particles per chunk held in shared memory
 constexpr int PP_THREADS = 256;
 
 struct PPArgs {
@@ -50,12 +50,11 @@ struct Decoded {
   int fine;                       // fine cell index within the CTA's row segment
 };
 
-__device__ __forceinline__ Decoded decode_one(const PPArgs& a, const PCodes& cs, int64_t p, int cx, int cy, int cz,
-                                              int ix0) {
+__device__ __forceinline__ Decoded decode_word(const PPArgs& a, uint32_t word, int cx, int cy, int cz, int ix0) {
   const int r = a.g.rcmp;
   const float pscale = (float)r / 256.0f;
   int q[3];
-  unpack_pos(cs.pos[p], q);
+  unpack_pos(word, q);
   Decoded d;
   d.x = decode_pos(cx, q[0], pscale);
   d.y = decode_pos(cy, q[1], pscale);
@@ -66,6 +65,11 @@ __device__ __forceinline__ Decoded decode_one(const PPArgs& a, const PCodes& cs,
   const int fz = ((2 * q[2] + 1) * r) >> 9;
   d.fine = (fz * r + fy) * (a.rx * r) + fx;
   return d;
+}
+
+__device__ __forceinline__ Decoded decode_one(const PPArgs& a, const PCodes& cs, int64_t p, int cx, int cy, int cz,
+                                              int ix0) {
+  return decode_word(a, cs.pos[p], cx, cy, cz, ix0);
 }
 
 __device__ __forceinline__ void pair_add(float xi, float yi, float zi, float xj, float yj, float zj, float mj,
@@ -95,7 +99,6 @@ __global__ void __launch_bounds__(PP_THREADS) k_pp(PPArgs a) {
   const int nseg = n / a.rx;
   const int seg = blockIdx.x % nseg, row = blockIdx.x / nseg;
   const int cy = row % n, cz = row / n, ix0 = seg * a.rx;
-  const int nfine = a.rx * r * r * r;
   float4* P = reinterpret_cast<float4*>(smraw);                 // x, y, z, m
   int* nxt = reinterpret_cast<int*>(P + PP_CAP);
   int* fin = nxt + PP_CAP;                                      // fine cell of each chunk particle
@@ -156,22 +159,36 @@ __global__ void __launch_bounds__(PP_THREADS) k_pp(PPArgs a) {
     const int64_t b0 = r0[0][c0], e0 = r0[0][c1], b1 = r0[1][c0], e1 = r0[1][c1];
     const int n0 = (int)(e0 - b0), ntot = n0 + (int)(e1 - b1);
     const int f0 = c0 * r, f1 = c1 * r;   // fine x range of the chunk within the segment
-    for (int i = threadIdx.x; i < nfine; i += blockDim.x) {
-      const int fx = i % (a.rx * r);
-      if (fx >= f0 && fx < f1) head[i] = -1;
+    // reset the chunk's list heads: fine rows (z, y) of the segment, x in [f0, f1)
+    for (int i = threadIdx.x; i < r * r * (f1 - f0); i += blockDim.x) {
+      const int line = i / (f1 - f0), fx = f0 + (i - line * (f1 - f0));
+      head[line * (a.rx * r) + fx] = -1;
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < ntot; i += blockDim.x) {
-      const bool s1 = i >= n0;
-      const int64_t p = s1 ? b1 + (i - n0) : b0 + i;
-      const int64_t* ro = r0[s1 ? 1 : 0];
-      // compression cell of p within [c0, c1): rows are short, scan them
-      int c = c0;
-      while (c + 1 < c1 && ro[c + 1] <= p) ++c;
-      const Decoded d = decode_one(a, s1 ? a.c1 : a.c0, p, ix0 + c, cy, cz, ix0);
-      P[i] = make_float4(d.x, d.y, d.z, s1 ? a.m1 : a.m0);
-      fin[i] = d.fine;
-      nxt[i] = atomicExch(&head[d.fine], i);
+    // four particles per thread: position words loaded before any is linked
+    for (int i0 = threadIdx.x; i0 < ntot; i0 += 4 * blockDim.x) {
+      uint32_t w[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int i = i0 + u * blockDim.x;
+        const bool s1 = i >= n0;
+        w[u] = i < ntot ? (s1 ? a.c1 : a.c0).pos[s1 ? b1 + (i - n0) : b0 + i] : 0u;
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int i = i0 + u * blockDim.x;
+        if (i >= ntot) break;
+        const bool s1 = i >= n0;
+        const int64_t p = s1 ? b1 + (i - n0) : b0 + i;
+        const int64_t* ro = r0[s1 ? 1 : 0];
+        // compression cell of p within [c0, c1): rows are short, scan them
+        int c = c0;
+        while (c + 1 < c1 && ro[c + 1] <= p) ++c;
+        const Decoded d = decode_word(a, w[u], ix0 + c, cy, cz, ix0);
+        P[i] = make_float4(d.x, d.y, d.z, s1 ? a.m1 : a.m0);
+        fin[i] = d.fine;
+        nxt[i] = atomicExch(&head[d.fine], i);
+      }
     }
     __syncthreads();
     for (int i = threadIdx.x; i < ntot; i += blockDim.x) {
