@@ -315,6 +315,23 @@ int pm_last_error(const pm_handle_t* h, char* buf, size_t n);
  * The step adds the same values when cfg.pp = 1. */
 int pm_pp_accel(pm_handle_t* h, const pm_codes_t in[2], float* acc, void* stream);
 
+/* Asynchronous checkpoint of a compressed state (the single-GPU analogue of
+ * writing checkpoints through a RAM burst buffer): pm_checkpoint_begin
+ * queues device -> host copies of both species' codes (cnt, the esc_cap
+ * escape pairs, n_esc, pos, vel, vmax; same padded layouts) into the
+ * caller's host buffers on a library-owned stream, ordered after the work
+ * already queued on `stream`, and returns at once; the caller keeps
+ * stepping meanwhile.  The device codes must not be overwritten until the
+ * copies are done: pm_checkpoint_fence(h, s) makes stream s wait for them
+ * (no host block), pm_checkpoint_wait(h) blocks the host until they are
+ * done, after which the host codes hold the state and pm_serialize turns
+ * them into the Sec. 2.4 byte stream.  One checkpoint may be pending per
+ * handle (PM_ERR_ARG otherwise).  Host buffers should be pinned; host[s].n
+ * must equal codes[s].n and host[s].esc_cap >= codes[s].esc_cap. */
+int pm_checkpoint_begin(pm_handle_t* h, const pm_codes_t codes[2], pm_host_codes_t host[2], void* stream);
+int pm_checkpoint_fence(pm_handle_t* h, void* stream);
+int pm_checkpoint_wait(pm_handle_t* h);
+
 /* Per-stage timing of pm_step with CUDA events on its stream: enable (1) or
  * disable (0); pm_stage_times writes up to cap averages in ms over the
  * steps since enabling, names into the ';'-separated buffer. */

@@ -66,6 +66,10 @@ struct pm_handle {
   };
   bool graphs = false;
   cudaStream_t capture_stream = nullptr;
+  // asynchronous checkpoint: device -> pinned host copies on their own stream
+  cudaStream_t ckpt_stream = nullptr;
+  cudaEvent_t ckpt_ready = nullptr, ckpt_done = nullptr;
+  bool ckpt_pending = false;
   std::vector<StepGraph> step_graphs;
 };
 
@@ -477,6 +481,9 @@ int pm_destroy(pm_handle_t* h) {
   cudaDeviceSynchronize();
   for (auto& g : h->step_graphs) cudaGraphExecDestroy(g.exec);
   if (h->capture_stream) cudaStreamDestroy(h->capture_stream);
+  if (h->ckpt_stream) cudaStreamDestroy(h->ckpt_stream);
+  if (h->ckpt_ready) cudaEventDestroy(h->ckpt_ready);
+  if (h->ckpt_done) cudaEventDestroy(h->ckpt_done);
   h->timer.flush();
   for (auto e : h->timer.pool) cudaEventDestroy(e);
   for (void* p : h->allocs) cudaFree(p);
@@ -566,6 +573,60 @@ int pm_pp_accel(pm_handle_t* h, const pm_codes_t in[2], float* acc, void* stream
   CK(h, launch_pp(view(in[0], vel16), view(in[1], vel16), h->off[0], h->off[1], h->geo, (float)h->cfg.mass[0],
                   (float)h->cfg.mass[1], (float)h->cfg.G, (float)h->cfg.r_soft, reinterpret_cast<float4*>(acc), nullptr,
                   st));
+  return PM_OK;
+}
+
+int pm_checkpoint_begin(pm_handle_t* h, const pm_codes_t codes[2], pm_host_codes_t host[2], void* stream) {
+  if (!h || !codes || !host) return fail(h, PM_ERR_ARG, "null argument");
+  if (h->ckpt_pending) return fail(h, PM_ERR_ARG, "a checkpoint is still pending: call pm_checkpoint_wait first");
+  const bool vel16 = h->cfg.vel_bits == 16;
+  const int64_t ncell = h->gm.ncell();
+  for (int s = 0; s < 2; ++s) {
+    const pm_codes_t& d = codes[s];
+    const pm_host_codes_t& o = host[s];
+    if (!d.cnt || !d.esc || !d.n_esc || !d.vmax || !o.cnt || !o.esc || !o.n_esc || !o.vmax ||
+        (d.n > 0 && (!d.pos || !d.vel || !o.pos || !o.vel)))
+      return fail(h, PM_ERR_ARG, "null codes pointer");
+    if (o.n != d.n || o.esc_cap < d.esc_cap) return fail(h, PM_ERR_ARG, "host codes smaller than the device codes");
+  }
+  if (!h->ckpt_stream) {
+    CK(h, cudaStreamCreateWithFlags(&h->ckpt_stream, cudaStreamNonBlocking));
+    CK(h, cudaEventCreateWithFlags(&h->ckpt_ready, cudaEventDisableTiming));
+    CK(h, cudaEventCreateWithFlags(&h->ckpt_done, cudaEventDisableTiming));
+  }
+  // the copies start once the caller's stream has produced the codes
+  CK(h, cudaEventRecord(h->ckpt_ready, (cudaStream_t)stream));
+  CK(h, cudaStreamWaitEvent(h->ckpt_stream, h->ckpt_ready, 0));
+  cudaStream_t cs = h->ckpt_stream;
+  for (int s = 0; s < 2; ++s) {
+    const pm_codes_t& d = codes[s];
+    pm_host_codes_t& o = host[s];
+    CK(h, cudaMemcpyAsync(o.cnt, d.cnt, (size_t)ncell, cudaMemcpyDeviceToHost, cs));
+    CK(h, cudaMemcpyAsync(o.esc, d.esc, (size_t)d.esc_cap * 8, cudaMemcpyDeviceToHost, cs));
+    CK(h, cudaMemcpyAsync(o.n_esc, d.n_esc, 4, cudaMemcpyDeviceToHost, cs));
+    CK(h, cudaMemcpyAsync(o.vmax, d.vmax, 4, cudaMemcpyDeviceToHost, cs));
+    if (d.n > 0) {
+      CK(h, cudaMemcpyAsync(o.pos, d.pos, (size_t)d.n * 4, cudaMemcpyDeviceToHost, cs));
+      CK(h, cudaMemcpyAsync(o.vel, d.vel, (size_t)d.n * (vel16 ? 8 : 4), cudaMemcpyDeviceToHost, cs));
+    }
+  }
+  CK(h, cudaEventRecord(h->ckpt_done, cs));
+  h->ckpt_pending = true;
+  return PM_OK;
+}
+
+int pm_checkpoint_fence(pm_handle_t* h, void* stream) {
+  if (!h) return PM_ERR_ARG;
+  if (!h->ckpt_pending) return PM_OK;
+  CK(h, cudaStreamWaitEvent((cudaStream_t)stream, h->ckpt_done, 0));
+  return PM_OK;
+}
+
+int pm_checkpoint_wait(pm_handle_t* h) {
+  if (!h) return PM_ERR_ARG;
+  if (!h->ckpt_pending) return PM_OK;
+  h->ckpt_pending = false;
+  CK(h, cudaEventSynchronize(h->ckpt_done));
   return PM_OK;
 }
 

@@ -259,6 +259,20 @@ class PM:
         self._err(self.lib.pm_pp_accel(self.h, arr, _ptr(acc), _stream(stream)))
         return acc
 
+    def checkpoint_begin(self, codes: Sequence[Codes], host: Sequence[Codes], stream=None):
+        """Queue device -> host copies of both species' codes (host: pinned Codes, same shapes)."""
+        dev = (pm_codes_t * 2)(codes[0].struct(), codes[1].struct())
+        hst = (pm_codes_t * 2)(host[0].struct(), host[1].struct())
+        self._err(self.lib.pm_checkpoint_begin(self.h, dev, hst, _stream(stream)))
+
+    def checkpoint_fence(self, stream=None):
+        """Make `stream` wait for the pending checkpoint copies."""
+        self._err(self.lib.pm_checkpoint_fence(self.h, _stream(stream)))
+
+    def checkpoint_wait(self):
+        """Block until the pending checkpoint copies are in host memory."""
+        self._err(self.lib.pm_checkpoint_wait(self.h))
+
     def set_timing(self, on: bool):
         self._err(self.lib.pm_set_timing(self.h, 1 if on else 0))
 
