@@ -894,7 +894,22 @@ __device__ __forceinline__ uint32_t window_x(const Geo& g, const Win& w, int lx)
 // step's scratch arrays in stream order; new-cell counts are histogrammed in
 // shared memory over the block's window (far movers: global atomics) and
 // flushed once per window cell; per-species max |v'_d| is reduced.
-__global__ void __launch_bounds__(512, 2) k_ikd_count(PCodes c0, PCodes c1, const int64_t* off0, const int64_t* off1, Geo g, Blk bk,
+// Threads per CTA of the deposit and of the two kick passes, and the resident
+// CTAs per SM the kick passes are compiled for (sets their register budget).
+#ifndef PM_DEPOSIT_THREADS
+#define PM_DEPOSIT_THREADS 256
+#endif
+#ifndef PM_IKD_THREADS
+#define PM_IKD_THREADS 512
+#endif
+#ifndef PM_IKD_MIN_BLOCKS
+#define PM_IKD_MIN_BLOCKS 2
+#endif
+#ifndef PM_SCATTER_MIN_BLOCKS
+#define PM_SCATTER_MIN_BLOCKS 2
+#endif
+
+__global__ void __launch_bounds__(PM_IKD_THREADS, PM_IKD_MIN_BLOCKS) k_ikd_count(PCodes c0, PCodes c1, const int64_t* off0, const int64_t* off1, Geo g, Blk bk,
                             const float* acc_c, const float* acc_f, float ck, float cd, uint32_t* counts0,
                             uint32_t* counts1, uint32_t* vmax_bits, uint32_t* tkey, uint4* tpv,
                             const float* vq0, const float* vq1, const float4* app) {
@@ -1057,7 +1072,7 @@ __global__ void __launch_bounds__(512, 2) k_ikd_count(PCodes c0, PCodes c1, cons
 // counted down to zero); phase 3 hands out slots from those ranges with
 // shared-memory atomics (far movers take single global slots), quantises the
 // velocity with the new v_max and writes the codes.
-__global__ void __launch_bounds__(512, 2) k_ikd_scatter(int64_t n0, int64_t n1, const int64_t* off0, const int64_t* off1, Geo g, Blk bk,
+__global__ void __launch_bounds__(PM_IKD_THREADS, PM_SCATTER_MIN_BLOCKS) k_ikd_scatter(int64_t n0, int64_t n1, const int64_t* off0, const int64_t* off1, Geo g, Blk bk,
                               uint32_t* counts0, uint32_t* counts1, const int64_t* newoff0, const int64_t* newoff1,
                               PCodesOut o0, PCodesOut o1, const uint32_t* tkey, const uint4* tpv, int coded,
                               int* status) {
@@ -1296,13 +1311,13 @@ cudaError_t launch_deposit_codes(const PCodes& c0, const PCodes& c1, const int64
   int nblk = bk.nbx * bk.nby * bk.nbz;
   if (fixed) {
     cudaFuncSetAttribute(k_deposit_codes<long long>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    nblk = block_grid(k_deposit_codes<long long>, bk, 256, smem);
-    k_deposit_codes<long long><<<nblk, 256, smem, st>>>(c0, c1, off0, off1, g, bk, m0, m1, M0, M1,
+    nblk = block_grid(k_deposit_codes<long long>, bk, PM_DEPOSIT_THREADS, smem);
+    k_deposit_codes<long long><<<nblk, PM_DEPOSIT_THREADS, smem, st>>>(c0, c1, off0, off1, g, bk, m0, m1, M0, M1,
                                                        static_cast<long long*>(rho_c), static_cast<long long*>(rho_f));
   } else {
     cudaFuncSetAttribute(k_deposit_codes<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    nblk = block_grid(k_deposit_codes<float>, bk, 256, smem);
-    k_deposit_codes<float><<<nblk, 256, smem, st>>>(c0, c1, off0, off1, g, bk, m0, m1, M0, M1,
+    nblk = block_grid(k_deposit_codes<float>, bk, PM_DEPOSIT_THREADS, smem);
+    k_deposit_codes<float><<<nblk, PM_DEPOSIT_THREADS, smem, st>>>(c0, c1, off0, off1, g, bk, m0, m1, M0, M1,
                                                    static_cast<float*>(rho_c), static_cast<float*>(rho_f));
   }
   note_launches(1);
@@ -1316,8 +1331,8 @@ cudaError_t launch_ikd_count(const PCodes& c0, const PCodes& c1, const int64_t* 
   size_t smem = ikd_count_smem(g, bk);
   int nblk = bk.nbx * bk.nby * bk.nbz;
   cudaFuncSetAttribute(k_ikd_count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  nblk = block_grid(k_ikd_count, bk, 512, smem);
-  k_ikd_count<<<nblk, 512, smem, st>>>(c0, c1, off0, off1, g, bk, acc_c, acc_f, ck, cd, counts0, counts1, vmax_bits,
+  nblk = block_grid(k_ikd_count, bk, PM_IKD_THREADS, smem);
+  k_ikd_count<<<nblk, PM_IKD_THREADS, smem, st>>>(c0, c1, off0, off1, g, bk, acc_c, acc_f, ck, cd, counts0, counts1, vmax_bits,
                                        tkey, tpv, vq0, vq1, app);
   note_launches(1);
   return cudaGetLastError();
@@ -1330,8 +1345,8 @@ cudaError_t launch_ikd_scatter(int64_t n0, int64_t n1, const int64_t* off0, cons
   size_t smem = ikd_scatter_smem(g, bk);
   int nblk = bk.nbx * bk.nby * bk.nbz;
   cudaFuncSetAttribute(k_ikd_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  nblk = block_grid(k_ikd_scatter, bk, 512, smem);
-  k_ikd_scatter<<<nblk, 512, smem, st>>>(n0, n1, off0, off1, g, bk, counts0, counts1, newoff0, newoff1, o0, o1, tkey,
+  nblk = block_grid(k_ikd_scatter, bk, PM_IKD_THREADS, smem);
+  k_ikd_scatter<<<nblk, PM_IKD_THREADS, smem, st>>>(n0, n1, off0, off1, g, bk, counts0, counts1, newoff0, newoff1, o0, o1, tkey,
                                          tpv, coded ? 1 : 0, status);
   note_launches(1);
   return cudaGetLastError();

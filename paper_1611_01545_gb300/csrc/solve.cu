@@ -23,7 +23,16 @@ using namespace pmfft;
 
 template <int N> struct SolveCfg {
   static constexpr int NH = N / 2 + 1;
-  static constexpr int threads = (N >= 96) ? 512 : 256;
+// Threads per block of passes A and C (compile-time tunables; measured on the
+// 96^3 tiles: 512 for A, 384 for C).
+#ifndef PM_SOLVE_THREADS
+#define PM_SOLVE_THREADS 512
+#endif
+#ifndef PM_SOLVE_C_THREADS
+#define PM_SOLVE_C_THREADS 384
+#endif
+  static constexpr int threads = (N >= 96) ? PM_SOLVE_THREADS : 256;
+  static constexpr int threads_c = (N >= 96) ? PM_SOLVE_C_THREADS : 256;
   static constexpr size_t smem_a = sizeof(float2) * (N + (size_t)N * N / 2 + (size_t)N * NH);
   static constexpr size_t smem_b = sizeof(float2) * (N + 2 * (size_t)N * NH);
 };
@@ -121,7 +130,10 @@ __global__ void __launch_bounds__(SolveCfg<N>::threads) k_solve_a(SolveArgs a) {
 template <int N> struct PassB {
   static constexpr int NH = N / 2 + 1;
   static constexpr int KC = (NH + 1) / 2;
-  static constexpr int threads = (N >= 96) ? 384 : 256;
+#ifndef PM_PASSB_THREADS
+#define PM_PASSB_THREADS 512
+#endif
+  static constexpr int threads = (N >= 96) ? PM_PASSB_THREADS : 256;
   static constexpr size_t smem = sizeof(float2) * (N + 4 * (size_t)N * KC);
 };
 
@@ -220,7 +232,7 @@ __global__ void __launch_bounds__(PassB<N>::threads) k_solve_b_adj(SolveArgs a) 
 }
 
 template <int N>
-__global__ void __launch_bounds__(SolveCfg<N>::threads) k_solve_c(SolveArgs a) {
+__global__ void __launch_bounds__(SolveCfg<N>::threads_c) k_solve_c(SolveArgs a) {
   constexpr int NH = SolveCfg<N>::NH;
   extern __shared__ float2 sm[];
   float2* tw = sm;
@@ -318,7 +330,7 @@ static cudaError_t solve_n(const SolvePlan& p, const void* src, bool fixed, floa
     }
     {
       TimedScope ts(tm, N == p.src_n && p.b == 0 ? "fft_c_mesh" : "fft_c_tiles", st);
-      k_solve_c<N><<<dim3(p.t, 3, nb), C::threads, C::smem_a, st>>>(a);
+      k_solve_c<N><<<dim3(p.t, 3, nb), C::threads_c, C::smem_a, st>>>(a);
     }
     note_launches(3);
     cudaError_t e = cudaGetLastError();
@@ -351,7 +363,7 @@ static cudaError_t solve_adjoint_n(const SolvePlan& p, const float* lam_acc, flo
   k_solve_a<N, false><<<dim3(N, 3), C::threads, C::smem_a, st>>>(a);
   a.comp_mode = 0;
   k_solve_b_adj<N><<<dim3(N, 2, 1), PassB<N>::threads, sizeof(float2) * (N + 2 * (size_t)N * PassB<N>::KC), st>>>(a);
-  k_solve_c<N><<<dim3(N, 1, 1), C::threads, C::smem_a, st>>>(a);
+  k_solve_c<N><<<dim3(N, 1, 1), C::threads_c, C::smem_a, st>>>(a);
   note_launches(3);
   return cudaGetLastError();
 }
