@@ -184,10 +184,12 @@ def build_state(pm, w, torch):
     return codes, spare
 
 
-def codes_bytes(c, vel_bits):
-    """Bytes of one species' in-memory codes (padded 4-byte position words)."""
+def codes_bytes(c, vel_bits, packed=False):
+    """Bytes of one species' codes: packed record bytes (3 + 3 or 6 per particle)
+    or the padded in-memory words (4 + 4 or 8), plus counts, escapes and v_max."""
     vb = 2 if vel_bits == 16 else 1
-    return c.cnt.numel() + c.esc.numel() * 4 + 4 + c.n * 4 * (1 + vb) + 4
+    per = 3 * (1 + vb) if packed else 4 * (1 + vb)
+    return c.cnt.numel() + c.esc.numel() * 4 + 4 + c.n * per + 4
 
 
 def timed_loop(torch, stream, fn, steps: int) -> float:
@@ -310,22 +312,30 @@ def run_gb300(args):
     pm.set_timing(False)
     plain_ms = plain_step_ms(pm, w, a, b, torch, stream, max(3, args.steps // 4))
 
-    # end-to-end through the C ABI with host buffers (pinned), copies in the timed region
-    hin = [c.to("cpu", pin=True) for c in a]
-    hout = [c.to("cpu", pin=True) for c in b]
+    # end-to-end through the C ABI with host buffers (pinned), copies in the timed
+    # region: the packed record form (pm_step_packed) and the padded in-memory
+    # form (pm_step_host)
     pm.set_graphs(True)
-    pm.step_host(hin, hout, 1.0, 1.0)     # first call allocates the library's staging buffers
-    torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
     k_e2e = max(1, min(args.steps, 10))
-    t0 = time.perf_counter()
-    for _ in range(k_e2e):
-        pm.step_host(hin, hout, 1.0, 1.0)
-    e2e_s = time.perf_counter() - t0
+
+    def e2e_run(fn, hin, hout):
+        fn(hin, hout, 1.0, 1.0)           # first call allocates the library's staging buffers
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(k_e2e):
+            fn(hin, hout, 1.0, 1.0)
+        return time.perf_counter() - t0
+
+    pk_in = [pm.pack(c).to("cpu", pin=True) for c in a]
+    pk_out = [pm.pack(c).to("cpu", pin=True) for c in b]
+    e2e_s = e2e_run(pm.step_packed, pk_in, pk_out)
+    pad_s = e2e_run(pm.step_host, [c.to("cpu", pin=True) for c in a], [c.to("cpu", pin=True) for c in b])
     pm.set_graphs(False)
     e2e_value, _ = job_rate(e2e_s, n_total * k_e2e, world, "cuda", dist)
-    h2d = sum(codes_bytes(c, w.vel_bits) for c in a)
+    pad_value, _ = job_rate(pad_s, n_total * k_e2e, world, "cuda", dist)
+    h2d = sum(codes_bytes(c, w.vel_bits, packed=True) for c in a)
     d2h = h2d
 
     alg = algorithmic_bytes(dict(cfg, tile_batch=tuning["tile_batch"]), counts, w.vel_bits)
@@ -362,7 +372,9 @@ def run_gb300(args):
                    "global_batch": n_total * world, "parallelism": f"replicas{world}",
                    "l2": "working set > L2 (126 MB): codes 113 MB + meshes > 400 MB per step"},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                "steps": k_e2e},
+                "steps": k_e2e, "host_form": "packed record bytes (pm_step_packed)",
+                "padded": {"value": pad_value, "bytes_per_step_each_way": sum(codes_bytes(c, w.vel_bits) for c in a),
+                           "host_form": "padded in-memory words (pm_step_host)"}},
         "gpu_launches": int(launches),
         "roofline": roofline,
         "tuning": tuning,

@@ -272,6 +272,22 @@ int pm_step(pm_handle_t* h, const pm_codes_t in[2], pm_codes_t out[2], double c_
 int pm_step_host(pm_handle_t* h, const pm_host_codes_t in[2], pm_host_codes_t out[2], double c_kick,
                  double c_drift, void* stream);
 
+/* Packed codes: the same pm_codes_t fields, but pos points to u8[n][3]
+ * (px, py, pz) and vel to u8[n][3] or u16[n][3] (vx, vy, vz, little-endian):
+ * the Sec. 2.4 record bytes without the one-word-per-particle padding of the
+ * in-memory form (6 or 9 bytes per particle instead of 8 or 12).
+ * pm_pack_codes / pm_unpack_codes convert between the forms in device memory
+ * (cnt, esc, n_esc and vmax are copied as they are); padded pos/vel must be
+ * 16-byte aligned, packed pos 4-byte and packed vel 4-byte (8-bit) or 8-byte
+ * (16-bit) aligned, out->n == in->n and out->esc_cap >= in->esc_cap.
+ * pm_step_packed is pm_step_host with packed host codes: only the record
+ * bytes cross the host link, and the library (un)packs them on the device.
+ * The paper keeps its compressed particles in this record form. */
+int pm_pack_codes(pm_handle_t* h, const pm_codes_t* in, pm_codes_t* out, void* stream);
+int pm_unpack_codes(pm_handle_t* h, const pm_codes_t* in, pm_codes_t* out, void* stream);
+int pm_step_packed(pm_handle_t* h, const pm_host_codes_t in[2], pm_host_codes_t out[2], double c_kick,
+                   double c_drift, void* stream);
+
 /* Reverse mode of the single-mesh step (coarse_ratio == 1), for gradients of
  * losses of the final positions or density with respect to initial
  * conditions.  The paper has no adjoint; these are the chain rule of the

@@ -57,6 +57,10 @@ struct pm_handle {
   // staging for pm_step_host
   pm_codes_t stage_in[2]{}, stage_out[2]{};
   bool staged = false;
+  // packed record bytes for pm_step_packed (pos 3 B, vel 3 or 6 B per particle)
+  uint8_t* pk_pos[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};   // [in/out][species]
+  uint8_t* pk_vel[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+  bool pk_staged = false;
   // pm_step replay: one instantiated graph per (codes descriptors, c_k, c_d)
   struct StepGraph {
     pm_codes_t in[2], out[2];
@@ -1069,6 +1073,105 @@ static int copy_codes(pm_handle* h, const pm_codes_t& dst, const pm_codes_t& src
   CK(h, cudaMemcpyAsync(dst.vel, src.vel, (size_t)src.n * 4 * vb, kind, st));
   CK(h, cudaMemcpyAsync(dst.vmax, src.vmax, 4, kind, st));
   return PM_OK;
+}
+
+namespace {
+bool aligned(const void* p, uintptr_t a) { return (reinterpret_cast<uintptr_t>(p) & (a - 1)) == 0; }
+
+// Counts, escape list and v_max are the same in both forms.
+int copy_meta(pm_handle* h, const pm_codes_t& dst, const pm_codes_t& src, int64_t ncell, cudaMemcpyKind kind,
+              cudaStream_t st) {
+  CK(h, cudaMemcpyAsync(dst.cnt, src.cnt, (size_t)ncell, kind, st));
+  CK(h, cudaMemcpyAsync(dst.n_esc, src.n_esc, 4, kind, st));
+  const int64_t ecap = src.esc_cap < dst.esc_cap ? src.esc_cap : dst.esc_cap;
+  if (ecap > 0) CK(h, cudaMemcpyAsync(dst.esc, src.esc, (size_t)ecap * 8, kind, st));
+  CK(h, cudaMemcpyAsync(dst.vmax, src.vmax, 4, kind, st));
+  return PM_OK;
+}
+}  // namespace
+
+int pm_pack_codes(pm_handle_t* h, const pm_codes_t* in, pm_codes_t* out, void* stream) {
+  if (!h || !in || !out) return fail(h, PM_ERR_ARG, "null argument");
+  const bool vel16 = h->cfg.vel_bits == 16;
+  if (in->n != out->n || out->esc_cap < in->esc_cap) return fail(h, PM_ERR_ARG, "out must hold in's particles and escapes");
+  if (in->n > 0 && (!aligned(in->pos, 16) || !aligned(in->vel, 16) || !aligned(out->pos, 4) ||
+                    !aligned(out->vel, vel16 ? 8 : 4)))
+    return fail(h, PM_ERR_ARG, "pos/vel alignment: padded 16 B, packed 4 B (8 B for 16-bit velocities)");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (int r = copy_meta(h, *out, *in, h->gm.ncell(), cudaMemcpyDeviceToDevice, st)) return r;
+  CK(h, launch_pack(reinterpret_cast<const uint32_t*>(in->pos), in->vel, vel16, in->n,
+                    reinterpret_cast<uint8_t*>(out->pos), reinterpret_cast<uint8_t*>(out->vel), st));
+  return PM_OK;
+}
+
+int pm_unpack_codes(pm_handle_t* h, const pm_codes_t* in, pm_codes_t* out, void* stream) {
+  if (!h || !in || !out) return fail(h, PM_ERR_ARG, "null argument");
+  const bool vel16 = h->cfg.vel_bits == 16;
+  if (in->n != out->n || out->esc_cap < in->esc_cap) return fail(h, PM_ERR_ARG, "out must hold in's particles and escapes");
+  if (in->n > 0 && (!aligned(out->pos, 16) || !aligned(out->vel, 16) || !aligned(in->pos, 4) ||
+                    !aligned(in->vel, vel16 ? 8 : 4)))
+    return fail(h, PM_ERR_ARG, "pos/vel alignment: padded 16 B, packed 4 B (8 B for 16-bit velocities)");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (int r = copy_meta(h, *out, *in, h->gm.ncell(), cudaMemcpyDeviceToDevice, st)) return r;
+  CK(h, launch_unpack(reinterpret_cast<const uint8_t*>(in->pos), reinterpret_cast<const uint8_t*>(in->vel), vel16,
+                      in->n, reinterpret_cast<uint32_t*>(out->pos), out->vel, st));
+  return PM_OK;
+}
+
+int pm_step_packed(pm_handle_t* h, const pm_host_codes_t in[2], pm_host_codes_t out[2], double c_kick,
+                   double c_drift, void* stream) {
+  if (!h || !in || !out) return fail(h, PM_ERR_ARG, "null argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  const bool vel16 = h->cfg.vel_bits == 16;
+  const int64_t ncell = h->gm.ncell();
+  for (int s = 0; s < 2; ++s) {
+    if (out[s].n != in[s].n) return fail(h, PM_ERR_ARG, "out[s].n must equal in[s].n");
+    if (!in[s].cnt || !in[s].esc || !in[s].n_esc || !in[s].vmax || !out[s].cnt || !out[s].esc || !out[s].n_esc ||
+        !out[s].vmax || (in[s].n > 0 && (!in[s].pos || !in[s].vel || !out[s].pos || !out[s].vel)))
+      return fail(h, PM_ERR_ARG, "null codes pointer");
+  }
+  if (!h->staged) {
+    for (int s = 0; s < 2; ++s) {
+      int64_t cap = in[s].esc_cap > out[s].esc_cap ? in[s].esc_cap : out[s].esc_cap;
+      if (int r = alloc_codes(h, h->stage_in[s], in[s].n, cap)) return r;
+      if (int r = alloc_codes(h, h->stage_out[s], in[s].n, cap)) return r;
+    }
+    h->staged = true;
+  }
+  if (!h->pk_staged) {
+    for (int io = 0; io < 2; ++io)
+      for (int s = 0; s < 2; ++s) {
+        const size_t n = (size_t)h->stage_in[s].n;
+        CK(h, dalloc(h, &h->pk_pos[io][s], 3 * n + 16));
+        CK(h, dalloc(h, &h->pk_vel[io][s], 3 * n * (vel16 ? 2 : 1) + 16));
+      }
+    h->pk_staged = true;
+  }
+  for (int s = 0; s < 2; ++s)
+    if (h->stage_in[s].n != in[s].n) return fail(h, PM_ERR_ARG, "particle counts changed");
+  const size_t vbytes = vel16 ? 6 : 3;
+  for (int s = 0; s < 2; ++s) {
+    const int64_t n = in[s].n;
+    if (int r = copy_meta(h, h->stage_in[s], in[s], ncell, cudaMemcpyHostToDevice, st)) return r;
+    if (n > 0) {
+      CK(h, cudaMemcpyAsync(h->pk_pos[0][s], in[s].pos, (size_t)n * 3, cudaMemcpyHostToDevice, st));
+      CK(h, cudaMemcpyAsync(h->pk_vel[0][s], in[s].vel, (size_t)n * vbytes, cudaMemcpyHostToDevice, st));
+    }
+    CK(h, launch_unpack(h->pk_pos[0][s], h->pk_vel[0][s], vel16, n, reinterpret_cast<uint32_t*>(h->stage_in[s].pos),
+                        h->stage_in[s].vel, st));
+  }
+  if (int r = pm_step(h, h->stage_in, h->stage_out, c_kick, c_drift, stream)) return r;
+  for (int s = 0; s < 2; ++s) {
+    const int64_t n = in[s].n;
+    CK(h, launch_pack(reinterpret_cast<const uint32_t*>(h->stage_out[s].pos), h->stage_out[s].vel, vel16, n,
+                      h->pk_pos[1][s], h->pk_vel[1][s], st));
+    if (int r = copy_meta(h, out[s], h->stage_out[s], ncell, cudaMemcpyDeviceToHost, st)) return r;
+    if (n > 0) {
+      CK(h, cudaMemcpyAsync(out[s].pos, h->pk_pos[1][s], (size_t)n * 3, cudaMemcpyDeviceToHost, st));
+      CK(h, cudaMemcpyAsync(out[s].vel, h->pk_vel[1][s], (size_t)n * vbytes, cudaMemcpyDeviceToHost, st));
+    }
+  }
+  return pm_check(h, stream);
 }
 
 int pm_step_host(pm_handle_t* h, const pm_host_codes_t in[2], pm_host_codes_t out[2], double c_kick, double c_drift,

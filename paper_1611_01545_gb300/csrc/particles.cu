@@ -902,11 +902,14 @@ __device__ __forceinline__ uint32_t window_x(const Geo& g, const Win& w, int lx)
 #ifndef PM_IKD_THREADS
 #define PM_IKD_THREADS 512
 #endif
+#ifndef PM_SCATTER_THREADS
+#define PM_SCATTER_THREADS 256
+#endif
 #ifndef PM_IKD_MIN_BLOCKS
 #define PM_IKD_MIN_BLOCKS 2
 #endif
 #ifndef PM_SCATTER_MIN_BLOCKS
-#define PM_SCATTER_MIN_BLOCKS 2
+#define PM_SCATTER_MIN_BLOCKS 4
 #endif
 
 __global__ void __launch_bounds__(PM_IKD_THREADS, PM_IKD_MIN_BLOCKS) k_ikd_count(PCodes c0, PCodes c1, const int64_t* off0, const int64_t* off1, Geo g, Blk bk,
@@ -1072,7 +1075,7 @@ __global__ void __launch_bounds__(PM_IKD_THREADS, PM_IKD_MIN_BLOCKS) k_ikd_count
 // counted down to zero); phase 3 hands out slots from those ranges with
 // shared-memory atomics (far movers take single global slots), quantises the
 // velocity with the new v_max and writes the codes.
-__global__ void __launch_bounds__(PM_IKD_THREADS, PM_SCATTER_MIN_BLOCKS) k_ikd_scatter(int64_t n0, int64_t n1, const int64_t* off0, const int64_t* off1, Geo g, Blk bk,
+__global__ void __launch_bounds__(PM_SCATTER_THREADS, PM_SCATTER_MIN_BLOCKS) k_ikd_scatter(int64_t n0, int64_t n1, const int64_t* off0, const int64_t* off1, Geo g, Blk bk,
                               uint32_t* counts0, uint32_t* counts1, const int64_t* newoff0, const int64_t* newoff1,
                               PCodesOut o0, PCodesOut o1, const uint32_t* tkey, const uint4* tpv, int coded,
                               int* status) {
@@ -1345,8 +1348,8 @@ cudaError_t launch_ikd_scatter(int64_t n0, int64_t n1, const int64_t* off0, cons
   size_t smem = ikd_scatter_smem(g, bk);
   int nblk = bk.nbx * bk.nby * bk.nbz;
   cudaFuncSetAttribute(k_ikd_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  nblk = block_grid(k_ikd_scatter, bk, PM_IKD_THREADS, smem);
-  k_ikd_scatter<<<nblk, PM_IKD_THREADS, smem, st>>>(n0, n1, off0, off1, g, bk, counts0, counts1, newoff0, newoff1, o0, o1, tkey,
+  nblk = block_grid(k_ikd_scatter, bk, PM_SCATTER_THREADS, smem);
+  k_ikd_scatter<<<nblk, PM_SCATTER_THREADS, smem, st>>>(n0, n1, off0, off1, g, bk, counts0, counts1, newoff0, newoff1, o0, o1, tkey,
                                          tpv, coded ? 1 : 0, status);
   note_launches(1);
   return cudaGetLastError();

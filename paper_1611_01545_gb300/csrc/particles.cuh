@@ -78,6 +78,11 @@ cudaError_t launch_set_vmax(const uint32_t* vmax_bits, float* out, cudaStream_t 
 size_t pp_smem(const Geo& g);
 cudaError_t launch_pp(const PCodes& c0, const PCodes& c1, const int64_t* off0, const int64_t* off1, const Geo& g,
                       float m0, float m1, float G, float r_soft, float4* acc, uint32_t* amax, cudaStream_t st);
+// Packed codes (pack.cu): padded position / velocity words <-> record bytes.
+cudaError_t launch_pack(const uint32_t* pos, const void* vel, bool vel16, int64_t n, uint8_t* ppos, uint8_t* pvel,
+                        cudaStream_t st);
+cudaError_t launch_unpack(const uint8_t* ppos, const uint8_t* pvel, bool vel16, int64_t n, uint32_t* pos, void* vel,
+                          cudaStream_t st);
 cudaError_t launch_vmax_bound(const float* vin0, const float* vin1, const uint32_t* amax, float ck, float* vout0,
                               float* vout1, cudaStream_t st);
 cudaError_t launch_adj_deposit(const float* x, int64_t n, float m, int nf, const float* lam_rho, float* lam_x,

@@ -55,6 +55,20 @@ class Codes:
                      vel=torch.zeros((n, 4), dtype=vdt, device=device),
                      vmax=torch.zeros(1, dtype=torch.float32, device=device))
 
+    @staticmethod
+    def empty_packed(n: int, n_cmp: int, vel_bits: int, esc_cap: Optional[int] = None, device="cuda") -> "Codes":
+        """Packed form: pos uint8 [n, 3], vel uint8 or int16 (u16 bits) [n, 3]."""
+        ncell = n_cmp ** 3
+        if esc_cap is None:
+            esc_cap = max(1, min(ncell, n // 255 + 1))
+        vdt = torch.int16 if vel_bits == 16 else torch.uint8
+        return Codes(n=n, cnt=torch.empty(ncell, dtype=torch.uint8, device=device),
+                     esc=torch.zeros((esc_cap, 2), dtype=torch.int32, device=device),
+                     n_esc=torch.zeros(1, dtype=torch.int32, device=device),
+                     pos=torch.zeros((n, 3), dtype=torch.uint8, device=device),
+                     vel=torch.zeros((n, 3), dtype=vdt, device=device),
+                     vmax=torch.zeros(1, dtype=torch.float32, device=device))
+
     def struct(self) -> pm_codes_t:
         return pm_codes_t(self.n, self.cnt.data_ptr(), self.esc.data_ptr(), self.esc.shape[0],
                           self.n_esc.data_ptr(), self.pos.data_ptr(), self.vel.data_ptr(), self.vmax.data_ptr())
@@ -272,6 +286,26 @@ class PM:
     def checkpoint_wait(self):
         """Block until the pending checkpoint copies are in host memory."""
         self._err(self.lib.pm_checkpoint_wait(self.h))
+
+    def pack(self, codes: Codes, stream=None) -> Codes:
+        """Packed copy (record bytes, no padding) of device codes."""
+        out = Codes.empty_packed(codes.n, self.n_cmp, self.vel_bits, codes.esc.shape[0])
+        a, b = codes.struct(), out.struct()
+        self._err(self.lib.pm_pack_codes(self.h, ctypes.byref(a), ctypes.byref(b), _stream(stream)))
+        return out
+
+    def unpack(self, packed: Codes, stream=None) -> Codes:
+        out = Codes.empty(packed.n, self.n_cmp, self.vel_bits, packed.esc.shape[0])
+        a, b = packed.struct(), out.struct()
+        self._err(self.lib.pm_unpack_codes(self.h, ctypes.byref(a), ctypes.byref(b), _stream(stream)))
+        return out
+
+    def step_packed(self, codes_in: Sequence[Codes], codes_out: Sequence[Codes], c_kick: float, c_drift: float,
+                    stream=None):
+        """pm_step_packed: packed host codes in and out."""
+        arr_in = (pm_codes_t * 2)(codes_in[0].struct(), codes_in[1].struct())
+        arr_out = (pm_codes_t * 2)(codes_out[0].struct(), codes_out[1].struct())
+        self._err(self.lib.pm_step_packed(self.h, arr_in, arr_out, c_kick, c_drift, _stream(stream)))
 
     def set_timing(self, on: bool):
         self._err(self.lib.pm_set_timing(self.h, 1 if on else 0))
