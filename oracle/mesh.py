@@ -125,3 +125,48 @@ def cic_deposit_fixed(x_f32, M: int, n: int) -> np.ndarray:
             for dz in (0, 1):
                 np.add.at(rho, ((i0[:, 2] + dz) % n, (i0[:, 1] + dy) % n, (i0[:, 0] + dx) % n), mz[dz])
     return rho
+
+
+def _coarse_weights(rc: int) -> np.ndarray:
+    """w(k) = 1 - |k| / rc for k = -(rc-1) .. rc-1: the coarse CIC tent sampled on fine nodes."""
+    k = np.arange(-(rc - 1), rc)
+    return 1.0 - np.abs(k) / rc
+
+
+def restrict(rho_f: np.ndarray, rc: int) -> np.ndarray:
+    """Coarse CIC density from the fine one.  A coarse tent Lambda(u / rc) is
+    piecewise linear with knots on fine nodes, so it equals the fine-node
+    interpolation sum_k w(k) Lambda(u - k); hence the coarse CIC deposit of
+    any particles is rho_c(C) = sum_k w(kx) w(ky) w(kz) rho_f(rc C + k)
+    (periodic).  Written as the plain triple sum."""
+    n = rho_f.shape[0]
+    nc = n // rc
+    w = _coarse_weights(rc)
+    ks = np.arange(-(rc - 1), rc)
+    out = np.zeros((nc, nc, nc))
+    for iz, kz in enumerate(ks):
+        for iy, ky in enumerate(ks):
+            for ix, kx in enumerate(ks):
+                zz = (rc * np.arange(nc) + kz) % n
+                yy = (rc * np.arange(nc) + ky) % n
+                xx = (rc * np.arange(nc) + kx) % n
+                out += w[iz] * w[iy] * w[ix] * rho_f[np.ix_(zz, yy, xx)]
+    return out
+
+
+def prolong(field_c: np.ndarray, rc: int) -> np.ndarray:
+    """Coarse field [.., nc, nc, nc] trilinearly interpolated onto the fine nodes
+    (the transpose of restrict).  By the same identity the fine CIC
+    interpolation of it at x equals the coarse CIC interpolation at x / rc."""
+    nc = field_c.shape[-1]
+    n = nc * rc
+    j = np.arange(n)
+    c0, f = j // rc, (j % rc) / rc
+    c1 = (c0 + 1) % nc
+    out = 0.0
+    for wz, cz in ((1 - f, c0), (f, c1)):
+        for wy, cy in ((1 - f, c0), (f, c1)):
+            for wx, cx in ((1 - f, c0), (f, c1)):
+                out = out + (wz[:, None, None] * wy[None, :, None] * wx[None, None, :]) * \
+                    field_c[..., cz[:, None, None], cy[None, :, None], cx[None, None, :]]
+    return out

@@ -70,6 +70,9 @@ struct pm_handle {
   };
   bool graphs = false;
   cudaStream_t capture_stream = nullptr;
+  // the coarse solve runs beside the tile solve on this stream (fork / join events)
+  cudaStream_t side_stream = nullptr;
+  cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
   // asynchronous checkpoint: device -> pinned host copies on their own stream
   cudaStream_t ckpt_stream = nullptr;
   cudaEvent_t ckpt_ready = nullptr, ckpt_done = nullptr;
@@ -485,6 +488,9 @@ int pm_destroy(pm_handle_t* h) {
   cudaDeviceSynchronize();
   for (auto& g : h->step_graphs) cudaGraphExecDestroy(g.exec);
   if (h->capture_stream) cudaStreamDestroy(h->capture_stream);
+  if (h->side_stream) cudaStreamDestroy(h->side_stream);
+  if (h->fork_ev) cudaEventDestroy(h->fork_ev);
+  if (h->join_ev) cudaEventDestroy(h->join_ev);
   if (h->ckpt_stream) cudaStreamDestroy(h->ckpt_stream);
   if (h->ckpt_ready) cudaEventDestroy(h->ckpt_ready);
   if (h->ckpt_done) cudaEventDestroy(h->ckpt_done);
@@ -644,7 +650,21 @@ int pm_tile_density(pm_handle_t* h, const float* rho_fine, int64_t tile, float* 
 static int solve_impl(pm_handle_t* h, const void* rho_c, const void* rho_f, bool fixed, float* acc_c, float* acc_f,
                       cudaStream_t st, uint32_t* amax = nullptr) {
   Timer* tm = h->timer.on ? &h->timer : nullptr;
-  if (h->gm.two) {
+  if (h->gm.two && !tm) {
+    // The coarse mesh (a few hundred blocks) and the tiles use separate plans,
+    // inputs and outputs: solve the coarse mesh on the side stream meanwhile.
+    if (!h->side_stream) {
+      CK(h, cudaStreamCreateWithFlags(&h->side_stream, cudaStreamNonBlocking));
+      CK(h, cudaEventCreateWithFlags(&h->fork_ev, cudaEventDisableTiming));
+      CK(h, cudaEventCreateWithFlags(&h->join_ev, cudaEventDisableTiming));
+    }
+    CK(h, cudaEventRecord(h->fork_ev, st));
+    CK(h, cudaStreamWaitEvent(h->side_stream, h->fork_ev, 0));
+    CK(h, solve_launch(h->plan_mesh, rho_c, fixed, acc_c, h->side_stream, nullptr, amax));
+    CK(h, cudaEventRecord(h->join_ev, h->side_stream));
+    CK(h, solve_launch(h->plan_tiles, rho_f, fixed, acc_f, st, nullptr, amax ? amax + 1 : nullptr));
+    CK(h, cudaStreamWaitEvent(st, h->join_ev, 0));
+  } else if (h->gm.two) {
     {
       TimedScope ts(tm, "solve_coarse", st);
       CK(h, solve_launch(h->plan_mesh, rho_c, fixed, acc_c, st, nullptr, amax));
