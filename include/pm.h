@@ -323,6 +323,17 @@ int pm_check(pm_handle_t* h, void* stream);
 /* Copies the last error message (NUL-terminated, truncated to n). */
 int pm_last_error(const pm_handle_t* h, char* buf, size_t n);
 
+/* Coarse density from a fine one (two-level handles): rho_coarse[C] =
+ * sum_k w(kx) w(ky) w(kz) rho_fine[rc C + k], w(k) = 1 - |k|/rc for
+ * |k| < rc (periodic; rc = coarse_ratio).  For CIC this equals depositing
+ * the particles on the coarse mesh directly (the coarse tent is piecewise
+ * linear on fine nodes), so the float pm_step deposits only the fine mesh
+ * and restricts it; likewise it adds the coarse force, trilinearly
+ * interpolated onto the fine nodes, to the fine force mesh and interpolates
+ * the particles from that one mesh.  float32 [nc^3] / [n^3], overwritten.
+ * No counterpart in the paper. */
+int pm_restrict(pm_handle_t* h, const float* rho_fine, float* rho_coarse, void* stream);
+
 /* Particle-particle acceleration of Eq. 4 (Sec. 2.1) for every particle of
  * the compressed state in[2]: a_i = G sum m_j (x_j - x_i)/|x_j - x_i|^3 over
  * the particles of both species in particle i's fine-mesh cell, pairs closer

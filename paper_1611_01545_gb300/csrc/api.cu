@@ -640,6 +640,13 @@ int pm_checkpoint_wait(pm_handle_t* h) {
   return PM_OK;
 }
 
+int pm_restrict(pm_handle_t* h, const float* rho_fine, float* rho_coarse, void* stream) {
+  if (!h || !rho_fine || !rho_coarse) return fail(h, PM_ERR_ARG, "null argument");
+  if (!h->gm.two) return fail(h, PM_ERR_CONFIG, "pm_restrict needs a two-level handle");
+  CK(h, launch_restrict(rho_fine, h->gm.nf, h->gm.rc, rho_coarse, (cudaStream_t)stream));
+  return PM_OK;
+}
+
 int pm_tile_density(pm_handle_t* h, const float* rho_fine, int64_t tile, float* out, void* stream) {
   if (!h || !rho_fine || !out) return fail(h, PM_ERR_ARG, "null argument");
   if (!h->gm.two || tile < 0 || tile >= h->gm.ntiles()) return fail(h, PM_ERR_ARG, "no such tile");
@@ -648,7 +655,7 @@ int pm_tile_density(pm_handle_t* h, const float* rho_fine, int64_t tile, float* 
 }
 
 static int solve_impl(pm_handle_t* h, const void* rho_c, const void* rho_f, bool fixed, float* acc_c, float* acc_f,
-                      cudaStream_t st, uint32_t* amax = nullptr) {
+                      cudaStream_t st, uint32_t* amax = nullptr, bool prolong = false) {
   Timer* tm = h->timer.on ? &h->timer : nullptr;
   if (h->gm.two && !tm) {
     // The coarse mesh (a few hundred blocks) and the tiles use separate plans,
@@ -662,14 +669,18 @@ static int solve_impl(pm_handle_t* h, const void* rho_c, const void* rho_f, bool
     CK(h, cudaStreamWaitEvent(h->side_stream, h->fork_ev, 0));
     CK(h, solve_launch(h->plan_mesh, rho_c, fixed, acc_c, h->side_stream, nullptr, amax));
     CK(h, cudaEventRecord(h->join_ev, h->side_stream));
-    CK(h, solve_launch(h->plan_tiles, rho_f, fixed, acc_f, st, nullptr, amax ? amax + 1 : nullptr));
+    // with prolongation the tile solve's last pass waits for the coarse force
+    const Prolong pro{acc_c, h->gm.nc, h->gm.rc, h->join_ev};
+    CK(h, solve_launch(h->plan_tiles, rho_f, fixed, acc_f, st, nullptr, amax ? amax + 1 : nullptr,
+                       prolong ? &pro : nullptr));
     CK(h, cudaStreamWaitEvent(st, h->join_ev, 0));
   } else if (h->gm.two) {
     {
       TimedScope ts(tm, "solve_coarse", st);
       CK(h, solve_launch(h->plan_mesh, rho_c, fixed, acc_c, st, nullptr, amax));
     }
-    CK(h, solve_launch(h->plan_tiles, rho_f, fixed, acc_f, st, tm, amax ? amax + 1 : nullptr));
+    const Prolong pro{acc_c, h->gm.nc, h->gm.rc, nullptr};
+    CK(h, solve_launch(h->plan_tiles, rho_f, fixed, acc_f, st, tm, amax ? amax + 1 : nullptr, prolong ? &pro : nullptr));
   } else {
     CK(h, solve_launch(h->plan_mesh, rho_f, fixed, acc_f, st, tm, amax ? amax + 1 : nullptr));
   }
@@ -959,20 +970,27 @@ int step_launch(pm_handle_t* h, const pm_codes_t in[2], pm_codes_t out[2], doubl
   }
   void* rc = fixed ? (void*)h->rho_c_fix : (void*)h->rho_c;
   void* rf = fixed ? (void*)h->rho_f_fix : (void*)h->rho_f;
+  // Float two-level step: the coarse mesh comes from the fine one (CIC
+  // restriction, exact for CIC), and the coarse force is prolongated onto the
+  // fine force mesh as the tile solve writes it, so the particle passes touch
+  // only the fine meshes.  The fixed-point mode keeps the direct integer coarse
+  // deposit and gathers both meshes (bit-reproducible against the plain calls).
+  const bool via_fine = g.two && !fixed;
   {
     TimedScope ts(tm, "deposit", st);
     CK(h, cudaMemsetAsync(rf, 0, (size_t)g.nfine3() * (fixed ? 8 : 4), st));
-    if (g.two) CK(h, cudaMemsetAsync(rc, 0, (size_t)g.ncoarse3() * (fixed ? 8 : 4), st));
+    if (g.two && !via_fine) CK(h, cudaMemsetAsync(rc, 0, (size_t)g.ncoarse3() * 8, st));
     long long M0 = llrint(h->cfg.mass[0] * 4294967296.0), M1 = llrint(h->cfg.mass[1] * 4294967296.0);
     CK(h, zero_work(h, st));
     CK(h, launch_deposit_codes(view(in[0], vel16), view(in[1], vel16), h->off[0], h->off[1], h->geo, dep_blk(h),
-                               (float)h->cfg.mass[0], (float)h->cfg.mass[1], M0, M1, g.two ? rc : nullptr, rf, fixed,
-                               st));
+                               (float)h->cfg.mass[0], (float)h->cfg.mass[1], M0, M1,
+                               (g.two && !via_fine) ? rc : nullptr, rf, fixed, st));
+    if (via_fine) CK(h, launch_restrict(h->rho_f, g.nf, g.rc, h->rho_c, st));
   }
   const bool bound = h->cfg.vmax_mode == 1;
   const float ck = (float)c_kick, cd = (float)c_drift;
   if (bound) CK(h, cudaMemsetAsync(h->amax, 0, 12, st));
-  if (int r = solve_impl(h, rc, rf, fixed, h->acc_c, h->acc_f, st, bound ? h->amax : nullptr)) return r;
+  if (int r = solve_impl(h, rc, rf, fixed, h->acc_c, h->acc_f, st, bound ? h->amax : nullptr, via_fine)) return r;
   if (h->cfg.pp) {
     TimedScope ts(tm, "pp", st);
     CK(h, launch_pp(view(in[0], vel16), view(in[1], vel16), h->off[0], h->off[1], h->geo, (float)h->cfg.mass[0],
@@ -988,7 +1006,7 @@ int step_launch(pm_handle_t* h, const pm_codes_t in[2], pm_codes_t out[2], doubl
     CK(h, launch_ikd_count(view(in[0], vel16), view(in[1], vel16), h->off[0], h->off[1], h->geo, ikd_blk(h, 0),
                            h->acc_c, h->acc_f, ck, cd, h->counts[0], h->counts[1], h->vmax_bits, h->tkey, h->tpv,
                            bound ? out[0].vmax : nullptr, bound ? out[1].vmax : nullptr, h->cfg.pp ? h->app : nullptr,
-                           st));
+                           !via_fine, st));
   }
   {
     TimedScope ts(tm, "scan_out", st);

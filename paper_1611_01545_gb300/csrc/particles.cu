@@ -727,7 +727,9 @@ __global__ void k_deposit_codes(PCodes c0, PCodes c1, const int64_t* off0, const
     int64_t* roff = reinterpret_cast<int64_t*>(smraw);
     Acc* sf = reinterpret_cast<Acc*>(roff + 2 * nrow * (bk.RX + 1));
     Acc* sc = sf + fx * fy * fz;
-    const int nsf = fx * fy * fz, nsc = g.two ? cx * cy * cz : 0;
+    // coarse corners only when a coarse mesh is given (the fused float step restricts the fine mesh instead)
+    const bool dep_coarse = g.two && rho_c != nullptr;
+    const int nsf = fx * fy * fz, nsc = dep_coarse ? cx * cy * cz : 0;
     for (int i = threadIdx.x; i < nsf + nsc; i += blockDim.x) sf[i] = (Acc)0;
     const CellBlock cb = block_of(bk, bid);
     load_row_offsets(off0, g, bk, cb, roff);
@@ -772,7 +774,7 @@ __global__ void k_deposit_codes(PCodes c0, PCodes c1, const int64_t* off0, const
               smem_acc(&sf[((lz + dz) * fy + (ly + dy)) * fx + (lx + dx)], t8[c]);
             }
           }
-          if (g.two) {
+          if (dep_coarse) {
             // Coarse cell == compression cell (coarse_ratio == cmp_ratio), so every
             // particle of a run shares its 8 coarse corners: sum the run in
             // registers and let its last lane do 8 shared-memory adds.
@@ -915,8 +917,11 @@ __device__ __forceinline__ uint32_t window_x(const Geo& g, const Win& w, int lx)
 __global__ void __launch_bounds__(PM_IKD_THREADS, PM_IKD_MIN_BLOCKS) k_ikd_count(PCodes c0, PCodes c1, const int64_t* off0, const int64_t* off1, Geo g, Blk bk,
                             const float* acc_c, const float* acc_f, float ck, float cd, uint32_t* counts0,
                             uint32_t* counts1, uint32_t* vmax_bits, uint32_t* tkey, uint4* tpv,
-                            const float* vq0, const float* vq1, const float4* app) {
+                            const float* vq0, const float* vq1, const float4* app, int coarse) {
   extern __shared__ __align__(16) unsigned char smraw[];
+  // coarse: gather the coarse force separately (0 when the fine force mesh
+  // already carries the prolongated coarse force)
+  const bool two_c = g.two && coarse != 0;
   for_each_block(bk, [&](const int bid) {
     const int r = g.rcmp;
     const int nrow = bk.RY * bk.RZ;
@@ -951,7 +956,7 @@ __global__ void __launch_bounds__(PM_IKD_THREADS, PM_IKD_MIN_BLOCKS) k_ikd_count
           dst[lx] = __ldg(src + gx);
         }
       }
-      if (g.two) {
+      if (two_c) {
         const int nc = g.nc;
         const int64_t nc3 = (int64_t)nc * nc * nc;
         for (int i = threadIdx.x; i < 3 * cx * cy * cz; i += blockDim.x) {
@@ -1012,7 +1017,7 @@ __global__ void __launch_bounds__(PM_IKD_THREADS, PM_IKD_MIN_BLOCKS) k_ikd_count
             w1[d] = __fmul_rn(__int2float_rn(num[d] & 511), 1.0f / 512.0f);
           }
           gather_idx(sf, fx, fy, fz, ixl * r + (num[0] >> 9), ky * r + (num[1] >> 9), kz * r + (num[2] >> 9), w1, a);
-          if (g.two) {
+          if (two_c) {
             // coarse cell == compression cell: corner (ixl, ky, kz), weight (2q + 1) / 512
             float b[3], u1[3];
 #pragma unroll
@@ -1330,13 +1335,13 @@ cudaError_t launch_deposit_codes(const PCodes& c0, const PCodes& c1, const int64
 cudaError_t launch_ikd_count(const PCodes& c0, const PCodes& c1, const int64_t* off0, const int64_t* off1,
                              const Geo& g, const Blk& bk, const float* acc_c, const float* acc_f, float ck, float cd,
                              uint32_t* counts0, uint32_t* counts1, uint32_t* vmax_bits, uint32_t* tkey,
-                             uint4* tpv, const float* vq0, const float* vq1, const float4* app, cudaStream_t st) {
+                             uint4* tpv, const float* vq0, const float* vq1, const float4* app, bool coarse, cudaStream_t st) {
   size_t smem = ikd_count_smem(g, bk);
   int nblk = bk.nbx * bk.nby * bk.nbz;
   cudaFuncSetAttribute(k_ikd_count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   nblk = block_grid(k_ikd_count, bk, PM_IKD_THREADS, smem);
   k_ikd_count<<<nblk, PM_IKD_THREADS, smem, st>>>(c0, c1, off0, off1, g, bk, acc_c, acc_f, ck, cd, counts0, counts1, vmax_bits,
-                                       tkey, tpv, vq0, vq1, app);
+                                       tkey, tpv, vq0, vq1, app, coarse ? 1 : 0);
   note_launches(1);
   return cudaGetLastError();
 }

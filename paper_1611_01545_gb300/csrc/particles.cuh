@@ -65,7 +65,8 @@ cudaError_t launch_deposit_codes(const PCodes& c0, const PCodes& c1, const int64
 cudaError_t launch_ikd_count(const PCodes& c0, const PCodes& c1, const int64_t* off0, const int64_t* off1,
                              const Geo& g, const Blk& bk, const float* acc_c, const float* acc_f, float ck, float cd,
                              uint32_t* counts0, uint32_t* counts1, uint32_t* vmax_bits, uint32_t* tkey,
-                             uint4* tpv, const float* vq0, const float* vq1, const float4* app, cudaStream_t st);
+                             uint4* tpv, const float* vq0, const float* vq1, const float4* app, bool coarse,
+                             cudaStream_t st);
 cudaError_t launch_ikd_scatter(int64_t n0, int64_t n1, const int64_t* off0, const int64_t* off1, const Geo& g,
                                const Blk& bk, uint32_t* counts0, uint32_t* counts1, const int64_t* newoff0,
                                const int64_t* newoff1, const PCodesOut& o0, const PCodesOut& o1, const uint32_t* tkey,

@@ -48,9 +48,20 @@ struct SolvePlan {
 void note_launches(int k);
 
 // Launch helpers implemented in solve.cu.
-// amax (optional): atomicMax of max |a| over the written force values, as float bits.
+// Prolongation added by the last solve pass: the coarse force [3][nc^3] (rc
+// fine cells per coarse cell) interpolated onto the written fine nodes, after
+// waiting for `ready` (may be null) on the launching stream.
+struct Prolong {
+  const float* coarse;
+  int nc, rc;
+  cudaEvent_t ready;
+};
+// amax (optional): atomicMax of max |a| over the written force values (before
+// any prolongation is added), as float bits.
 cudaError_t solve_launch(const SolvePlan& p, const void* src, bool src_fixed, float* dst, cudaStream_t st,
-                         struct Timer* timer, unsigned int* amax = nullptr);
+                         struct Timer* timer, unsigned int* amax = nullptr, const Prolong* pro = nullptr);
+// Coarse density from the fine one (CIC restriction, float32).
+cudaError_t launch_restrict(const float* rho_f, int nf, int rc, float* rho_c, cudaStream_t st);
 // Transpose of the periodic-mesh solve (adjoint): lam_rho = A^T lam_acc; spec3comp holds
 // the three component spectra [3][N][N][N/2+1].
 cudaError_t solve_adjoint_launch(const SolvePlan& p, const float* lam_acc, float* lam_rho, float2* spec3comp,

@@ -51,6 +51,8 @@ struct SolveArgs {
   float* dst;
   int comp_mode;   // pass A only: blockIdx.y selects component pb of a [3][n^3] source at origin 0
   unsigned int* amax;   // pass C: if set, atomicMax of max |output| (float bits; values are >= 0)
+  const float* pc;      // pass C: if set, add this coarse force [3][pnc^3] trilinearly prolongated to the fine nodes
+  int pnc, prc;         // its edge and the fine cells per coarse cell (a power of two dividing t)
 };
 
 __device__ __forceinline__ int pmod(int a, int n) {
@@ -269,6 +271,33 @@ __global__ void __launch_bounds__(SolveCfg<N>::threads_c) k_solve_c(SolveArgs a)
   int ox, oy, oz;
   problem_origin(a, a.p0 + pb, ox, oy, oz);
   const int n = a.src_n;
+  // Prolongation of the coarse force onto this output plane: the coarse values
+  // around the tile interior, interpolated in z, staged in P (free by now).
+  float* Q = reinterpret_cast<float*>(P);
+  const int nq = a.pc ? a.t / a.prc + 1 : 0;
+  int lr = 0;
+  float inv_r = 0.f;
+  if (a.pc) {
+    lr = __ffs(a.prc) - 1;
+    inv_r = 1.0f / (float)a.prc;
+    const int gz = oz + a.b + zo;
+    const int cz0 = gz >> lr, cz1 = cz0 + 1 == a.pnc ? 0 : cz0 + 1;
+    const float wz = (float)(gz & (a.prc - 1)) * inv_r;
+    const int cyb = (oy + a.b) >> lr, cxb = (ox + a.b) >> lr;
+    const float* c0 = a.pc + ((size_t)d * a.pnc + cz0) * a.pnc * a.pnc;
+    const float* c1 = a.pc + ((size_t)d * a.pnc + cz1) * a.pnc * a.pnc;
+    PM_ROWS(qy, nq) {
+      int cy = cyb + qy;
+      if (cy >= a.pnc) cy -= a.pnc;
+      PM_COLS(qx, nq) {
+        int cx = cxb + qx;
+        if (cx >= a.pnc) cx -= a.pnc;
+        const size_t o = (size_t)cy * a.pnc + cx;
+        Q[qy * nq + qx] = (1.0f - wz) * __ldg(c0 + o) + wz * __ldg(c1 + o);
+      }
+    }
+    __syncthreads();
+  }
   // Output cells are interior cells: origin + b + local lies inside [0, n) without wrap.
   const int gz = oz + a.b + zo;
   float* dst = a.dst + (size_t)d * n * n * n + ((int64_t)gz * n + oy + a.b) * n + ox + a.b;
@@ -277,9 +306,16 @@ __global__ void __launch_bounds__(SolveCfg<N>::threads_c) k_solve_c(SolveArgs a)
     const float* w = reinterpret_cast<const float*>(W + (yl >> 1) * N + a.b) + (yl & 1);
     float* drow = dst + (int64_t)yl * n;
     PM_COLS(xl, a.t) {
-      const float val = w[2 * xl];
-      drow[xl] = val;
+      float val = w[2 * xl];
       m = fmaxf(m, fabsf(val));
+      if (a.pc) {
+        const int qy = yl >> lr, qx = xl >> lr;
+        const float fy = (float)(yl & (a.prc - 1)) * inv_r, fx = (float)(xl & (a.prc - 1)) * inv_r;
+        const float* q = Q + qy * nq + qx;
+        const float lo = fmaf(fx, q[1] - q[0], q[0]), hi = fmaf(fx, q[nq + 1] - q[nq], q[nq]);
+        val += fmaf(fy, hi - lo, lo);
+      }
+      drow[xl] = val;
     }
   }
   if (a.amax) {
@@ -305,7 +341,7 @@ __global__ void k_tile_window(const float* src, int src_n, int nts, int t, int b
 
 template <int N>
 static cudaError_t solve_n(const SolvePlan& p, const void* src, bool fixed, float* dst, cudaStream_t st, Timer* tm,
-                           unsigned int* amax) {
+                           unsigned int* amax, const Prolong* pro) {
   using C = SolveCfg<N>;
   static bool attr_done = false;
   if (!attr_done) {
@@ -318,7 +354,8 @@ static cudaError_t solve_n(const SolvePlan& p, const void* src, bool fixed, floa
   const int nprob = p.nts * p.nts * p.nts;
   for (int p0 = 0; p0 < nprob; p0 += p.batch) {
     int nb = (nprob - p0 < p.batch) ? (nprob - p0) : p.batch;
-    SolveArgs a{src, fixed ? 1 : 0, p.src_n, p.nts, p.t, p.b, p0, p.spec, p.spec3, p.kern, p.tw, dst, 0, amax};
+    SolveArgs a{src, fixed ? 1 : 0, p.src_n, p.nts, p.t, p.b, p0, p.spec, p.spec3, p.kern, p.tw, dst, 0, amax,
+                pro ? pro->coarse : nullptr, pro ? pro->nc : 0, pro ? pro->rc : 1};
     {
       TimedScope ts(tm, N == p.src_n && p.b == 0 ? "fft_a_mesh" : "fft_a_tiles", st);
       if (fixed) k_solve_a<N, true><<<dim3(N, nb), C::threads, C::smem_a, st>>>(a);
@@ -327,6 +364,10 @@ static cudaError_t solve_n(const SolvePlan& p, const void* src, bool fixed, floa
     {
       TimedScope ts(tm, N == p.src_n && p.b == 0 ? "fft_b_mesh" : "fft_b_tiles", st);
       k_solve_b<N><<<dim3(N, 2, nb), PassB<N>::threads, PassB<N>::smem, st>>>(a);
+    }
+    if (pro && pro->ready && p0 == 0) {
+      cudaError_t e = cudaStreamWaitEvent(st, pro->ready, 0);   // the coarse force must be complete
+      if (e != cudaSuccess) return e;
     }
     {
       TimedScope ts(tm, N == p.src_n && p.b == 0 ? "fft_c_mesh" : "fft_c_tiles", st);
@@ -340,14 +381,15 @@ static cudaError_t solve_n(const SolvePlan& p, const void* src, bool fixed, floa
 }
 
 cudaError_t solve_launch(const SolvePlan& p, const void* src, bool fixed, float* dst, cudaStream_t st, Timer* tm,
-                         unsigned int* amax) {
+                         unsigned int* amax, const Prolong* pro) {
+  if (pro && (p.t % pro->rc || (pro->rc & (pro->rc - 1)))) return cudaErrorInvalidValue;
   switch (p.N) {
-    case 16: return solve_n<16>(p, src, fixed, dst, st, tm, amax);
-    case 32: return solve_n<32>(p, src, fixed, dst, st, tm, amax);
-    case 48: return solve_n<48>(p, src, fixed, dst, st, tm, amax);
-    case 64: return solve_n<64>(p, src, fixed, dst, st, tm, amax);
-    case 96: return solve_n<96>(p, src, fixed, dst, st, tm, amax);
-    case 128: return solve_n<128>(p, src, fixed, dst, st, tm, amax);
+    case 16: return solve_n<16>(p, src, fixed, dst, st, tm, amax, pro);
+    case 32: return solve_n<32>(p, src, fixed, dst, st, tm, amax, pro);
+    case 48: return solve_n<48>(p, src, fixed, dst, st, tm, amax, pro);
+    case 64: return solve_n<64>(p, src, fixed, dst, st, tm, amax, pro);
+    case 96: return solve_n<96>(p, src, fixed, dst, st, tm, amax, pro);
+    case 128: return solve_n<128>(p, src, fixed, dst, st, tm, amax, pro);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -393,6 +435,51 @@ cudaError_t tile_window_launch(const SolvePlan& p, const float* src, int64_t til
     case 128: k_tile_window<128><<<blocks, 256, 0, st>>>(src, p.src_n, p.nts, p.t, p.b, tile, out); break;
     default: return cudaErrorInvalidValue;
   }
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+// Coarse CIC density from the fine one (exact for CIC: the coarse tent is the
+// fine-node interpolation of itself): rho_c(C) = sum_k w(kx) w(ky) w(kz)
+// rho_f(rc C + k), w(k) = 1 - |k| / rc, k = -(rc-1) .. rc-1, periodic.  One
+// block per coarse (y, z) row: threads sum the (2 rc - 1)^2 fine rows with
+// their y, z weights along x into shared memory, then the x weights.
+__global__ void k_restrict(const float* rho_f, int nf, int rc, float* rho_c) {
+  extern __shared__ float acc[];   // [nf]
+  const int nc = nf / rc;
+  const int cy = blockIdx.x % nc, cz = blockIdx.x / nc;
+  const float inv = 1.0f / (float)rc;
+  for (int x = threadIdx.x; x < nf; x += blockDim.x) {
+    float s = 0.f;
+    for (int kz = 1 - rc; kz < rc; ++kz) {
+      int z = rc * cz + kz;
+      z += z < 0 ? nf : (z >= nf ? -nf : 0);
+      const float wz = 1.0f - (float)(kz < 0 ? -kz : kz) * inv;
+      for (int ky = 1 - rc; ky < rc; ++ky) {
+        int y = rc * cy + ky;
+        y += y < 0 ? nf : (y >= nf ? -nf : 0);
+        const float wy = 1.0f - (float)(ky < 0 ? -ky : ky) * inv;
+        s = fmaf(wz * wy, __ldg(rho_f + ((size_t)z * nf + y) * nf + x), s);
+      }
+    }
+    acc[x] = s;
+  }
+  __syncthreads();
+  for (int cx = threadIdx.x; cx < nc; cx += blockDim.x) {
+    float t = 0.f;
+    for (int kx = 1 - rc; kx < rc; ++kx) {
+      int x = rc * cx + kx;
+      x += x < 0 ? nf : (x >= nf ? -nf : 0);
+      t = fmaf(1.0f - (float)(kx < 0 ? -kx : kx) * inv, acc[x], t);
+    }
+    rho_c[((size_t)cz * nc + cy) * nc + cx] = t;
+  }
+}
+
+cudaError_t launch_restrict(const float* rho_f, int nf, int rc, float* rho_c, cudaStream_t st) {
+  if (rc < 1 || nf % rc) return cudaErrorInvalidValue;
+  const int nc = nf / rc;
+  k_restrict<<<nc * nc, 256, (size_t)nf * sizeof(float), st>>>(rho_f, nf, rc, rho_c);
   note_launches(1);
   return cudaGetLastError();
 }

@@ -266,6 +266,12 @@ class PM:
                                      for a, b in zip(lam_x, lam_v)])
         self._err(self.lib.pm_step_adjoint(self.h, st, lam, c_kick, c_drift, _stream(stream)))
 
+    def restrict(self, rho_fine: torch.Tensor, stream=None) -> torch.Tensor:
+        """Coarse density from a fine one (CIC restriction)."""
+        out = torch.empty((self.n_coarse,) * 3, dtype=torch.float32, device="cuda")
+        self._err(self.lib.pm_restrict(self.h, _ptr(rho_fine), _ptr(out), _stream(stream)))
+        return out
+
     def pp_accel(self, codes: Sequence[Codes], stream=None) -> torch.Tensor:
         """Eq. 4 accelerations [n0 + n1, 4] (x, y, z, 0), stream order, species 0 first."""
         acc = torch.empty((codes[0].n + codes[1].n, 4), dtype=torch.float32, device="cuda")

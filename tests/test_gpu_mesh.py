@@ -51,6 +51,10 @@ def test_deposit_float_parity(name, n_cdm, n_nu):
     assert rel_rms(rf2.cpu().numpy(), ref_f) < DENSITY_TOL
     if w.coarse_ratio > 1:
         assert rel_rms(rc2.cpu().numpy(), ref_c) < DENSITY_TOL
+        # coarse density by restriction of the fine one (what the float step uses)
+        rc3 = pm.restrict(rf)
+        pm.check()
+        assert rel_rms(rc3.cpu().numpy(), ref_c) < DENSITY_TOL
 
 
 @pytest.mark.parametrize("name,n_cdm,n_nu", CASES)
