@@ -661,6 +661,14 @@ __device__ __forceinline__ int row_cell(const int64_t* ro, int RX, int64_t p) {
   return lo;
 }
 
+// 4-byte global -> shared copy that does not stall the issuing thread
+// (cp.async); async_copies_wait() waits for all of the thread's copies.
+__device__ __forceinline__ void copy_async4(float* smem_dst, const float* gmem_src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void async_copies_wait() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 __device__ __forceinline__ void smem_acc(long long* a, long long v) {
   atomicAdd(reinterpret_cast<unsigned long long*>(a), (unsigned long long)v);
 }
@@ -953,9 +961,10 @@ __global__ void __launch_bounds__(PM_IKD_THREADS, PM_IKD_MIN_BLOCKS) k_ikd_count
         for (int lx = threadIdx.x & 31; lx < fx; lx += 32) {
           int gx = bxf + lx;
           if (gx >= nf) gx -= nf;
-          dst[lx] = __ldg(src + gx);
+          copy_async4(dst + lx, src + gx);   // all of a thread's copies in flight at once
         }
       }
+      async_copies_wait();
       if (two_c) {
         const int nc = g.nc;
         const int64_t nc3 = (int64_t)nc * nc * nc;

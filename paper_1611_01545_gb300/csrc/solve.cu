@@ -69,6 +69,22 @@ __device__ __forceinline__ void problem_origin(const SolveArgs& a, int p, int& o
 
 // Row loops below give each warp whole rows and each lane strided columns, so
 // row indices are computed once per row and no division is needed.
+// Global -> shared copies that do not stall the issuing thread (cp.async);
+// async_wait() waits for all of the thread's copies (a barrier must follow).
+__device__ __forceinline__ void async_copy4(void* smem_dst, const void* gmem_src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"((unsigned)__cvta_generic_to_shared(smem_dst)),
+               "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void async_copy8(void* smem_dst, const void* gmem_src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"((unsigned)__cvta_generic_to_shared(smem_dst)),
+               "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void async_copy16(void* smem_dst, const void* gmem_src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"((unsigned)__cvta_generic_to_shared(smem_dst)),
+               "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void async_wait() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 #define PM_ROWS(row, nrows) for (int row = threadIdx.x >> 5; row < (nrows); row += (blockDim.x >> 5))
 #define PM_COLS(col, ncols) for (int col = threadIdx.x & 31; col < (ncols); col += 32)
 
@@ -103,8 +119,14 @@ __global__ void __launch_bounds__(SolveCfg<N>::threads) k_solve_a(SolveArgs a) {
   PM_ROWS(y, N) {
     const int64_t rowbase = ((int64_t)gz * n + wrap1(oy + y, n)) * n;
     float* w = reinterpret_cast<float*>(W + (y >> 1) * N) + (y & 1);
-    PM_COLS(x, N) w[2 * x] = src_value<FIXED>(src, rowbase + wrap1(ox + x, n));
+    if (FIXED) {
+      PM_COLS(x, N) w[2 * x] = src_value<FIXED>(src, rowbase + wrap1(ox + x, n));
+    } else {
+      const float* srow = static_cast<const float*>(src) + rowbase;
+      PM_COLS(x, N) async_copy4(w + 2 * x, srow + wrap1(ox + x, n));
+    }
   }
+  if (!FIXED) async_wait();
   __syncthreads();
   fft_fwd<N, N / 2, N, 1>(W, tw);
   // Unpack the two real rows of each packed row: A = (Z_k + conj Z_-k)/2, B = (Z_k - conj Z_-k)/(2i).
@@ -155,8 +177,10 @@ __global__ void __launch_bounds__(PassB<N>::threads) k_solve_b(SolveArgs a) {
   const float2* in = a.spec + (size_t)pb * N * N * NH + (size_t)ys * NH + kx0;
   for (int i = threadIdx.x; i < N * KC; i += blockDim.x) {
     const int z = i / KC, c = i - z * KC;
-    F[i] = c < ncol ? in[(size_t)z * N * NH + c] : make_float2(0.f, 0.f);
+    if (c < ncol) async_copy8(F + i, in + (size_t)z * N * NH + c);
+    else F[i] = make_float2(0.f, 0.f);
   }
+  async_wait();
   __syncthreads();
   fft_fwd<N, KC, 1, KC>(F, tw);
   const float* K = a.kern + (size_t)ys * NH + kx0;
@@ -246,7 +270,8 @@ __global__ void __launch_bounds__(SolveCfg<N>::threads_c) k_solve_c(SolveArgs a)
   const int pb = blockIdx.z;
   const float4* in = reinterpret_cast<const float4*>(a.spec3 + (((size_t)pb * 3 + d) * a.t + zo) * N * NH);
   float4* P4 = reinterpret_cast<float4*>(P);
-  for (int i = threadIdx.x; i < N * NH / 2; i += blockDim.x) P4[i] = in[i];
+  for (int i = threadIdx.x; i < N * NH / 2; i += blockDim.x) async_copy16(P4 + i, in + i);
+  async_wait();
   __syncthreads();
   fft_inv<N, NH, 1, NH>(P, tw);
   const int half_rows = a.t / 2;
