@@ -424,7 +424,7 @@ int pm_init(const pm_config_t* cfg, pm_handle_t** out) {
   h->scratch_n = c.count[0] + c.count[1];
   A(&h->tkey, (size_t)h->scratch_n * 4);
   A(&h->tpv, (size_t)h->scratch_n * 16);
-  A(&h->partial, scan_partial_bytes((int64_t)ncell));
+  A(&h->partial, 2 * scan_partial_bytes((int64_t)ncell));
   A(&h->status, 4);
   // plans and tables
   auto make_plan = [&](SolvePlan& p, int N, int nts, int t, int b, int src_n, int batch, const std::vector<float>& kern) {
@@ -560,7 +560,7 @@ int pm_deposit_codes(pm_handle_t* h, const pm_codes_t in[2], void* rho_coarse, v
   cudaStream_t st = (cudaStream_t)stream;
   const bool fixed = h->cfg.deposit_mode == 1;
   const bool vel16 = h->cfg.vel_bits == 16;
-  for (int s = 0; s < 2; ++s) CK(h, scan_codes(in[s], h->gm.ncell(), h->off[s], h->partial, h->status, st));
+  CK(h, scan_codes2(in, h->gm.ncell(), h->off[0], h->off[1], h->partial, h->status, st));
   long long M0 = llrint(h->cfg.mass[0] * 4294967296.0), M1 = llrint(h->cfg.mass[1] * 4294967296.0);
   CK(h, zero_work(h, st));
   CK(h, launch_deposit_codes(view(in[0], vel16), view(in[1], vel16), h->off[0], h->off[1], h->geo, dep_blk(h),
@@ -579,7 +579,7 @@ int pm_pp_accel(pm_handle_t* h, const pm_codes_t in[2], float* acc, void* stream
   if (!(h->cfg.r_soft >= 0.0 && h->cfg.r_soft < 1.0)) return fail(h, PM_ERR_ARG, "r_soft must lie in [0, 1)");
   cudaStream_t st = (cudaStream_t)stream;
   const bool vel16 = h->cfg.vel_bits == 16;
-  for (int s = 0; s < 2; ++s) CK(h, scan_codes(in[s], h->gm.ncell(), h->off[s], h->partial, h->status, st));
+  CK(h, scan_codes2(in, h->gm.ncell(), h->off[0], h->off[1], h->partial, h->status, st));
   CK(h, launch_pp(view(in[0], vel16), view(in[1], vel16), h->off[0], h->off[1], h->geo, (float)h->cfg.mass[0],
                   (float)h->cfg.mass[1], (float)h->cfg.G, (float)h->cfg.r_soft, reinterpret_cast<float4*>(acc), nullptr,
                   st));
@@ -966,7 +966,7 @@ int step_launch(pm_handle_t* h, const pm_codes_t in[2], pm_codes_t out[2], doubl
   const int64_t ncell = g.ncell();
   {
     TimedScope ts(tm, "scan_in", st);
-    for (int s = 0; s < 2; ++s) CK(h, scan_codes(in[s], ncell, h->off[s], h->partial, h->status, st));
+    CK(h, scan_codes2(in, ncell, h->off[0], h->off[1], h->partial, h->status, st));
   }
   void* rc = fixed ? (void*)h->rho_c_fix : (void*)h->rho_c;
   void* rf = fixed ? (void*)h->rho_f_fix : (void*)h->rho_f;
@@ -1010,10 +1010,10 @@ int step_launch(pm_handle_t* h, const pm_codes_t in[2], pm_codes_t out[2], doubl
   }
   {
     TimedScope ts(tm, "scan_out", st);
-    for (int s = 0; s < 2; ++s) {
-      if (!bound) CK(h, launch_set_vmax(h->vmax_bits + s, out[s].vmax, st));
-      CK(h, scan_counts(h->counts[s], ncell, in[s].n, h->newoff[s], out[s], h->partial, h->status, st));
-    }
+    if (!bound) CK(h, launch_set_vmax2(h->vmax_bits, out[0].vmax, out[1].vmax, st));
+    const int64_t expect[2] = {in[0].n, in[1].n};
+    CK(h, scan_counts2(h->counts[0], h->counts[1], ncell, expect, h->newoff[0], h->newoff[1], out, h->partial,
+                       h->status, st));
   }
   {
     TimedScope ts(tm, "ikd_scatter", st);

@@ -93,8 +93,16 @@ struct U32Count {
   }
 };
 
+// Each scan launch serves one or two species: blockIdx.y (blockIdx.x for the
+// one-block kernels) selects the species' getter / output and its partials
+// (stride pstride V2 per species).
+template <class T> struct Pair { T v[2]; };
+
 template <class Get>
-__global__ void __launch_bounds__(SCAN_THREADS) k_scan_reduce(Get get, int64_t n, V2* partial) {
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_reduce(Pair<Get> gets, int64_t n, V2* partial_all,
+                                                            int pstride) {
+  const Get& get = gets.v[blockIdx.y];
+  V2* partial = partial_all + (size_t)blockIdx.y * pstride;
   const int64_t base = (int64_t)blockIdx.x * SCAN_TILE;
   V2 s{0, 0};
   for (int i = threadIdx.x; i < SCAN_TILE; i += SCAN_THREADS) {
@@ -106,8 +114,9 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_reduce(Get get, int64_t n
   if (threadIdx.x == 0) partial[blockIdx.x] = tot;
 }
 
-// Exclusive scan of the partials in place (one block); partial[nb] = grand total.
-__global__ void __launch_bounds__(1024) k_scan_partials(V2* partial, int nb) {
+// Exclusive scan of the partials in place (one block per species); partial[nb] = grand total.
+__global__ void __launch_bounds__(1024) k_scan_partials(V2* partial_all, int nb, int pstride) {
+  V2* partial = partial_all + (size_t)blockIdx.x * pstride;
   __shared__ V2 carry;
   if (threadIdx.x == 0) carry = V2{0, 0};
   __syncthreads();
@@ -154,7 +163,11 @@ struct PutCodes {
 };
 
 template <class Get, class Put>
-__global__ void __launch_bounds__(SCAN_THREADS) k_scan_final(Get get, Put put, int64_t n, const V2* partial) {
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_final(Pair<Get> gets, Pair<Put> puts, int64_t n,
+                                                           const V2* partial_all, int pstride) {
+  const Get& get = gets.v[blockIdx.y];
+  const Put& put = puts.v[blockIdx.y];
+  const V2* partial = partial_all + (size_t)blockIdx.y * pstride;
   const int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
   V2 v[SCAN_ITEMS];
   V2 s{0, 0};
@@ -174,62 +187,125 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_final(Get get, Put put, i
   }
 }
 
-// Writes off[n] = total, checks the total and the escape list, sets n_esc / vmax if asked.
-__global__ void k_scan_finish(const V2* partial, int nb, int64_t n, int64_t expect, int64_t* off, int* status,
-                              uint32_t* n_esc_out, int64_t esc_cap) {
-  V2 t = partial[nb];
-  off[n] = t.a;
-  if (t.a != expect) atomicOr(status, ST_CORRUPT);
-  if (n_esc_out) *n_esc_out = (uint32_t)(t.b < esc_cap ? t.b : esc_cap);
+struct FinishArgs {
+  int64_t expect;
+  int64_t* off;
+  uint32_t* n_esc_out;   // set for compressed outputs
+  int64_t esc_cap;
+};
+
+// Writes off[n] = total, checks the total, sets n_esc if asked; thread s = species s.
+__global__ void k_scan_finish(const V2* partial_all, int nb, int pstride, int64_t n, Pair<FinishArgs> fa, int nsp,
+                              int* status) {
+  const int s = threadIdx.x;
+  if (s >= nsp) return;
+  const FinishArgs& f = fa.v[s];
+  V2 t = partial_all[(size_t)s * pstride + nb];
+  f.off[n] = t.a;
+  if (t.a != f.expect) atomicOr(status, ST_CORRUPT);
+  if (f.n_esc_out) *f.n_esc_out = (uint32_t)(t.b < f.esc_cap ? t.b : f.esc_cap);
 }
 
-// Every escape entry must name a cell whose byte is 255, hold >= 255, ascend.
-__global__ void k_check_escapes(const uint8_t* cnt, const uint32_t* esc, const uint32_t* n_esc, int64_t esc_cap,
-                                int64_t ncell, const float* vmax, int* status) {
-  long long ne = *n_esc;
+struct EscArgs {
+  const uint8_t* cnt;
+  const uint32_t* esc;
+  const uint32_t* n_esc;
+  int64_t esc_cap;
+  const float* vmax;
+};
+
+// Every escape entry must name a cell whose byte is 255, hold >= 255, ascend; blockIdx.y = species.
+__global__ void k_check_escapes(Pair<EscArgs> ea, int64_t ncell, int* status) {
+  const EscArgs& e = ea.v[blockIdx.y];
+  long long ne = *e.n_esc;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
-    float vm = *vmax;
+    float vm = *e.vmax;
     if (!(vm >= 0.f) || isinf(vm)) atomicOr(status, ST_CORRUPT);
-    if (ne > esc_cap) atomicOr(status, ST_CORRUPT);
+    if (ne > e.esc_cap) atomicOr(status, ST_CORRUPT);
   }
-  if (ne > esc_cap) ne = esc_cap;
+  if (ne > e.esc_cap) ne = e.esc_cap;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < ne; i += (long long)gridDim.x * blockDim.x) {
-    uint32_t c = esc[2 * i], k = esc[2 * i + 1];
-    bool bad = (int64_t)c >= ncell || k < 255u || cnt[c] != 255u || (i > 0 && esc[2 * (i - 1)] >= c);
+    uint32_t c = e.esc[2 * i], k = e.esc[2 * i + 1];
+    bool bad = (int64_t)c >= ncell || k < 255u || e.cnt[c] != 255u || (i > 0 && e.esc[2 * (i - 1)] >= c);
     if (bad) atomicOr(status, ST_CORRUPT);
   }
 }
 
 static int scan_blocks(int64_t n) { return (int)((n + SCAN_TILE - 1) / SCAN_TILE); }
 
+// Offsets of nsp (1 or 2) species' input codes in one set of launches.
+static cudaError_t scan_codes_n(const pm_codes_t* in, int nsp, int64_t ncell, int64_t* const* off, void* partial_ws,
+                                int* status, cudaStream_t st) {
+  V2* partial = static_cast<V2*>(partial_ws);
+  const int nb = scan_blocks(ncell), ps = nb + 1;
+  Pair<CodesCount> get{};
+  Pair<PutOffsets> put{};
+  Pair<FinishArgs> fin{};
+  Pair<EscArgs> esc{};
+  for (int s = 0; s < nsp; ++s) {
+    get.v[s] = CodesCount{in[s].cnt, in[s].esc, in[s].n_esc, in[s].esc_cap, status};
+    put.v[s] = PutOffsets{off[s]};
+    fin.v[s] = FinishArgs{in[s].n, off[s], nullptr, 0};
+    esc.v[s] = EscArgs{in[s].cnt, in[s].esc, in[s].n_esc, in[s].esc_cap, in[s].vmax};
+  }
+  k_check_escapes<<<dim3(64, nsp), 256, 0, st>>>(esc, ncell, status);
+  k_scan_reduce<<<dim3(nb, nsp), SCAN_THREADS, 0, st>>>(get, ncell, partial, ps);
+  k_scan_partials<<<nsp, 1024, 0, st>>>(partial, nb, ps);
+  k_scan_final<<<dim3(nb, nsp), SCAN_THREADS, 0, st>>>(get, put, ncell, partial, ps);
+  k_scan_finish<<<1, 32, 0, st>>>(partial, nb, ps, ncell, fin, nsp, status);
+  note_launches(5);
+  return cudaGetLastError();
+}
+
 cudaError_t scan_codes(const pm_codes_t& in, int64_t ncell, int64_t* off, void* partial_ws, int* status,
                        cudaStream_t st) {
+  int64_t* offs[1] = {off};
+  return scan_codes_n(&in, 1, ncell, offs, partial_ws, status, st);
+}
+
+cudaError_t scan_codes2(const pm_codes_t in[2], int64_t ncell, int64_t* off0, int64_t* off1, void* partial_ws,
+                        int* status, cudaStream_t st) {
+  int64_t* offs[2] = {off0, off1};
+  return scan_codes_n(in, 2, ncell, offs, partial_ws, status, st);
+}
+
+static cudaError_t scan_counts_n(const uint32_t* const* counts, int nsp, int64_t ncell, const int64_t* expect,
+                                 int64_t* const* off, pm_codes_t* out, void* partial_ws, int* status,
+                                 cudaStream_t st) {
   V2* partial = static_cast<V2*>(partial_ws);
-  int nb = scan_blocks(ncell);
-  CodesCount get{in.cnt, in.esc, in.n_esc, in.esc_cap, status};
-  k_check_escapes<<<64, 256, 0, st>>>(in.cnt, in.esc, in.n_esc, in.esc_cap, ncell, in.vmax, status);
-  k_scan_reduce<<<nb, SCAN_THREADS, 0, st>>>(get, ncell, partial);
-  k_scan_partials<<<1, 1024, 0, st>>>(partial, nb);
-  k_scan_final<<<nb, SCAN_THREADS, 0, st>>>(get, PutOffsets{off}, ncell, partial);
-  k_scan_finish<<<1, 1, 0, st>>>(partial, nb, ncell, in.n, off, status, nullptr, 0);
-  note_launches(5);
+  const int nb = scan_blocks(ncell), ps = nb + 1;
+  Pair<U32Count> get{};
+  Pair<PutCodes> put{};
+  Pair<FinishArgs> fin{};
+  for (int s = 0; s < nsp; ++s) {
+    get.v[s] = U32Count{counts[s]};
+    put.v[s] = PutCodes{off[s], out[s].cnt, out[s].esc, out[s].esc_cap, status};
+    fin.v[s] = FinishArgs{expect[s], off[s], out[s].n_esc, out[s].esc_cap};
+  }
+  k_scan_reduce<<<dim3(nb, nsp), SCAN_THREADS, 0, st>>>(get, ncell, partial, ps);
+  k_scan_partials<<<nsp, 1024, 0, st>>>(partial, nb, ps);
+  k_scan_final<<<dim3(nb, nsp), SCAN_THREADS, 0, st>>>(get, put, ncell, partial, ps);
+  k_scan_finish<<<1, 32, 0, st>>>(partial, nb, ps, ncell, fin, nsp, status);
+  note_launches(4);
   return cudaGetLastError();
 }
 
 cudaError_t scan_counts(const uint32_t* counts, int64_t ncell, int64_t expect, int64_t* off, pm_codes_t& out,
                         void* partial_ws, int* status, cudaStream_t st) {
-  V2* partial = static_cast<V2*>(partial_ws);
-  int nb = scan_blocks(ncell);
-  U32Count get{counts};
-  k_scan_reduce<<<nb, SCAN_THREADS, 0, st>>>(get, ncell, partial);
-  k_scan_partials<<<1, 1024, 0, st>>>(partial, nb);
-  k_scan_final<<<nb, SCAN_THREADS, 0, st>>>(get, PutCodes{off, out.cnt, out.esc, out.esc_cap, status}, ncell,
-                                             partial);
-  k_scan_finish<<<1, 1, 0, st>>>(partial, nb, ncell, expect, off, status, out.n_esc, out.esc_cap);
-  note_launches(4);
-  return cudaGetLastError();
+  const uint32_t* c[1] = {counts};
+  int64_t* o[1] = {off};
+  return scan_counts_n(c, 1, ncell, &expect, o, &out, partial_ws, status, st);
 }
 
+cudaError_t scan_counts2(const uint32_t* counts0, const uint32_t* counts1, int64_t ncell, const int64_t expect[2],
+                         int64_t* off0, int64_t* off1, pm_codes_t out[2], void* partial_ws, int* status,
+                         cudaStream_t st) {
+  const uint32_t* c[2] = {counts0, counts1};
+  int64_t* o[2] = {off0, off1};
+  return scan_counts_n(c, 2, ncell, expect, o, out, partial_ws, status, st);
+}
+
+// Partials of one species; the two-species scans use twice this.
 size_t scan_partial_bytes(int64_t ncell) { return sizeof(V2) * (size_t)(scan_blocks(ncell) + 1); }
 
 // ------------------------------------------------- plain per-particle -----
@@ -918,6 +994,10 @@ __device__ __forceinline__ uint32_t window_x(const Geo& g, const Win& w, int lx)
 #ifndef PM_IKD_MIN_BLOCKS
 #define PM_IKD_MIN_BLOCKS 2
 #endif
+// Scratch records a scatter thread loads before placing any of them.
+#ifndef PM_SCATTER_UNROLL
+#define PM_SCATTER_UNROLL 2
+#endif
 #ifndef PM_SCATTER_MIN_BLOCKS
 #define PM_SCATTER_MIN_BLOCKS 4
 #endif
@@ -1171,20 +1251,22 @@ __global__ void __launch_bounds__(PM_SCATTER_THREADS, PM_SCATTER_MIN_BLOCKS) k_i
       for (int row = 0; row < nrow; ++row) {
         const int64_t* ro = roff + (s * nrow + row) * (bk.RX + 1);
         const int64_t p0 = ro[0] < n ? ro[0] : n, p1 = ro[bk.RX] < n ? ro[bk.RX] : n;
-        // Two particles per thread per iteration keep more independent loads in flight.
-        for (int64_t p = p0 + threadIdx.x; p < p1; p += 2 * blockDim.x) {
-          const int64_t pp[2] = {p, p + blockDim.x};
-          uint32_t tk[2];
-          uint4 pv[2];
+        // PM_SCATTER_UNROLL particles per thread per iteration, all loaded
+        // before any is placed, keep that many independent loads in flight.
+        for (int64_t p = p0 + threadIdx.x; p < p1; p += PM_SCATTER_UNROLL * (int64_t)blockDim.x) {
+          int64_t pp[PM_SCATTER_UNROLL];
+          uint32_t tk[PM_SCATTER_UNROLL];
+          uint4 pv[PM_SCATTER_UNROLL];
 #pragma unroll
-          for (int u = 0; u < 2; ++u) {
+          for (int u = 0; u < PM_SCATTER_UNROLL; ++u) {
+            pp[u] = p + u * (int64_t)blockDim.x;
             if (pp[u] < p1) {
               tk[u] = tkey[toff + pp[u]];
               pv[u] = tpv[toff + pp[u]];
             }
           }
 #pragma unroll
-          for (int u = 0; u < 2; ++u) {
+          for (int u = 0; u < PM_SCATTER_UNROLL; ++u) {
             if (pp[u] >= p1) continue;
             int64_t dst;
             if (tk[u] & kInWindow) {
@@ -1372,6 +1454,17 @@ cudaError_t launch_ikd_scatter(int64_t n0, int64_t n1, const int64_t* off0, cons
 cudaError_t launch_vmax_bound(const float* vin0, const float* vin1, const uint32_t* amax, float ck, float* vout0,
                               float* vout1, cudaStream_t st) {
   k_vmax_bound<<<1, 1, 0, st>>>(vin0, vin1, amax, ck, vout0, vout1);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+__global__ void k_set_vmax2(const uint32_t* vmax_bits, float* out0, float* out1) {
+  *out0 = __uint_as_float(vmax_bits[0]);
+  *out1 = __uint_as_float(vmax_bits[1]);
+}
+
+cudaError_t launch_set_vmax2(const uint32_t* vmax_bits, float* out0, float* out1, cudaStream_t st) {
+  k_set_vmax2<<<1, 1, 0, st>>>(vmax_bits, out0, out1);
   note_launches(1);
   return cudaGetLastError();
 }

@@ -41,6 +41,12 @@ cudaError_t scan_codes(const pm_codes_t& in, int64_t ncell, int64_t* off, void* 
                        cudaStream_t st);
 cudaError_t scan_counts(const uint32_t* counts, int64_t ncell, int64_t expect, int64_t* off, pm_codes_t& out,
                         void* partial_ws, int* status, cudaStream_t st);
+// Both species in one set of launches (partials: 2 * scan_partial_bytes).
+cudaError_t scan_codes2(const pm_codes_t in[2], int64_t ncell, int64_t* off0, int64_t* off1, void* partial_ws,
+                        int* status, cudaStream_t st);
+cudaError_t scan_counts2(const uint32_t* counts0, const uint32_t* counts1, int64_t ncell, const int64_t expect[2],
+                         int64_t* off0, int64_t* off1, pm_codes_t out[2], void* partial_ws, int* status,
+                         cudaStream_t st);
 size_t scan_partial_bytes(int64_t ncell);
 
 cudaError_t launch_decompress(const PCodes& in, const int64_t* off, const Geo& g, float* x, float* v, cudaStream_t st);
@@ -72,6 +78,7 @@ cudaError_t launch_ikd_scatter(int64_t n0, int64_t n1, const int64_t* off0, cons
                                const int64_t* newoff1, const PCodesOut& o0, const PCodesOut& o1, const uint32_t* tkey,
                                const uint4* tpv, bool coded, int* status, cudaStream_t st);
 cudaError_t launch_set_vmax(const uint32_t* vmax_bits, float* out, cudaStream_t st);
+cudaError_t launch_set_vmax2(const uint32_t* vmax_bits, float* out0, float* out1, cudaStream_t st);
 // v_max' bound of both species from v_max and the maxima amax[3] (coarse mesh,
 // fine mesh, PP accelerations; float bits).
 // PP acceleration (Eq. 4) of every particle of both species into acc[t] (stream index t,

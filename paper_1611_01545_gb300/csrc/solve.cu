@@ -469,22 +469,32 @@ cudaError_t tile_window_launch(const SolvePlan& p, const float* src, int64_t til
 // rho_f(rc C + k), w(k) = 1 - |k| / rc, k = -(rc-1) .. rc-1, periodic.  One
 // block per coarse (y, z) row: threads sum the (2 rc - 1)^2 fine rows with
 // their y, z weights along x into shared memory, then the x weights.
-__global__ void k_restrict(const float* rho_f, int nf, int rc, float* rho_c) {
+template <int RC>   // RC > 0: compile-time ratio (loops unrolled); 0: runtime ratio rc
+__global__ void __launch_bounds__(256, 1) k_restrict(const float* rho_f, int nf, int rc_rt, float* rho_c) {
   extern __shared__ float acc[];   // [nf]
+  const int rc = RC > 0 ? RC : rc_rt;
   const int nc = nf / rc;
   const int cy = blockIdx.x % nc, cz = blockIdx.x / nc;
   const float inv = 1.0f / (float)rc;
+  int zrow[2 * (RC > 0 ? RC : 16) - 1], yrow[2 * (RC > 0 ? RC : 16) - 1];
+#pragma unroll
+  for (int k = 1 - rc; k < rc; ++k) {
+    int z = rc * cz + k, y = rc * cy + k;
+    z += z < 0 ? nf : (z >= nf ? -nf : 0);
+    y += y < 0 ? nf : (y >= nf ? -nf : 0);
+    zrow[k + rc - 1] = z;
+    yrow[k + rc - 1] = y;
+  }
   for (int x = threadIdx.x; x < nf; x += blockDim.x) {
     float s = 0.f;
+#pragma unroll
     for (int kz = 1 - rc; kz < rc; ++kz) {
-      int z = rc * cz + kz;
-      z += z < 0 ? nf : (z >= nf ? -nf : 0);
       const float wz = 1.0f - (float)(kz < 0 ? -kz : kz) * inv;
+      const float* zp = rho_f + (size_t)zrow[kz + rc - 1] * nf * nf + x;
+#pragma unroll
       for (int ky = 1 - rc; ky < rc; ++ky) {
-        int y = rc * cy + ky;
-        y += y < 0 ? nf : (y >= nf ? -nf : 0);
         const float wy = 1.0f - (float)(ky < 0 ? -ky : ky) * inv;
-        s = fmaf(wz * wy, __ldg(rho_f + ((size_t)z * nf + y) * nf + x), s);
+        s = fmaf(wz * wy, __ldg(zp + (size_t)yrow[ky + rc - 1] * nf), s);
       }
     }
     acc[x] = s;
@@ -492,6 +502,7 @@ __global__ void k_restrict(const float* rho_f, int nf, int rc, float* rho_c) {
   __syncthreads();
   for (int cx = threadIdx.x; cx < nc; cx += blockDim.x) {
     float t = 0.f;
+#pragma unroll
     for (int kx = 1 - rc; kx < rc; ++kx) {
       int x = rc * cx + kx;
       x += x < 0 ? nf : (x >= nf ? -nf : 0);
@@ -502,9 +513,10 @@ __global__ void k_restrict(const float* rho_f, int nf, int rc, float* rho_c) {
 }
 
 cudaError_t launch_restrict(const float* rho_f, int nf, int rc, float* rho_c, cudaStream_t st) {
-  if (rc < 1 || nf % rc) return cudaErrorInvalidValue;
+  if (rc < 1 || rc > 16 || nf % rc) return cudaErrorInvalidValue;
   const int nc = nf / rc;
-  k_restrict<<<nc * nc, 256, (size_t)nf * sizeof(float), st>>>(rho_f, nf, rc, rho_c);
+  if (rc == 4) k_restrict<4><<<nc * nc, 256, (size_t)nf * sizeof(float), st>>>(rho_f, nf, rc, rho_c);
+  else k_restrict<0><<<nc * nc, 256, (size_t)nf * sizeof(float), st>>>(rho_f, nf, rc, rho_c);
   note_launches(1);
   return cudaGetLastError();
 }
