@@ -979,13 +979,13 @@ int step_launch(pm_handle_t* h, const pm_codes_t in[2], pm_codes_t out[2], doubl
   {
     TimedScope ts(tm, "deposit", st);
     CK(h, cudaMemsetAsync(rf, 0, (size_t)g.nfine3() * (fixed ? 8 : 4), st));
-    if (g.two && !via_fine) CK(h, cudaMemsetAsync(rc, 0, (size_t)g.ncoarse3() * 8, st));
+    if (g.two) CK(h, cudaMemsetAsync(rc, 0, (size_t)g.ncoarse3() * (fixed ? 8 : 4), st));
     long long M0 = llrint(h->cfg.mass[0] * 4294967296.0), M1 = llrint(h->cfg.mass[1] * 4294967296.0);
     CK(h, zero_work(h, st));
+    // (float: the coarse density is restricted from each block's fine tile as it flushes)
     CK(h, launch_deposit_codes(view(in[0], vel16), view(in[1], vel16), h->off[0], h->off[1], h->geo, dep_blk(h),
-                               (float)h->cfg.mass[0], (float)h->cfg.mass[1], M0, M1,
-                               (g.two && !via_fine) ? rc : nullptr, rf, fixed, st));
-    if (via_fine) CK(h, launch_restrict(h->rho_f, g.nf, g.rc, h->rho_c, st));
+                               (float)h->cfg.mass[0], (float)h->cfg.mass[1], M0, M1, g.two ? rc : nullptr, rf, fixed,
+                               st));
   }
   const bool bound = h->cfg.vmax_mode == 1;
   const float ck = (float)c_kick, cd = (float)c_drift;

@@ -811,8 +811,12 @@ __global__ void k_deposit_codes(PCodes c0, PCodes c1, const int64_t* off0, const
     int64_t* roff = reinterpret_cast<int64_t*>(smraw);
     Acc* sf = reinterpret_cast<Acc*>(roff + 2 * nrow * (bk.RX + 1));
     Acc* sc = sf + fx * fy * fz;
-    // coarse corners only when a coarse mesh is given (the fused float step restricts the fine mesh instead)
-    const bool dep_coarse = g.two && rho_c != nullptr;
+    // Coarse density: the int64 mode deposits each particle's 8 coarse corners
+    // (exact, order independent); the float mode restricts the block's fine
+    // tile onto the coarse cells it touches when it flushes (CIC restriction
+    // is exact and linear, so the blocks' partial sums add up to it).
+    const bool dep_coarse = g.two && rho_c != nullptr && sizeof(Acc) == 8;
+    const bool restr = g.two && rho_c != nullptr && sizeof(Acc) == 4;
     const int nsf = fx * fy * fz, nsc = dep_coarse ? cx * cy * cz : 0;
     for (int i = threadIdx.x; i < nsf + nsc; i += blockDim.x) sf[i] = (Acc)0;
     const CellBlock cb = block_of(bk, bid);
@@ -913,6 +917,56 @@ __global__ void k_deposit_codes(PCodes c0, PCodes c1, const int64_t* off0, const
       if (gy >= nc) gy -= nc;
       if (gz >= nc) gz -= nc;
       global_add(&rho_c[((int64_t)gz * nc + gy) * nc + gx], val);
+    }
+    if (restr) {
+      // rho_c(C) += sum_k w(kx) w(ky) w(kz) tile(r C + k), w(k) = 1 - |k| / r, over the
+      // tile's part; coarse cells C = block cell + (0 .. RX, 0 .. RY, 0 .. RZ); separable.
+      const float* tile = reinterpret_cast<const float*>(sf);
+      float* T1 = reinterpret_cast<float*>(sc) + cx * cy * cz;   // [fz][fy][cx]
+      float* T2 = T1 + fz * fy * cx;                             // [fz][cy][cx]
+      const float inv = 1.0f / (float)r;
+      const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+      for (int line = warp; line < fz * fy; line += nwarp) {
+        const float* row = tile + line * fx;
+        for (int q = lane; q < cx; q += 32) {
+          float t = 0.f;
+          for (int k = 1 - r; k < r; ++k) {
+            const int j = r * q + k;
+            if (j >= 0 && j < fx) t = fmaf(1.0f - (float)(k < 0 ? -k : k) * inv, row[j], t);
+          }
+          T1[line * cx + q] = t;
+        }
+      }
+      __syncthreads();
+      for (int line = warp; line < fz * cy; line += nwarp) {
+        const int lz = line / cy, qy = line - lz * cy;
+        for (int q = lane; q < cx; q += 32) {
+          float t = 0.f;
+          for (int k = 1 - r; k < r; ++k) {
+            const int j = r * qy + k;
+            if (j >= 0 && j < fy) t = fmaf(1.0f - (float)(k < 0 ? -k : k) * inv, T1[(lz * fy + j) * cx + q], t);
+          }
+          T2[line * cx + q] = t;
+        }
+      }
+      __syncthreads();
+      for (int line = warp; line < cz * cy; line += nwarp) {
+        const int qz = line / cy, qy = line - qz * cy;
+        int gy = cb.iy0 + qy, gz = cb.iz0 + qz;
+        if (gy >= nc) gy -= nc;
+        if (gz >= nc) gz -= nc;
+        float* crow = reinterpret_cast<float*>(rho_c) + ((int64_t)gz * nc + gy) * nc;
+        for (int q = lane; q < cx; q += 32) {
+          float t = 0.f;
+          for (int k = 1 - r; k < r; ++k) {
+            const int j = r * qz + k;
+            if (j >= 0 && j < fz) t = fmaf(1.0f - (float)(k < 0 ? -k : k) * inv, T2[(j * cy + qy) * cx + q], t);
+          }
+          int gx = cb.ix0 + q;
+          if (gx >= nc) gx -= nc;
+          if (t != 0.f) atomicAdd(crow + gx, t);
+        }
+      }
     }
   });
 }
@@ -1386,7 +1440,10 @@ size_t deposit_codes_smem(const Geo& g, const Blk& bk, bool fixed) {
   size_t nrow = (size_t)bk.RY * bk.RZ;
   size_t fine = (size_t)(bk.RX * g.rcmp + 1) * (bk.RY * g.rcmp + 1) * (bk.RZ * g.rcmp + 1);
   size_t coarse = g.two ? (size_t)(bk.RX + 1) * (bk.RY + 1) * (bk.RZ + 1) : 0;
-  return 2 * nrow * (bk.RX + 1) * sizeof(int64_t) + (fine + coarse) * (fixed ? 8 : 4);
+  // float two-level: room for the restriction's x and y partial sums
+  size_t restr = (g.two && !fixed) ? ((size_t)(bk.RZ * g.rcmp + 1) * ((bk.RY * g.rcmp + 1) + (bk.RY + 1)) *
+                                      (bk.RX + 1)) : 0;
+  return 2 * nrow * (bk.RX + 1) * sizeof(int64_t) + (fine + coarse) * (fixed ? 8 : 4) + restr * 4;
 }
 
 // Grid of a cell-block launch: one CTA per block, or (bk.work set) as many
