@@ -108,16 +108,16 @@ bool supported_fft(int n) { return n == 16 || n == 32 || n == 48 || n == 64 || n
 bool pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
 
 int slot_of_rt(int N, int k) {
-  int N1 = 0, N2 = 0;
+  // the same factorisation the device transforms use (fft.cuh)
   switch (N) {
-    case 16: N1 = 4; N2 = 4; break;
-    case 32: N1 = 4; N2 = 8; break;
-    case 48: N1 = 6; N2 = 8; break;
-    case 64: N1 = 8; N2 = 8; break;
-    case 96: N1 = 8; N2 = 12; break;
-    case 128: N1 = 8; N2 = 16; break;
+    case 16: return pmfft::slot_of<16>(k);
+    case 32: return pmfft::slot_of<32>(k);
+    case 48: return pmfft::slot_of<48>(k);
+    case 64: return pmfft::slot_of<64>(k);
+    case 96: return pmfft::slot_of<96>(k);
+    case 128: return pmfft::slot_of<128>(k);
   }
-  return N2 * (k % N1) + k / N1;
+  return k;
 }
 
 int mode_number(int j, int n) { return j <= n / 2 ? j : j - n; }

@@ -127,7 +127,10 @@ template <> struct Factor<16> { static constexpr int N1 = 4, N2 = 4; };
 template <> struct Factor<32> { static constexpr int N1 = 4, N2 = 8; };
 template <> struct Factor<48> { static constexpr int N1 = 6, N2 = 8; };
 template <> struct Factor<64> { static constexpr int N1 = 8, N2 = 8; };
-template <> struct Factor<96> { static constexpr int N1 = 8, N2 = 12; };
+#ifndef PM_FFT96_N1
+#define PM_FFT96_N1 8
+#endif
+template <> struct Factor<96> { static constexpr int N1 = PM_FFT96_N1, N2 = 96 / PM_FFT96_N1; };
 template <> struct Factor<128> { static constexpr int N1 = 8, N2 = 16; };
 
 template <int N> __host__ __device__ constexpr int slot_of(int k) {

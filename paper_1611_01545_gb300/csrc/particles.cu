@@ -1324,7 +1324,11 @@ __global__ void __launch_bounds__(PM_SCATTER_THREADS, PM_SCATTER_MIN_BLOCKS) k_i
             if (pp[u] >= p1) continue;
             int64_t dst;
             if (tk[u] & kInWindow) {
-              dst = (int64_t)atomicAdd(base + s * W + (tk[u] & ~kInWindow), 1ull);
+              {
+              // rank within the block's range of the cell: count its histogram entry down
+              const uint32_t sl = s * W + (tk[u] & ~kInWindow);
+              dst = (int64_t)base[sl] + (int64_t)atomicSub(hist + sl, 1u) - 1;
+            }
             } else {
               const uint32_t top = atomicSub(counts + tk[u], 1u);
               dst = newoff[tk[u]] + (int64_t)top - 1;
