@@ -96,13 +96,8 @@ __device__ __forceinline__ float src_value(const void* src, int64_t idx) {
 
 __device__ __forceinline__ int wrap1(int g, int n) { return g < 0 ? g + n : (g >= n ? g - n : g); }
 
-// Resident blocks per SM pass A is compiled for on the 96^3 tiles (its
-// register budget: 3 blocks fit their shared memory; measured 0.205 -> 0.188 ms).
-#ifndef PM_SOLVE_A_MINB
-#define PM_SOLVE_A_MINB 3
-#endif
 template <int N, bool FIXED>
-__global__ void __launch_bounds__(SolveCfg<N>::threads, N == 96 ? PM_SOLVE_A_MINB : 1) k_solve_a(SolveArgs a) {
+__device__ __forceinline__ void solve_a_body(const SolveArgs& a) {
   constexpr int NH = SolveCfg<N>::NH;
   extern __shared__ float2 sm[];
   float2* tw = sm;
@@ -150,6 +145,27 @@ __global__ void __launch_bounds__(SolveCfg<N>::threads, N == 96 ? PM_SOLVE_A_MIN
   float4* out = reinterpret_cast<float4*>(a.spec + ((size_t)pb * N + z) * N * NH);
   const float4* P4 = reinterpret_cast<const float4*>(P);
   for (int i = threadIdx.x; i < N * NH / 2; i += blockDim.x) out[i] = P4[i];
+}
+
+template <int N, bool FIXED>
+__global__ void __launch_bounds__(SolveCfg<N>::threads) k_solve_a(SolveArgs a) {
+  solve_a_body<N, FIXED>(a);
+}
+
+// The 96^3 tiles' pass A is compiled for 3 resident blocks per SM (40
+// registers; 3 blocks fit its shared memory): measured 0.205 -> 0.188 ms.
+#ifndef PM_SOLVE_A_MINB
+#define PM_SOLVE_A_MINB 3
+#endif
+template <bool FIXED>
+__global__ void __launch_bounds__(SolveCfg<96>::threads, PM_SOLVE_A_MINB) k_solve_a96(SolveArgs a) {
+  solve_a_body<96, FIXED>(a);
+}
+
+template <int N, bool FIXED>
+constexpr auto solve_a_kernel() {
+  if constexpr (N == 96) return k_solve_a96<FIXED>;
+  else return k_solve_a<N, FIXED>;
 }
 
 // Pass B works on one ky row and one half of the kx columns (KC = ceil(NH/2)
@@ -375,8 +391,8 @@ static cudaError_t solve_n(const SolvePlan& p, const void* src, bool fixed, floa
   using C = SolveCfg<N>;
   static bool attr_done = false;
   if (!attr_done) {
-    cudaFuncSetAttribute(k_solve_a<N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem_a);
-    cudaFuncSetAttribute(k_solve_a<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem_a);
+    cudaFuncSetAttribute(solve_a_kernel<N, false>(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem_a);
+    cudaFuncSetAttribute(solve_a_kernel<N, true>(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem_a);
     cudaFuncSetAttribute(k_solve_b<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PassB<N>::smem);
     cudaFuncSetAttribute(k_solve_c<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem_a);
     attr_done = true;
@@ -388,8 +404,8 @@ static cudaError_t solve_n(const SolvePlan& p, const void* src, bool fixed, floa
                 pro ? pro->coarse : nullptr, pro ? pro->nc : 0, pro ? pro->rc : 1};
     {
       TimedScope ts(tm, N == p.src_n && p.b == 0 ? "fft_a_mesh" : "fft_a_tiles", st);
-      if (fixed) k_solve_a<N, true><<<dim3(N, nb), C::threads, C::smem_a, st>>>(a);
-      else k_solve_a<N, false><<<dim3(N, nb), C::threads, C::smem_a, st>>>(a);
+      if (fixed) solve_a_kernel<N, true>()<<<dim3(N, nb), C::threads, C::smem_a, st>>>(a);
+      else solve_a_kernel<N, false>()<<<dim3(N, nb), C::threads, C::smem_a, st>>>(a);
     }
     {
       TimedScope ts(tm, N == p.src_n && p.b == 0 ? "fft_b_mesh" : "fft_b_tiles", st);
@@ -428,11 +444,11 @@ template <int N>
 static cudaError_t solve_adjoint_n(const SolvePlan& p, const float* lam_acc, float* lam_rho, float2* spec3comp,
                                    cudaStream_t st) {
   using C = SolveCfg<N>;
-  cudaFuncSetAttribute(k_solve_a<N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem_a);
+  cudaFuncSetAttribute(solve_a_kernel<N, false>(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem_a);
   cudaFuncSetAttribute(k_solve_b_adj<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sizeof(float2) * (N + 2 * (size_t)N * PassB<N>::KC)));
   cudaFuncSetAttribute(k_solve_c<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem_a);
   SolveArgs a{lam_acc, 0, p.src_n, 1, N, 0, 0, spec3comp, p.spec3, p.kern, p.tw, lam_rho, 1};
-  k_solve_a<N, false><<<dim3(N, 3), C::threads, C::smem_a, st>>>(a);
+  solve_a_kernel<N, false>()<<<dim3(N, 3), C::threads, C::smem_a, st>>>(a);
   a.comp_mode = 0;
   k_solve_b_adj<N><<<dim3(N, 2, 1), PassB<N>::threads, sizeof(float2) * (N + 2 * (size_t)N * PassB<N>::KC), st>>>(a);
   k_solve_c<N><<<dim3(N, 1, 1), C::threads_c, C::smem_a, st>>>(a);
