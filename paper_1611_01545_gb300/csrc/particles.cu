@@ -1067,7 +1067,7 @@ __device__ __forceinline__ uint32_t window_x(const Geo& g, const Win& w, int lx)
 #define PM_SCATTER_UNROLL 2
 #endif
 #ifndef PM_SCATTER_MIN_BLOCKS
-#define PM_SCATTER_MIN_BLOCKS 4
+#define PM_SCATTER_MIN_BLOCKS 5
 #endif
 
 __global__ void __launch_bounds__(PM_IKD_THREADS, PM_IKD_MIN_BLOCKS) k_ikd_count(PCodes c0, PCodes c1, const int64_t* off0, const int64_t* off1, Geo g, Blk bk,
