@@ -179,16 +179,20 @@ template <int N> struct PassB {
 #define PM_PASSB_THREADS 512
 #endif
   static constexpr int threads = (N >= 96) ? PM_PASSB_THREADS : 256;
-  static constexpr size_t smem = sizeof(float2) * (N + 4 * (size_t)N * KC);
+  // twiddles + [z][3 KC]: the forward transform runs in the first KC columns
+  static constexpr size_t smem = sizeof(float2) * (N + 3 * (size_t)N * KC);
 };
 
 template <int N>
-__global__ void __launch_bounds__(PassB<N>::threads) k_solve_b(SolveArgs a) {
+__device__ __forceinline__ void solve_b_body(const SolveArgs& a) {
   constexpr int NH = PassB<N>::NH, KC = PassB<N>::KC;
   extern __shared__ float2 sm[];
   float2* tw = sm;
-  float2* F = sm + N;             // [z][KC]
-  float2* G = F + N * KC;         // [z][3 KC]: component d in columns d KC .. d KC + KC - 1
+  // [z][3 KC]: component d of the products in columns d KC .. d KC + KC - 1; the
+  // density spectrum F is transformed in the columns of component 0 and each
+  // thread overwrites its element with the three products (in place for d = 0)
+  float2* G = sm + N;
+  float2* F = G;
   for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = a.tw[i];
   const int ys = blockIdx.x;      // ky in slot order
   const int half = blockIdx.y;    // which half of the kx columns
@@ -198,18 +202,18 @@ __global__ void __launch_bounds__(PassB<N>::threads) k_solve_b(SolveArgs a) {
   const float2* in = a.spec + (size_t)pb * N * N * NH + (size_t)ys * NH + kx0;
   for (int i = threadIdx.x; i < N * KC; i += blockDim.x) {
     const int z = i / KC, c = i - z * KC;
-    if (c < ncol) async_copy8(F + i, in + (size_t)z * N * NH + c);
-    else F[i] = make_float2(0.f, 0.f);
+    if (c < ncol) async_copy8(F + z * 3 * KC + c, in + (size_t)z * N * NH + c);
+    else F[z * 3 * KC + c] = make_float2(0.f, 0.f);
   }
   async_wait();
   __syncthreads();
-  fft_fwd<N, KC, 1, KC>(F, tw);
+  fft_fwd<N, KC, 1, 3 * KC>(F, tw);
   const float* K = a.kern + (size_t)ys * NH + kx0;
   const size_t kstride = (size_t)N * N * NH;
   for (int i = threadIdx.x; i < N * KC; i += blockDim.x) {
     const int zs = i / KC, c = i - zs * KC;
-    const float2 f = F[i];
     float2* g = G + zs * 3 * KC + c;
+    const float2 f = g[0];
     if (c < ncol) {
       const float* Kz = K + (size_t)zs * N * NH + c;
 #pragma unroll
@@ -231,6 +235,26 @@ __global__ void __launch_bounds__(PassB<N>::threads) k_solve_b(SolveArgs a) {
       if (c < ncol) out[(size_t)zo * N * NH + c] = G[(zo + a.b) * 3 * KC + d * KC + c];
     }
   }
+}
+
+template <int N>
+__global__ void __launch_bounds__(PassB<N>::threads) k_solve_b(SolveArgs a) {
+  solve_b_body<N>(a);
+}
+
+// The 96^3 tiles' pass B compiled for 3 resident blocks per SM (its shared
+// memory allows 3 since the forward transform shares the product buffer).
+#ifndef PM_PASSB_MINB
+#define PM_PASSB_MINB 3
+#endif
+__global__ void __launch_bounds__(PassB<96>::threads, PM_PASSB_MINB) k_solve_b96(SolveArgs a) {
+  solve_b_body<96>(a);
+}
+
+template <int N>
+constexpr auto solve_b_kernel() {
+  if constexpr (N == 96) return k_solve_b96;
+  else return k_solve_b<N>;
 }
 
 // Transpose of the solve for one periodic mesh (the adjoint of a_d = K_d * rho):
@@ -393,7 +417,7 @@ static cudaError_t solve_n(const SolvePlan& p, const void* src, bool fixed, floa
   if (!attr_done) {
     cudaFuncSetAttribute(solve_a_kernel<N, false>(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem_a);
     cudaFuncSetAttribute(solve_a_kernel<N, true>(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem_a);
-    cudaFuncSetAttribute(k_solve_b<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PassB<N>::smem);
+    cudaFuncSetAttribute(solve_b_kernel<N>(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PassB<N>::smem);
     cudaFuncSetAttribute(k_solve_c<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem_a);
     attr_done = true;
   }
@@ -409,7 +433,7 @@ static cudaError_t solve_n(const SolvePlan& p, const void* src, bool fixed, floa
     }
     {
       TimedScope ts(tm, N == p.src_n && p.b == 0 ? "fft_b_mesh" : "fft_b_tiles", st);
-      k_solve_b<N><<<dim3(N, 2, nb), PassB<N>::threads, PassB<N>::smem, st>>>(a);
+      solve_b_kernel<N>()<<<dim3(N, 2, nb), PassB<N>::threads, PassB<N>::smem, st>>>(a);
     }
     if (pro && pro->ready && p0 == 0) {
       cudaError_t e = cudaStreamWaitEvent(st, pro->ready, 0);   // the coarse force must be complete
