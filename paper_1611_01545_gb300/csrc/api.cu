@@ -61,8 +61,14 @@ struct pm_handle {
   uint8_t* pk_pos[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};   // [in/out][species]
   uint8_t* pk_vel[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
   bool pk_staged = false;
+  // pm_step_packed: velocity bytes come over on their own stream while the
+  // deposit and the solve run; the count pass waits for them
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t pk_fork = nullptr, pk_vel_ready = nullptr;
+  cudaEvent_t pre_count_wait = nullptr;   // set only while a packed step is being enqueued
   // pm_step replay: one instantiated graph per (codes descriptors, c_k, c_d)
   struct StepGraph {
+    int kind;   // 0: pm_step (device codes); 1: pm_step_packed (host codes)
     pm_codes_t in[2], out[2];
     double ck, cd;
     cudaGraphExec_t exec;
@@ -488,6 +494,9 @@ int pm_destroy(pm_handle_t* h) {
   cudaDeviceSynchronize();
   for (auto& g : h->step_graphs) cudaGraphExecDestroy(g.exec);
   if (h->capture_stream) cudaStreamDestroy(h->capture_stream);
+  if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
+  if (h->pk_fork) cudaEventDestroy(h->pk_fork);
+  if (h->pk_vel_ready) cudaEventDestroy(h->pk_vel_ready);
   if (h->side_stream) cudaStreamDestroy(h->side_stream);
   if (h->fork_ev) cudaEventDestroy(h->fork_ev);
   if (h->join_ev) cudaEventDestroy(h->join_ev);
@@ -724,11 +733,14 @@ bool same_codes(const pm_codes_t& a, const pm_codes_t& b) { return memcmp(&a, &b
 // Replays (capturing on first use) the step's launch sequence as one graph.
 // Capture runs on a library stream, since the caller's stream may be the
 // legacy default stream, which cannot be captured.
+int packed_launch(pm_handle_t* h, const pm_host_codes_t in[2], pm_host_codes_t out[2], double c_kick,
+                  double c_drift, cudaStream_t st);
+
 int step_graph(pm_handle_t* h, const pm_codes_t in[2], pm_codes_t out[2], double c_kick, double c_drift,
-               cudaStream_t st) {
+               cudaStream_t st, int kind = 0) {
   for (auto& g : h->step_graphs) {
-    if (g.ck == c_kick && g.cd == c_drift && same_codes(g.in[0], in[0]) && same_codes(g.in[1], in[1]) &&
-        same_codes(g.out[0], out[0]) && same_codes(g.out[1], out[1])) {
+    if (g.kind == kind && g.ck == c_kick && g.cd == c_drift && same_codes(g.in[0], in[0]) &&
+        same_codes(g.in[1], in[1]) && same_codes(g.out[0], out[0]) && same_codes(g.out[1], out[1])) {
       CK(h, cudaGraphLaunch(g.exec, st));
       note_launches((int)g.launches);
       return PM_OK;
@@ -737,7 +749,8 @@ int step_graph(pm_handle_t* h, const pm_codes_t in[2], pm_codes_t out[2], double
   if (!h->capture_stream) CK(h, cudaStreamCreateWithFlags(&h->capture_stream, cudaStreamNonBlocking));
   const long long before = pm_launch_count();
   CK(h, cudaStreamBeginCapture(h->capture_stream, cudaStreamCaptureModeThreadLocal));
-  const int r = step_launch(h, in, out, c_kick, c_drift, h->capture_stream);
+  const int r = kind == 0 ? step_launch(h, in, out, c_kick, c_drift, h->capture_stream)
+                          : packed_launch(h, in, out, c_kick, c_drift, h->capture_stream);
   cudaGraph_t graph = nullptr;
   const cudaError_t ec = cudaStreamEndCapture(h->capture_stream, &graph);
   const long long captured = pm_launch_count() - before;
@@ -748,6 +761,7 @@ int step_graph(pm_handle_t* h, const pm_codes_t in[2], pm_codes_t out[2], double
   }
   if (ec != cudaSuccess) return fail(h, PM_ERR_CUDA, std::string("step capture: ") + cudaGetErrorString(ec));
   pm_handle::StepGraph g{};
+  g.kind = kind;
   for (int s = 0; s < 2; ++s) {
     g.in[s] = in[s];
     g.out[s] = out[s];
@@ -999,6 +1013,7 @@ int step_launch(pm_handle_t* h, const pm_codes_t in[2], pm_codes_t out[2], doubl
   }
   // bound mode: v_max' from the mesh maxima, before any particle is kicked
   if (bound) CK(h, launch_vmax_bound(in[0].vmax, in[1].vmax, h->amax, ck, out[0].vmax, out[1].vmax, st));
+  if (h->pre_count_wait) CK(h, cudaStreamWaitEvent(st, h->pre_count_wait, 0));   // packed step: velocities in
   {
     TimedScope ts(tm, "ikd_count", st);
     if (!bound) CK(h, cudaMemsetAsync(h->vmax_bits, 0, 8, st));
@@ -1156,12 +1171,54 @@ int pm_unpack_codes(pm_handle_t* h, const pm_codes_t* in, pm_codes_t* out, void*
   return PM_OK;
 }
 
+namespace {
+// Enqueues one packed step: counts, escapes, v_max and position bytes on st,
+// unpacked there; velocity bytes on the copy stream (forked from st), needed
+// only by the count pass; the step; then pack and device -> host copies.
+int packed_launch(pm_handle_t* h, const pm_host_codes_t in[2], pm_host_codes_t out[2], double c_kick,
+                  double c_drift, cudaStream_t st) {
+  const bool vel16 = h->cfg.vel_bits == 16;
+  const int64_t ncell = h->gm.ncell();
+  const size_t vbytes = vel16 ? 6 : 3;
+  for (int s = 0; s < 2; ++s) {
+    const int64_t n = in[s].n;
+    if (int r = copy_meta(h, h->stage_in[s], in[s], ncell, cudaMemcpyHostToDevice, st)) return r;
+    if (n > 0) CK(h, cudaMemcpyAsync(h->pk_pos[0][s], in[s].pos, (size_t)n * 3, cudaMemcpyHostToDevice, st));
+    CK(h, launch_unpack(h->pk_pos[0][s], nullptr, vel16, n, reinterpret_cast<uint32_t*>(h->stage_in[s].pos), nullptr,
+                        st));
+  }
+  CK(h, cudaEventRecord(h->pk_fork, st));
+  CK(h, cudaStreamWaitEvent(h->copy_stream, h->pk_fork, 0));
+  for (int s = 0; s < 2; ++s) {
+    const int64_t n = in[s].n;
+    if (n > 0)
+      CK(h, cudaMemcpyAsync(h->pk_vel[0][s], in[s].vel, (size_t)n * vbytes, cudaMemcpyHostToDevice, h->copy_stream));
+    CK(h, launch_unpack(nullptr, h->pk_vel[0][s], vel16, n, nullptr, h->stage_in[s].vel, h->copy_stream));
+  }
+  CK(h, cudaEventRecord(h->pk_vel_ready, h->copy_stream));
+  h->pre_count_wait = h->pk_vel_ready;
+  const int r = step_launch(h, h->stage_in, h->stage_out, c_kick, c_drift, st);
+  h->pre_count_wait = nullptr;
+  if (r != PM_OK) return r;
+  for (int s = 0; s < 2; ++s) {
+    const int64_t n = in[s].n;
+    CK(h, launch_pack(reinterpret_cast<const uint32_t*>(h->stage_out[s].pos), h->stage_out[s].vel, vel16, n,
+                      h->pk_pos[1][s], h->pk_vel[1][s], st));
+    if (int r2 = copy_meta(h, out[s], h->stage_out[s], ncell, cudaMemcpyDeviceToHost, st)) return r2;
+    if (n > 0) {
+      CK(h, cudaMemcpyAsync(out[s].pos, h->pk_pos[1][s], (size_t)n * 3, cudaMemcpyDeviceToHost, st));
+      CK(h, cudaMemcpyAsync(out[s].vel, h->pk_vel[1][s], (size_t)n * vbytes, cudaMemcpyDeviceToHost, st));
+    }
+  }
+  return PM_OK;
+}
+}  // namespace
+
 int pm_step_packed(pm_handle_t* h, const pm_host_codes_t in[2], pm_host_codes_t out[2], double c_kick,
                    double c_drift, void* stream) {
   if (!h || !in || !out) return fail(h, PM_ERR_ARG, "null argument");
   cudaStream_t st = (cudaStream_t)stream;
   const bool vel16 = h->cfg.vel_bits == 16;
-  const int64_t ncell = h->gm.ncell();
   for (int s = 0; s < 2; ++s) {
     if (out[s].n != in[s].n) return fail(h, PM_ERR_ARG, "out[s].n must equal in[s].n");
     if (!in[s].cnt || !in[s].esc || !in[s].n_esc || !in[s].vmax || !out[s].cnt || !out[s].esc || !out[s].n_esc ||
@@ -1185,30 +1242,19 @@ int pm_step_packed(pm_handle_t* h, const pm_host_codes_t in[2], pm_host_codes_t 
       }
     h->pk_staged = true;
   }
-  for (int s = 0; s < 2; ++s)
+  if (!h->copy_stream) {
+    CK(h, cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking));
+    CK(h, cudaEventCreateWithFlags(&h->pk_fork, cudaEventDisableTiming));
+    CK(h, cudaEventCreateWithFlags(&h->pk_vel_ready, cudaEventDisableTiming));
+  }
+  for (int s = 0; s < 2; ++s) {
     if (h->stage_in[s].n != in[s].n) return fail(h, PM_ERR_ARG, "particle counts changed");
-  const size_t vbytes = vel16 ? 6 : 3;
-  for (int s = 0; s < 2; ++s) {
-    const int64_t n = in[s].n;
-    if (int r = copy_meta(h, h->stage_in[s], in[s], ncell, cudaMemcpyHostToDevice, st)) return r;
-    if (n > 0) {
-      CK(h, cudaMemcpyAsync(h->pk_pos[0][s], in[s].pos, (size_t)n * 3, cudaMemcpyHostToDevice, st));
-      CK(h, cudaMemcpyAsync(h->pk_vel[0][s], in[s].vel, (size_t)n * vbytes, cudaMemcpyHostToDevice, st));
-    }
-    CK(h, launch_unpack(h->pk_pos[0][s], h->pk_vel[0][s], vel16, n, reinterpret_cast<uint32_t*>(h->stage_in[s].pos),
-                        h->stage_in[s].vel, st));
+    if (in[s].esc_cap > h->stage_in[s].esc_cap)
+      return fail(h, PM_ERR_ARG, "input escape capacity larger than at the first call");
   }
-  if (int r = pm_step(h, h->stage_in, h->stage_out, c_kick, c_drift, stream)) return r;
-  for (int s = 0; s < 2; ++s) {
-    const int64_t n = in[s].n;
-    CK(h, launch_pack(reinterpret_cast<const uint32_t*>(h->stage_out[s].pos), h->stage_out[s].vel, vel16, n,
-                      h->pk_pos[1][s], h->pk_vel[1][s], st));
-    if (int r = copy_meta(h, out[s], h->stage_out[s], ncell, cudaMemcpyDeviceToHost, st)) return r;
-    if (n > 0) {
-      CK(h, cudaMemcpyAsync(out[s].pos, h->pk_pos[1][s], (size_t)n * 3, cudaMemcpyDeviceToHost, st));
-      CK(h, cudaMemcpyAsync(out[s].vel, h->pk_vel[1][s], (size_t)n * vbytes, cudaMemcpyDeviceToHost, st));
-    }
-  }
+  const int r = (h->graphs && !h->timer.on) ? step_graph(h, in, out, c_kick, c_drift, st, 1)
+                                            : packed_launch(h, in, out, c_kick, c_drift, st);
+  if (r != PM_OK) return r;
   return pm_check(h, stream);
 }
 

@@ -8,7 +8,8 @@
 // i.e. 6 or 9 bytes per particle instead of 8 or 12 -- the form to move over
 // the host link.  A thread packs or unpacks four consecutive particles at a
 // time (12 / 24 byte groups, word aligned); the last, incomplete group is
-// done byte by byte.
+// done byte by byte.  Unpacking takes positions only (pvel null) or
+// velocities only (ppos null) when asked.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -66,11 +67,14 @@ __global__ void k_unpack(const uint8_t* ppos, const uint8_t* pvel, int vel16, in
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g <= ngroups; g += (int64_t)gridDim.x * blockDim.x) {
     const int64_t p = 4 * g;
     if (g < ngroups) {
-      const uint32_t* i = reinterpret_cast<const uint32_t*>(ppos + 3 * p);
-      const uint32_t i0 = i[0], i1 = i[1], i2 = i[2];
-      *reinterpret_cast<uint4*>(pos + p) =
-          make_uint4(i0 & 0xFFFFFFu, (i0 >> 24) | ((i1 & 0xFFFFu) << 8), (i1 >> 16) | ((i2 & 0xFFu) << 16), i2 >> 8);
-      if (vel16) {
+      if (ppos) {
+        const uint32_t* i = reinterpret_cast<const uint32_t*>(ppos + 3 * p);
+        const uint32_t i0 = i[0], i1 = i[1], i2 = i[2];
+        *reinterpret_cast<uint4*>(pos + p) =
+            make_uint4(i0 & 0xFFFFFFu, (i0 >> 24) | ((i1 & 0xFFFFu) << 8), (i1 >> 16) | ((i2 & 0xFFu) << 16), i2 >> 8);
+      }
+      if (!pvel) {
+      } else if (vel16) {
         const unsigned long long* q = reinterpret_cast<const unsigned long long*>(pvel + 6 * p);
         const unsigned long long o0 = q[0], o1 = q[1], o2 = q[2];
         unsigned long long* v = reinterpret_cast<unsigned long long*>(vel) + p;
@@ -86,10 +90,13 @@ __global__ void k_unpack(const uint8_t* ppos, const uint8_t* pvel, int vel16, in
       }
     } else {
       for (int64_t k = p; k < n; ++k) {
-        uint32_t w = 0;
-        for (int b = 0; b < 3; ++b) w |= (uint32_t)ppos[3 * k + b] << (8 * b);
-        pos[k] = w;
-        if (vel16) {
+        if (ppos) {
+          uint32_t w = 0;
+          for (int b = 0; b < 3; ++b) w |= (uint32_t)ppos[3 * k + b] << (8 * b);
+          pos[k] = w;
+        }
+        if (!pvel) {
+        } else if (vel16) {
           unsigned long long v = 0;
           for (int b = 0; b < 6; ++b) v |= (unsigned long long)pvel[6 * k + b] << (8 * b);
           reinterpret_cast<unsigned long long*>(vel)[k] = v;

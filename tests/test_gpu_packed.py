@@ -55,10 +55,18 @@ def test_step_packed_equals_step():
     for c in hout:
         c.pos.zero_()
         c.vel.zero_()
-    pm.step_packed(hin, hout, 1.0, 1.0)
-    for s in range(2):
-        got = oracle_codes_from_lib(pm.unpack(hout[s].to("cuda")), nc, w.vel_bits)
-        ref = oracle_codes_from_lib(dout[s], nc, w.vel_bits)
-        assert got.vmax == ref.vmax
-        np.testing.assert_array_equal(got.cnt, ref.cnt)
-        np.testing.assert_array_equal(records(got), records(ref))
+    # direct launches, then captured into a graph and replayed (velocity bytes
+    # arrive on a second stream while the deposit and the solve run)
+    for graphs in (False, True, True):
+        pm.set_graphs(graphs)
+        for c in hout:
+            c.pos.zero_()
+            c.vel.zero_()
+        pm.step_packed(hin, hout, 1.0, 1.0)
+        for s in range(2):
+            got = oracle_codes_from_lib(pm.unpack(hout[s].to("cuda")), nc, w.vel_bits)
+            ref = oracle_codes_from_lib(dout[s], nc, w.vel_bits)
+            assert got.vmax == ref.vmax
+            np.testing.assert_array_equal(got.cnt, ref.cnt)
+            np.testing.assert_array_equal(records(got), records(ref))
+    pm.set_graphs(False)
