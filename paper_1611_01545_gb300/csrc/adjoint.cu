@@ -4,7 +4,9 @@
 // x' = x + c_d v'.  With W the CIC weight prod_d (1 - |x_d - c_d|), whose
 // derivative along d is -1 on the lower and +1 on the upper corner factor:
 //   k_adj_interp:  lam_v += c_d lam_x;  lam_a = c_k lam_v;
-//                  lam_A(c) += lam_a W(x - c)  (transpose of interpolation);
+//                  lam_A(c) += lam_a W(x - c)  (transpose of interpolation;
+//                  one float4 vector reduction per corner when lam_A is
+//                  interleaved);
 //                  lam_x += sum_c (lam_a . a(c)) grad W(x - c)
 //   (A^T on the mesh, solve.cu)
 //   k_adj_deposit: lam_x += m sum_c lam_rho(c) grad W(x - c)
@@ -65,6 +67,7 @@ __global__ void k_adj_deposit(const float* x, int64_t np, float m, int n, const 
   }
 }
 
+template <bool V4>
 __global__ void k_adj_interp(const float* x, int64_t np, int n, const float* acc, float ck, float cd, float* lam_x,
                              float* lam_v, float* lam_A) {
   const int64_t n3 = (int64_t)n * n * n;
@@ -84,9 +87,13 @@ __global__ void k_adj_interp(const float* x, int64_t np, int n, const float* acc
       const int dx = k & 1, dy = (k >> 1) & 1, dz = k >> 2;
       const int64_t idx = corner_index(c, dx, dy, dz, n);
       const float w = c.w[dx][0] * c.w[dy][1] * c.w[dz][2];
-      atomicAdd(lam_A + idx, la[0] * w);
-      atomicAdd(lam_A + n3 + idx, la[1] * w);
-      atomicAdd(lam_A + 2 * n3 + idx, la[2] * w);
+      if (V4) {
+        atomicAdd(reinterpret_cast<float4*>(lam_A) + idx, make_float4(la[0] * w, la[1] * w, la[2] * w, 0.f));
+      } else {
+        atomicAdd(lam_A + idx, la[0] * w);
+        atomicAdd(lam_A + n3 + idx, la[1] * w);
+        atomicAdd(lam_A + 2 * n3 + idx, la[2] * w);
+      }
       const float dot = la[0] * __ldg(acc + idx) + la[1] * __ldg(acc + n3 + idx) + la[2] * __ldg(acc + 2 * n3 + idx);
       g0 += dot * c.dw[dx][0] * c.w[dy][1] * c.w[dz][2];
       g1 += dot * c.w[dx][0] * c.dw[dy][1] * c.w[dz][2];
@@ -115,9 +122,12 @@ cudaError_t launch_adj_deposit(const float* x, int64_t n, float m, int nf, const
 }
 
 cudaError_t launch_adj_interp(const float* x, int64_t n, int nf, const float* acc, float ck, float cd, float* lam_x,
-                              float* lam_v, float* lam_A, cudaStream_t st) {
+                              float* lam_v, float* lam_A, bool interleaved, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
-  k_adj_interp<<<grid_of(n), 256, 0, st>>>(x, n, nf, acc, ck, cd, lam_x, lam_v, lam_A);
+  if (interleaved)
+    k_adj_interp<true><<<grid_of(n), 256, 0, st>>>(x, n, nf, acc, ck, cd, lam_x, lam_v, lam_A);
+  else
+    k_adj_interp<false><<<grid_of(n), 256, 0, st>>>(x, n, nf, acc, ck, cd, lam_x, lam_v, lam_A);
   note_launches(1);
   return cudaGetLastError();
 }

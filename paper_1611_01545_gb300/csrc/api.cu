@@ -51,7 +51,7 @@ struct pm_handle {
   uint4* tpv = nullptr;      // per particle: new in-cell position code, v'_x, v'_y, v'_z (float bits)
   std::vector<void*> allocs;
   Timer timer;
-  // adjoint workspace (single mesh): lam_acc [3][n^3], component spectra [3][N][N][N/2+1]
+  // adjoint workspace (single mesh): lam_acc float4 [n^3], component spectra [3][N][N][N/2+1]
   float* lam_acc = nullptr;
   float2* adj_spec = nullptr;
   // staging for pm_step_host
@@ -469,7 +469,7 @@ int pm_init(const pm_config_t* cfg, pm_handle_t** out) {
     if (cudaDeviceSynchronize() != cudaSuccess) rc = fail(h, PM_ERR_CUDA, "init sync");
   }
   if (!g.two) {
-    A(&h->lam_acc, 3 * nf3 * 4);
+    A(&h->lam_acc, 4 * nf3 * 4);
     A(&h->adj_spec, (size_t)3 * g.nf * g.nf * (g.nf / 2 + 1) * sizeof(float2));
   }
   h->blk_dep = choose_blk(g, fixed, true);
@@ -1052,7 +1052,7 @@ int pm_deposit_adjoint(pm_handle_t* h, int species, const float* x, int64_t n, c
 int pm_solve_adjoint(pm_handle_t* h, const float* lam_acc, float* lam_rho, void* stream) {
   if (!h || !lam_acc || !lam_rho) return fail(h, PM_ERR_ARG, "null argument");
   if (h->gm.two) return fail(h, PM_ERR_CONFIG, "adjoints are implemented for the single periodic mesh");
-  CK(h, solve_adjoint_launch(h->plan_mesh, lam_acc, lam_rho, h->adj_spec, (cudaStream_t)stream));
+  CK(h, solve_adjoint_launch(h->plan_mesh, lam_acc, false, lam_rho, h->adj_spec, (cudaStream_t)stream));
   return PM_OK;
 }
 
@@ -1060,7 +1060,7 @@ int pm_interpolate_adjoint(pm_handle_t* h, const float* x, int64_t n, const floa
                            double c_drift, float* lam_x, float* lam_v, float* lam_acc, void* stream) {
   if (!h || (n && (!x || !lam_x || !lam_v)) || !acc_fine || !lam_acc) return fail(h, PM_ERR_ARG, "null argument");
   if (h->gm.two) return fail(h, PM_ERR_CONFIG, "adjoints are implemented for the single periodic mesh");
-  CK(h, launch_adj_interp(x, n, h->gm.nf, acc_fine, (float)c_kick, (float)c_drift, lam_x, lam_v, lam_acc,
+  CK(h, launch_adj_interp(x, n, h->gm.nf, acc_fine, (float)c_kick, (float)c_drift, lam_x, lam_v, lam_acc, false,
                           (cudaStream_t)stream));
   return PM_OK;
 }
@@ -1090,11 +1090,12 @@ int pm_step_adjoint(pm_handle_t* h, const pm_particles_t state[2], pm_particles_
       CK(h, launch_deposit(state[s].x, state[s].n, (float)h->cfg.mass[s], h->geo, nullptr, h->rho_f, st));
     CK(h, solve_launch(h->plan_mesh, h->rho_f, false, h->acc_f, st, nullptr));
   }
-  CK(h, cudaMemsetAsync(h->lam_acc, 0, 3 * nf3 * 4, st));
+  // interleaved float4 accumulation mesh: one vector reduction per CIC corner
+  CK(h, cudaMemsetAsync(h->lam_acc, 0, 4 * nf3 * 4, st));
   for (int s = 0; s < 2; ++s)
     CK(h, launch_adj_interp(state[s].x, state[s].n, g.nf, h->acc_f, (float)c_kick, (float)c_drift, lam[s].x, lam[s].v,
-                            h->lam_acc, st));
-  CK(h, solve_adjoint_launch(h->plan_mesh, h->lam_acc, h->rho_f, h->adj_spec, st));   // rho_f holds lam_rho
+                            h->lam_acc, true, st));
+  CK(h, solve_adjoint_launch(h->plan_mesh, h->lam_acc, true, h->rho_f, h->adj_spec, st));   // rho_f holds lam_rho
   for (int s = 0; s < 2; ++s)
     CK(h, launch_adj_deposit(state[s].x, state[s].n, (float)h->cfg.mass[s], g.nf, h->rho_f, lam[s].x, st));
   return PM_OK;

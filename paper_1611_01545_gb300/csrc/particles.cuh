@@ -95,7 +95,9 @@ cudaError_t launch_vmax_bound(const float* vin0, const float* vin1, const uint32
                               float* vout1, cudaStream_t st);
 cudaError_t launch_adj_deposit(const float* x, int64_t n, float m, int nf, const float* lam_rho, float* lam_x,
                                cudaStream_t st);
+// lam_A is [3][n^3], or float4 [n^3] (x, y, z, unused) when interleaved (one vector
+// reduction per corner instead of three).
 cudaError_t launch_adj_interp(const float* x, int64_t n, int nf, const float* acc, float ck, float cd, float* lam_x,
-                              float* lam_v, float* lam_A, cudaStream_t st);
+                              float* lam_v, float* lam_A, bool interleaved, cudaStream_t st);
 
 }  // namespace pm

@@ -63,9 +63,10 @@ cudaError_t solve_launch(const SolvePlan& p, const void* src, bool src_fixed, fl
 // Coarse density from the fine one (CIC restriction, float32).
 cudaError_t launch_restrict(const float* rho_f, int nf, int rc, float* rho_c, cudaStream_t st);
 // Transpose of the periodic-mesh solve (adjoint): lam_rho = A^T lam_acc; spec3comp holds
-// the three component spectra [3][N][N][N/2+1].
-cudaError_t solve_adjoint_launch(const SolvePlan& p, const float* lam_acc, float* lam_rho, float2* spec3comp,
-                                 cudaStream_t st);
+// the three component spectra [3][N][N][N/2+1].  lam_acc is [3][n^3], or float4 [n^3]
+// (x, y, z, unused) when interleaved.
+cudaError_t solve_adjoint_launch(const SolvePlan& p, const float* lam_acc, bool interleaved, float* lam_rho,
+                                 float2* spec3comp, cudaStream_t st);
 cudaError_t tile_window_launch(const SolvePlan& p, const float* src, int64_t tile, float* out, cudaStream_t st);
 
 // Per-launch CUDA-event timing, accumulated by kind.

@@ -49,7 +49,7 @@ struct SolveArgs {
   const float* kern;
   const float2* tw;
   float* dst;
-  int comp_mode;   // pass A only: blockIdx.y selects component pb of a [3][n^3] source at origin 0
+  int comp_mode;   // pass A only: blockIdx.y selects component pb of a 3-component source at origin 0
   unsigned int* amax;   // pass C: if set, atomicMax of max |output| (float bits; values are >= 0)
   const float* pc;      // pass C: if set, add this coarse force [3][pnc^3] trilinearly prolongated to the fine nodes
   int pnc, prc;         // its edge and the fine cells per coarse cell (a power of two dividing t)
@@ -96,7 +96,9 @@ __device__ __forceinline__ float src_value(const void* src, int64_t idx) {
 
 __device__ __forceinline__ int wrap1(int g, int n) { return g < 0 ? g + n : (g >= n ? g - n : g); }
 
-template <int N, bool FIXED>
+// CS > 1 (comp_mode only): the components are interleaved, element i of
+// component pb at src[i * CS + pb] (the adjoint's float4 accumulation mesh).
+template <int N, bool FIXED, int CS = 1>
 __device__ __forceinline__ void solve_a_body(const SolveArgs& a) {
   constexpr int NH = SolveCfg<N>::NH;
   extern __shared__ float2 sm[];
@@ -112,7 +114,7 @@ __device__ __forceinline__ void solve_a_body(const SolveArgs& a) {
   const void* src = a.src;
   if (a.comp_mode) {
     ox = oy = oz = 0;
-    src = static_cast<const float*>(a.src) + (size_t)pb * n * n * n;
+    src = static_cast<const float*>(a.src) + (CS > 1 ? (size_t)pb : (size_t)pb * n * n * n);
   }
   // origins lie in (-n, n) and N <= n, so one conditional wrap suffices
   const int gz = wrap1(oz + z, n);
@@ -122,8 +124,8 @@ __device__ __forceinline__ void solve_a_body(const SolveArgs& a) {
     if (FIXED) {
       PM_COLS(x, N) w[2 * x] = src_value<FIXED>(src, rowbase + wrap1(ox + x, n));
     } else {
-      const float* srow = static_cast<const float*>(src) + rowbase;
-      PM_COLS(x, N) async_copy4(w + 2 * x, srow + wrap1(ox + x, n));
+      const float* srow = static_cast<const float*>(src) + rowbase * CS;
+      PM_COLS(x, N) async_copy4(w + 2 * x, srow + wrap1(ox + x, n) * CS);
     }
   }
   if (!FIXED) async_wait();
@@ -147,9 +149,9 @@ __device__ __forceinline__ void solve_a_body(const SolveArgs& a) {
   for (int i = threadIdx.x; i < N * NH / 2; i += blockDim.x) out[i] = P4[i];
 }
 
-template <int N, bool FIXED>
+template <int N, bool FIXED, int CS = 1>
 __global__ void __launch_bounds__(SolveCfg<N>::threads) k_solve_a(SolveArgs a) {
-  solve_a_body<N, FIXED>(a);
+  solve_a_body<N, FIXED, CS>(a);
 }
 
 // The 96^3 tiles' pass A is compiled for 3 resident blocks per SM (40
@@ -465,14 +467,15 @@ cudaError_t solve_launch(const SolvePlan& p, const void* src, bool fixed, float*
 }
 
 template <int N>
-static cudaError_t solve_adjoint_n(const SolvePlan& p, const float* lam_acc, float* lam_rho, float2* spec3comp,
-                                   cudaStream_t st) {
+static cudaError_t solve_adjoint_n(const SolvePlan& p, const float* lam_acc, bool interleaved, float* lam_rho,
+                                   float2* spec3comp, cudaStream_t st) {
   using C = SolveCfg<N>;
-  cudaFuncSetAttribute(solve_a_kernel<N, false>(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem_a);
+  const auto ka = interleaved ? k_solve_a<N, false, 4> : solve_a_kernel<N, false>();
+  cudaFuncSetAttribute(ka, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem_a);
   cudaFuncSetAttribute(k_solve_b_adj<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sizeof(float2) * (N + 2 * (size_t)N * PassB<N>::KC)));
   cudaFuncSetAttribute(k_solve_c<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem_a);
   SolveArgs a{lam_acc, 0, p.src_n, 1, N, 0, 0, spec3comp, p.spec3, p.kern, p.tw, lam_rho, 1};
-  solve_a_kernel<N, false>()<<<dim3(N, 3), C::threads, C::smem_a, st>>>(a);
+  ka<<<dim3(N, 3), C::threads, C::smem_a, st>>>(a);
   a.comp_mode = 0;
   k_solve_b_adj<N><<<dim3(N, 2, 1), PassB<N>::threads, sizeof(float2) * (N + 2 * (size_t)N * PassB<N>::KC), st>>>(a);
   k_solve_c<N><<<dim3(N, 1, 1), C::threads_c, C::smem_a, st>>>(a);
@@ -480,16 +483,16 @@ static cudaError_t solve_adjoint_n(const SolvePlan& p, const float* lam_acc, flo
   return cudaGetLastError();
 }
 
-cudaError_t solve_adjoint_launch(const SolvePlan& p, const float* lam_acc, float* lam_rho, float2* spec3comp,
-                                 cudaStream_t st) {
+cudaError_t solve_adjoint_launch(const SolvePlan& p, const float* lam_acc, bool interleaved, float* lam_rho,
+                                 float2* spec3comp, cudaStream_t st) {
   if (p.nts != 1 || p.b != 0 || p.t != p.N) return cudaErrorInvalidValue;
   switch (p.N) {
-    case 16: return solve_adjoint_n<16>(p, lam_acc, lam_rho, spec3comp, st);
-    case 32: return solve_adjoint_n<32>(p, lam_acc, lam_rho, spec3comp, st);
-    case 48: return solve_adjoint_n<48>(p, lam_acc, lam_rho, spec3comp, st);
-    case 64: return solve_adjoint_n<64>(p, lam_acc, lam_rho, spec3comp, st);
-    case 96: return solve_adjoint_n<96>(p, lam_acc, lam_rho, spec3comp, st);
-    case 128: return solve_adjoint_n<128>(p, lam_acc, lam_rho, spec3comp, st);
+    case 16: return solve_adjoint_n<16>(p, lam_acc, interleaved, lam_rho, spec3comp, st);
+    case 32: return solve_adjoint_n<32>(p, lam_acc, interleaved, lam_rho, spec3comp, st);
+    case 48: return solve_adjoint_n<48>(p, lam_acc, interleaved, lam_rho, spec3comp, st);
+    case 64: return solve_adjoint_n<64>(p, lam_acc, interleaved, lam_rho, spec3comp, st);
+    case 96: return solve_adjoint_n<96>(p, lam_acc, interleaved, lam_rho, spec3comp, st);
+    case 128: return solve_adjoint_n<128>(p, lam_acc, interleaved, lam_rho, spec3comp, st);
     default: return cudaErrorInvalidValue;
   }
 }

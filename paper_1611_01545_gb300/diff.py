@@ -5,9 +5,9 @@ The loss is L = sum_c (rho_K(c) - target(c))^2 of the density after K steps,
 the variable the initial CDM displacement field psi (x0 = q + psi wrapped
 into the box, v0 = beta psi); neutrinos start from fixed phase-space
 positions.  The forward pass keeps the state every `every` steps; the
-backward pass recomputes each segment from its checkpoint (the fixed-point
-deposit makes the recompute bit-identical) and runs pm_step_adjoint in
-reverse.  All mesh and particle arithmetic runs in libpm's kernels; torch
+backward pass recomputes each segment from its checkpoint up to the
+positions before its last step (the fixed-point deposit makes the
+recompute bit-identical) and runs pm_step_adjoint in reverse.  All mesh and particle arithmetic runs in libpm's kernels; torch
 supplies memory and the loss's elementwise terms.
 """
 from __future__ import annotations
@@ -62,12 +62,16 @@ class PMTrajectoryLoss(torch.autograd.Function):
         for idx in range(len(ctx.checkpoints) - 1, -1, -1):
             k0, x0, v0 = ctx.checkpoints[idx]
             k1 = ctx.checkpoints[idx + 1][0] if idx + 1 < len(ctx.checkpoints) else ctx.steps
-            x = [t.clone() for t in x0]
-            v = [t.clone() for t in v0]
-            pre = []
-            for _ in range(k0, k1):
-                pre.append([t.clone() for t in x])
-                pm.step_plain(x, v, ctx.ck, ctx.cd, fixed=True)
+            # pre-step positions of steps k0 .. k1-1: the checkpoint and k1-k0-1
+            # recomputed steps (the segment's last step is never re-run: its
+            # adjoint needs only the positions before it)
+            pre = [x0]
+            if k1 - k0 > 1:
+                x = [t.clone() for t in x0]
+                v = [t.clone() for t in v0]
+                for _ in range(k0, k1 - 1):
+                    pm.step_plain(x, v, ctx.ck, ctx.cd, fixed=True)
+                    pre.append([t.clone() for t in x])
             for xs in reversed(pre):
                 pm.step_adjoint(xs, lam_x, lam_v, ctx.ck, ctx.cd)
         grad = lam_x[0] + ctx.beta * lam_v[0]

@@ -66,8 +66,10 @@ def test_one_reverse_step_matches_oracle():
         assert rel_rms(gx[s].cpu().numpy(), rx[s]) < ADJ_TOL, (s, rel_rms(gx[s].cpu().numpy(), rx[s]))
 
 
-@pytest.mark.parametrize("beta", [0.0, 0.3])
-def test_trajectory_gradient_matches_oracle(beta):
+@pytest.mark.parametrize("beta,every", [(0.0, 2), (0.3, 2), (0.3, 3)])
+def test_trajectory_gradient_matches_oracle(beta, every):
+    """every=3 over 4 steps gives a 3-step segment (two recomputed steps) and a
+    1-step segment (none recomputed)."""
     from paper_1611_01545_gb300.diff import trajectory_loss
     w = make_workload("diff128", n_cdm=8, n_nu=16)
     n = 32
@@ -79,7 +81,7 @@ def test_trajectory_gradient_matches_oracle(beta):
     psi = (rng.standard_normal(q.shape) * 0.3).astype(np.float32)
     vnu = (w.v[1] * 0.2).astype(np.float32)
     target = (rng.random((n, n, n)) * 0.02).astype(np.float32)
-    steps, every, ck, cd = 4, 2, 0.5, 0.5
+    steps, ck, cd = 4, 0.5, 0.5
     psi_t = torch.from_numpy(psi).cuda().requires_grad_(True)
     L = trajectory_loss(pm, psi_t, torch.from_numpy(q).cuda(), torch.from_numpy(w.x[1]).cuda(),
                         torch.from_numpy(vnu).cuda(), torch.from_numpy(target).cuda(), beta, steps, every, ck, cd)
