@@ -307,7 +307,13 @@ int pm_step_packed(pm_handle_t* h, const pm_host_codes_t in[2], pm_host_codes_t 
  *                          state[s].x (cfg.deposit_mode as in the forward; use
  *                          the fixed-point mode for a bit-exact recompute), then
  *                          maps lam[s] = (dL/dx', dL/dv') after the step to
- *                          (dL/dx, dL/dv) before it, in place. */
+ *                          (dL/dx, dL/dv) before it, in place.
+ * pm_step_adjoint_acc:    the same reverse step with the step's acceleration
+ *                          mesh supplied (acc_fine [3][n^3] float32, device,
+ *                          read only: pm_solve's output at the pre-step
+ *                          positions, e.g. kept from a checkpoint segment's
+ *                          recompute), so nothing is recomputed.  PM_ERR_ARG
+ *                          for a null mesh. */
 int pm_deposit_adjoint(pm_handle_t* h, int species, const float* x, int64_t n, const float* lam_rho, float* lam_x,
                        void* stream);
 int pm_solve_adjoint(pm_handle_t* h, const float* lam_acc, float* lam_rho, void* stream);
@@ -315,6 +321,8 @@ int pm_interpolate_adjoint(pm_handle_t* h, const float* x, int64_t n, const floa
                            double c_drift, float* lam_x, float* lam_v, float* lam_acc, void* stream);
 int pm_step_adjoint(pm_handle_t* h, const pm_particles_t state[2], pm_particles_t lam[2], double c_kick,
                     double c_drift, void* stream);
+int pm_step_adjoint_acc(pm_handle_t* h, const pm_particles_t state[2], pm_particles_t lam[2], const float* acc_fine,
+                        double c_kick, double c_drift, void* stream);
 
 /* Synchronises `stream`, returns and clears the sticky device status
  * (PM_OK, PM_ERR_CORRUPT, PM_ERR_OVERFLOW, PM_ERR_RANGE, PM_ERR_TIMEOUT). */

@@ -57,7 +57,7 @@ EXPORTED = ["pm_init", "pm_destroy", "pm_geometry", "pm_decompress", "pm_compres
             "pm_step_packed", "pm_restrict",
             "pm_stage_times", "pm_serialize", "pm_deserialize", "pm_error_string", "pm_launch_count",
             "pm_decompress_noalloc", "pm_deposit_adjoint", "pm_solve_adjoint", "pm_interpolate_adjoint",
-            "pm_step_adjoint"]
+            "pm_step_adjoint", "pm_step_adjoint_acc"]
 
 _P = ctypes.c_void_p
 _I64 = ctypes.c_int64
@@ -108,6 +108,8 @@ _PROTOS = {
     "pm_interpolate_adjoint": (ctypes.c_int, [_P, _P, _I64, _P, _D, _D, _P, _P, _P, _P]),
     "pm_step_adjoint": (ctypes.c_int, [_P, ctypes.POINTER(pm_particles_t), ctypes.POINTER(pm_particles_t), _D, _D,
                                        _P]),
+    "pm_step_adjoint_acc": (ctypes.c_int, [_P, ctypes.POINTER(pm_particles_t), ctypes.POINTER(pm_particles_t), _P,
+                                           _D, _D, _P]),
     "pm_decompress_noalloc": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                              ctypes.POINTER(pm_codes_t), _P, _P, _P]),
 }

@@ -1065,17 +1065,37 @@ int pm_interpolate_adjoint(pm_handle_t* h, const float* x, int64_t n, const floa
   return PM_OK;
 }
 
-int pm_step_adjoint(pm_handle_t* h, const pm_particles_t state[2], pm_particles_t lam[2], double c_kick,
-                    double c_drift, void* stream) {
+// The reverse step given the step's acceleration mesh acc [3][n^3] at the pre-step positions.
+static int step_adjoint_core(pm_handle_t* h, const pm_particles_t state[2], pm_particles_t lam[2], const float* acc,
+                             double c_kick, double c_drift, cudaStream_t st) {
+  const Geom& g = h->gm;
+  const size_t nf3 = (size_t)g.nfine3();
+  // interleaved float4 accumulation mesh: one vector reduction per CIC corner
+  CK(h, cudaMemsetAsync(h->lam_acc, 0, 4 * nf3 * 4, st));
+  for (int s = 0; s < 2; ++s)
+    CK(h, launch_adj_interp(state[s].x, state[s].n, g.nf, acc, (float)c_kick, (float)c_drift, lam[s].x, lam[s].v,
+                            h->lam_acc, true, st));
+  CK(h, solve_adjoint_launch(h->plan_mesh, h->lam_acc, true, h->rho_f, h->adj_spec, st));   // rho_f holds lam_rho
+  for (int s = 0; s < 2; ++s)
+    CK(h, launch_adj_deposit(state[s].x, state[s].n, (float)h->cfg.mass[s], g.nf, h->rho_f, lam[s].x, st));
+  return PM_OK;
+}
+
+static int check_adjoint_args(pm_handle_t* h, const pm_particles_t state[2], pm_particles_t lam[2]) {
   if (!h || !state || !lam) return fail(h, PM_ERR_ARG, "null argument");
   if (h->gm.two) return fail(h, PM_ERR_CONFIG, "adjoints are implemented for the single periodic mesh");
   for (int s = 0; s < 2; ++s)
     if (state[s].n != lam[s].n || (state[s].n && (!state[s].x || !lam[s].x || !lam[s].v)))
       return fail(h, PM_ERR_ARG, "state and adjoint particle arrays disagree");
+  return PM_OK;
+}
+
+int pm_step_adjoint(pm_handle_t* h, const pm_particles_t state[2], pm_particles_t lam[2], double c_kick,
+                    double c_drift, void* stream) {
+  if (int rc = check_adjoint_args(h, state, lam)) return rc;
   cudaStream_t st = (cudaStream_t)stream;
-  const Geom& g = h->gm;
   const bool fixed = h->cfg.deposit_mode == 1;
-  const size_t nf3 = (size_t)g.nfine3();
+  const size_t nf3 = (size_t)h->gm.nfine3();
   // recompute the step's acceleration mesh at the pre-step positions
   if (fixed) {
     CK(h, cudaMemsetAsync(h->rho_f_fix, 0, nf3 * 8, st));
@@ -1090,15 +1110,14 @@ int pm_step_adjoint(pm_handle_t* h, const pm_particles_t state[2], pm_particles_
       CK(h, launch_deposit(state[s].x, state[s].n, (float)h->cfg.mass[s], h->geo, nullptr, h->rho_f, st));
     CK(h, solve_launch(h->plan_mesh, h->rho_f, false, h->acc_f, st, nullptr));
   }
-  // interleaved float4 accumulation mesh: one vector reduction per CIC corner
-  CK(h, cudaMemsetAsync(h->lam_acc, 0, 4 * nf3 * 4, st));
-  for (int s = 0; s < 2; ++s)
-    CK(h, launch_adj_interp(state[s].x, state[s].n, g.nf, h->acc_f, (float)c_kick, (float)c_drift, lam[s].x, lam[s].v,
-                            h->lam_acc, true, st));
-  CK(h, solve_adjoint_launch(h->plan_mesh, h->lam_acc, true, h->rho_f, h->adj_spec, st));   // rho_f holds lam_rho
-  for (int s = 0; s < 2; ++s)
-    CK(h, launch_adj_deposit(state[s].x, state[s].n, (float)h->cfg.mass[s], g.nf, h->rho_f, lam[s].x, st));
-  return PM_OK;
+  return step_adjoint_core(h, state, lam, h->acc_f, c_kick, c_drift, st);
+}
+
+int pm_step_adjoint_acc(pm_handle_t* h, const pm_particles_t state[2], pm_particles_t lam[2], const float* acc_fine,
+                        double c_kick, double c_drift, void* stream) {
+  if (int rc = check_adjoint_args(h, state, lam)) return rc;
+  if (!acc_fine) return fail(h, PM_ERR_ARG, "null acceleration mesh");
+  return step_adjoint_core(h, state, lam, acc_fine, c_kick, c_drift, (cudaStream_t)stream);
 }
 
 static int alloc_codes(pm_handle* h, pm_codes_t& c, int64_t n, int64_t esc_cap) {

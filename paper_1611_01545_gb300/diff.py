@@ -64,16 +64,18 @@ class PMTrajectoryLoss(torch.autograd.Function):
             k1 = ctx.checkpoints[idx + 1][0] if idx + 1 < len(ctx.checkpoints) else ctx.steps
             # pre-step positions of steps k0 .. k1-1: the checkpoint and k1-k0-1
             # recomputed steps (the segment's last step is never re-run: its
-            # adjoint needs only the positions before it)
-            pre = [x0]
+            # adjoint needs only the positions before it).  A recomputed step
+            # keeps its acceleration mesh for its reverse step; the last one's
+            # is recomputed by pm_step_adjoint.
+            pre = [[x0, None]]
             if k1 - k0 > 1:
                 x = [t.clone() for t in x0]
                 v = [t.clone() for t in v0]
                 for _ in range(k0, k1 - 1):
-                    pm.step_plain(x, v, ctx.ck, ctx.cd, fixed=True)
-                    pre.append([t.clone() for t in x])
-            for xs in reversed(pre):
-                pm.step_adjoint(xs, lam_x, lam_v, ctx.ck, ctx.cd)
+                    pre[-1][1] = pm.step_plain(x, v, ctx.ck, ctx.cd, fixed=True)
+                    pre.append([[t.clone() for t in x], None])
+            for xs, acc in reversed(pre):
+                pm.step_adjoint(xs, lam_x, lam_v, ctx.ck, ctx.cd, acc_fine=acc)
         grad = lam_x[0] + ctx.beta * lam_v[0]
         return grad, None, None, None, None, None, None, None, None, None, None
 

@@ -241,12 +241,14 @@ class PM:
 
     def step_plain(self, xs: Sequence[torch.Tensor], vs: Sequence[torch.Tensor], c_kick: float, c_drift: float,
                    fixed: bool = True, stream=None):
-        """One uncompressed step in place: deposit, solve, interpolate + kick + drift."""
+        """One uncompressed step in place: deposit, solve, interpolate + kick + drift.
+        Returns the step's fine acceleration mesh [3][n^3] (at the pre-step positions)."""
         rc, rf = self.density(xs, fixed, stream)
         ac, af = self.zeros_acc()
         self.solve(rc, rf, ac, af, stream)
         for x, v in zip(xs, vs):
             self.kick_drift(x, v, ac, af, c_kick, c_drift, stream)
+        return af
 
     def deposit_adjoint(self, species: int, x: torch.Tensor, lam_rho: torch.Tensor, lam_x: torch.Tensor, stream=None):
         self._err(self.lib.pm_deposit_adjoint(self.h, species, _ptr(x), x.shape[0], _ptr(lam_rho), _ptr(lam_x),
@@ -260,11 +262,17 @@ class PM:
                                                   _ptr(lam_x), _ptr(lam_v), _ptr(lam_acc), _stream(stream)))
 
     def step_adjoint(self, xs: Sequence[torch.Tensor], lam_x: Sequence[torch.Tensor], lam_v: Sequence[torch.Tensor],
-                     c_kick: float, c_drift: float, stream=None):
+                     c_kick: float, c_drift: float, acc_fine: Optional[torch.Tensor] = None, stream=None):
+        """Reverse step in place; acc_fine (the step's [3][n^3] acceleration mesh at
+        xs) skips its recompute."""
         st = (pm_particles_t * 2)(*[pm_particles_t(x.shape[0], x.data_ptr(), 0) for x in xs])
         lam = (pm_particles_t * 2)(*[pm_particles_t(a.shape[0], a.data_ptr(), b.data_ptr())
                                      for a, b in zip(lam_x, lam_v)])
-        self._err(self.lib.pm_step_adjoint(self.h, st, lam, c_kick, c_drift, _stream(stream)))
+        if acc_fine is None:
+            self._err(self.lib.pm_step_adjoint(self.h, st, lam, c_kick, c_drift, _stream(stream)))
+        else:
+            self._err(self.lib.pm_step_adjoint_acc(self.h, st, lam, _ptr(acc_fine), c_kick, c_drift,
+                                                   _stream(stream)))
 
     def restrict(self, rho_fine: torch.Tensor, stream=None) -> torch.Tensor:
         """Coarse density from a fine one (CIC restriction)."""
