@@ -184,6 +184,60 @@ def build_state(pm, w, torch):
     return codes, spare
 
 
+# Largest one-GPU workload: two-level PM on a 1536^3 fine mesh (384^3 coarse,
+# 13,824 tiles of 64^3 + 16), 768^3 Zel'dovich CDM + 1536^3 Fermi-Dirac
+# neutrinos (4.08e9 particles, 16-bit velocities), drawn on the device.
+LARGEST = dict(n_fine=1536, coarse_ratio=4, tile=64, buffer=16, cmp_ratio=4, vel_bits=16, n_cdm=768, n_nu=1536,
+               r_cut=14.0, seed=1619)
+
+
+def largest_config(tile_batch=64):
+    L = LARGEST
+    return dict(n_fine=L["n_fine"], coarse_ratio=L["coarse_ratio"], tile=L["tile"], buffer=L["buffer"],
+                cmp_ratio=L["cmp_ratio"], vel_bits=L["vel_bits"], G=1.0 / (4.0 * np.pi), mass=(8.0, 0.04),
+                count=(L["n_cdm"] ** 3, L["n_nu"] ** 3), r_split=L["r_cut"] / 4.5, r_cut=L["r_cut"],
+                tile_batch=tile_batch)
+
+
+def build_largest_codes(pm, torch):
+    """The largest workload's compressed state, built on the device: the CDM
+    set compressed whole; the neutrinos one z slab of compression cells at a
+    time (each slab's codes copied into place), with the species' v_max found
+    over all slabs first.  No host array holds the particles."""
+    from synth import device as dev
+    L = LARGEST
+    nf, ncmp = L["n_fine"], L["n_fine"] // L["cmp_ratio"]
+    ncell_slab = ncmp * ncmp
+    codes = []
+    x, v = dev.zeldovich_lattice(L["seed"], L["n_cdm"], nf)
+    c0 = pm.empty_codes(x.shape[0], esc_cap=x.shape[0] // 255 + 1)
+    pm.compress(0, x, v, out=c0)
+    del x, v
+    codes.append(c0)
+    n_nu = L["n_nu"] ** 3
+    per = n_nu // ncmp
+    seed = L["seed"] + 1
+    vmax = torch.zeros(1, dtype=torch.float32, device="cuda")
+    for k in range(ncmp):
+        vmax = torch.maximum(vmax, dev.neutrino_slab(seed, k, ncmp, per, nf, velocities_only=True).abs().max())
+    c1 = pm.empty_codes(n_nu, esc_cap=n_nu // 255 + 1)
+    c1.vmax.copy_(vmax)
+    slab = pm.empty_codes(per, esc_cap=per // 255 + 1)
+    for k in range(ncmp):
+        x, v = dev.neutrino_slab(seed, k, ncmp, per, nf)
+        pm.compress(1, x, v, vmax=vmax, out=slab)
+        lo = k * ncell_slab
+        c1.cnt[lo:lo + ncell_slab].copy_(slab.cnt[lo:lo + ncell_slab])
+        c1.pos[k * per:(k + 1) * per].copy_(slab.pos)
+        c1.vel[k * per:(k + 1) * per].copy_(slab.vel)
+        if int(slab.n_esc.item()) != 0:
+            raise RuntimeError("a neutrino slab produced escape entries; the slab assembly does not merge them")
+    del x, v, slab
+    codes.append(c1)
+    pm.check()
+    return codes
+
+
 def codes_bytes(c, vel_bits, packed=False):
     """Bytes of one species' codes: packed record bytes (3 + 3 or 6 per particle)
     or the padded in-memory words (4 + 4 or 8), plus counts, escapes and v_max."""
@@ -231,9 +285,90 @@ def plain_step_ms(pm, w, codes, spare, torch, stream, steps: int) -> float:
     return ms
 
 
+def run_largest(args):
+    """The largest one-GPU workload (1536^3, 4.08e9 particles): the fused step
+    replayed from a graph, then per-stage CUDA-event times.  Inputs are built
+    on the device; no host copy of the state is made, so there is no
+    end-to-end number for this workload."""
+    import torch
+
+    from paper_1611_01545_gb300 import PM, _lib
+
+    rank, world, local = dist_env()
+    if world > 1:
+        return None if rank else {"workload": "largest1536", "skipped": "one-GPU workload"}
+    torch.cuda.set_device(local)
+    cfg = largest_config(args.tile_batch or 64)
+    cfg["vmax_mode"] = args.vmax_mode
+    t0 = time.perf_counter()
+    pm = PM(cfg)
+    a = build_largest_codes(pm, torch)
+    b = [pm.empty_codes(c.n, esc_cap=c.esc.shape[0]) for c in a]
+    build_s = time.perf_counter() - t0
+    if args.tuning:
+        pm.set_tuning(json.loads(args.tuning))
+    tuning = pm.get_tuning()
+    n_total = sum(c.n for c in a)
+    lib = _lib.load()
+    stream = torch.cuda.current_stream()
+
+    def one_step():
+        pm.step(a, b, 1.0, 1.0)
+
+    pm.set_graphs(True)
+    for _ in range(args.warmup):
+        one_step()
+    pm.check()
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    torch.cuda.synchronize()
+    launches0 = lib.pm_launch_count()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        one_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    launches = lib.pm_launch_count() - launches0
+    sampler.stop()
+    ms = e0.elapsed_time(e1)
+    pm.check()
+    pm.set_graphs(False)
+    pm.set_timing(True)
+    for _ in range(max(1, min(args.steps, 3))):
+        one_step()
+    torch.cuda.synchronize()
+    pm.check()
+    stages = pm.stage_times()
+    pm.set_timing(False)
+    free, total = torch.cuda.mem_get_info()
+    alg = algorithmic_bytes(dict(cfg, tile_batch=tuning["tile_batch"]), [c.n for c in a], cfg["vel_bits"])
+    result = {
+        "metric": METRIC, "value": n_total * args.steps / (ms / 1e3), "unit": UNIT, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic (device-generated)",
+        "config": {"workload": "largest1536", "n_fine": cfg["n_fine"], "coarse_ratio": 4, "tile": 64, "buffer": 16,
+                   "tile_batch": tuning["tile_batch"], "particles": {"cdm": a[0].n, "nu": a[1].n},
+                   "vel_bits": 16, "vmax_mode": args.vmax_mode, "l2": "working set > L2"},
+        "e2e": None, "gpu_launches": int(launches), "tuning": tuning,
+        "stages_ms": {k: round(v[0], 4) for k, v in stages.items()},
+        "stage_launches": {k: v[1] for k, v in stages.items()},
+        "stage_gbs": {k: round(alg[k] / (v[0] / 1e3) / 1e9, 1) for k, v in stages.items() if k in alg},
+        "device_memory_used_gb": round((total - free) / 1e9, 1), "build_s": round(build_s, 1),
+        "clocks": sampler.summary(),
+    }
+    pm.close()
+    return result
+
+
 def run_gb300(args):
     import torch
     import torch.distributed as dist
+
+    if args.workload == "largest1536":
+        return run_largest(args)
 
     from paper_1611_01545_gb300 import PM, _lib
     from synth import make_workload

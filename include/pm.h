@@ -60,7 +60,10 @@ typedef struct pm_handle pm_handle_t;
  *  coarse_ratio  fine cells per coarse cell (the paper uses 4: the short-
  *                range mesh is 4x finer than the long-range one).  1 selects
  *                a single periodic mesh solved with the full Green's
- *                function of Eq. 2 (no tiles, no split).
+ *                function of Eq. 2 (no tiles, no split); its edge n_fine
+ *                must be one of 16, 32, 48, 64, 96, 128.  In two-level mode
+ *                the coarse edge n_fine / coarse_ratio must be one of those
+ *                or 192, 256, 384 (n_fine up to 1536).
  *  tile, buffer  fine-tile interior edge t and buffer width b (Fig. 1);
  *                tile edge T = t + 2b must be one of 16, 32, 48, 64, 96,
  *                128; t must divide n_fine; T <= n_fine.

@@ -22,7 +22,8 @@ removed); at the Nyquist index the gradient factor k_d is set to 0 (k^2
 keeps its full value) so the force stays real; no CIC deconvolution.
 
 Pins: tests/test_oracle_solve.py (plane waves, brute-force real-space
-convolution for the tile kernel, momentum conservation, 1/r^2).
+convolution for the tile kernel, momentum conservation, 1/r^2; the one-mode
+forms against the definition, the full transform and a plane wave).
 """
 from __future__ import annotations
 
@@ -61,6 +62,38 @@ def accel_periodic(M: np.ndarray, h: float, G: float, r_s: float = 0.0) -> np.nd
     for d, kd in enumerate((gx, gy, gz)):
         out[d] = fft3(1j * kd * g * Mk, inverse=True).real
     return out
+
+
+def dft_mode(F: np.ndarray, m) -> complex:
+    """One coefficient of the unnormalised forward 3-D DFT of a real field F
+    [n, n, n] ([z, y, x]) at mode numbers m = (mx, my, mz), straight from the
+    definition sum_c F(c) exp(-2 pi i m.c / n), summed one axis at a time."""
+    F = np.asarray(F, dtype=np.float64)
+    n = F.shape[0]
+    j = np.arange(n)
+    ex, ey, ez = (np.exp(-2j * np.pi * mm * j / n) for mm in m)
+    t = F @ ex.real + 1j * (F @ ex.imag)          # [z, y]
+    return complex(ez @ (t @ ey))
+
+
+def accel_mode(M: np.ndarray, h: float, G: float, r_s: float, m) -> np.ndarray:
+    """The DFT coefficient at mode numbers m = (mx, my, mz) of the three
+    components of accel_periodic(M, h, G, r_s), from Eqs. 2-3 at that one wave
+    vector: n^3 i k_d g(k) DFT[M](m), g = 4 pi G exp(-k^2 r_s^2) / (k^2 V),
+    with the same readings (0 at k = 0, k_d = 0 at the Nyquist index).  For
+    meshes too large for a full oracle transform."""
+    n = M.shape[0]
+    V = (n * h) ** 3
+    mm = [((int(c) + n // 2) % n) - n // 2 if (int(c) % n) != n // 2 else n // 2 for c in m]
+    k = np.array([2.0 * np.pi * c / (n * h) for c in mm])
+    kgrad = np.array([0.0 if 2 * abs(c) == n else kd for c, kd in zip(mm, k)])
+    k2 = float(np.sum(k * k))
+    if k2 == 0.0:
+        return np.zeros(3, dtype=np.complex128)
+    g = 4.0 * np.pi * G / (k2 * V)
+    if r_s > 0:
+        g *= math.exp(-k2 * r_s * r_s)
+    return n ** 3 * 1j * kgrad * g * dft_mode(M, m)
 
 
 def short_range_shape(r: np.ndarray, r_s: float) -> np.ndarray:

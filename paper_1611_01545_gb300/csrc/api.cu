@@ -111,6 +111,8 @@ cudaError_t dalloc(pm_handle* h, T** p, size_t bytes) {
 }
 
 bool supported_fft(int n) { return n == 16 || n == 32 || n == 48 || n == 64 || n == 96 || n == 128; }
+// The coarse mesh also takes the large sizes (row / column FFT passes).
+bool supported_coarse(int n) { return supported_fft(n) || n == 192 || n == 256 || n == 384; }
 bool pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
 
 int slot_of_rt(int N, int k) {
@@ -122,6 +124,9 @@ int slot_of_rt(int N, int k) {
     case 64: return pmfft::slot_of<64>(k);
     case 96: return pmfft::slot_of<96>(k);
     case 128: return pmfft::slot_of<128>(k);
+    case 192: return pmfft::slot_of<192>(k);
+    case 256: return pmfft::slot_of<256>(k);
+    case 384: return pmfft::slot_of<384>(k);
   }
   return k;
 }
@@ -385,7 +390,7 @@ int pm_init(const pm_config_t* cfg, pm_handle_t** out) {
     if (c.coarse_ratio != c.cmp_ratio) return bad("two-level mode needs coarse_ratio == cmp_ratio");
     if (c.n_fine % c.coarse_ratio) return bad("coarse_ratio must divide n_fine");
     g.nc = c.n_fine / c.coarse_ratio;
-    if (!supported_fft(g.nc)) return bad("coarse mesh edge must be 16, 32, 48, 64, 96 or 128");
+    if (!supported_coarse(g.nc)) return bad("coarse mesh edge must be 16, 32, 48, 64, 96, 128, 192, 256 or 384");
     g.t = c.tile;
     g.b = c.buffer;
     g.T = c.tile + 2 * c.buffer;

@@ -1,8 +1,9 @@
 // Shared-memory batched FFTs for the PM solve (paper Sec. 2.1, Eqs. 2-3;
 // the per-tile "Fourier_transforms" stage of Fig. 2).
 //
-// A length-N transform (N = N1 * N2, N in {16, 32, 48, 64, 96, 128}) is done
-// as two register passes with one shared-memory exchange (four-step):
+// A length-N transform (N = N1 * N2, N in {16, 32, 48, 64, 96, 128, 192, 256,
+// 384}) is done as two register passes with one shared-memory exchange
+// (four-step):
 //   forward, natural in -> "slot" out:
 //     step 1, item (seq, j2): N1-point DFT over x[N2 j1 + j2], times W_N^(j2 k1),
 //             written back to the same slots N2 k1 + j2;
@@ -73,7 +74,7 @@ struct TwApply {
   }
 };
 
-// In-register DFT of size R in {1, 2, 3, 4, 6, 8, 12, 16}, direction DIR (-1 forward, +1 inverse).
+// In-register DFT of size R in {1, 2, 3, 4, 6, 8, 12, 16, 24}, direction DIR (-1 forward, +1 inverse).
 template <int R, int DIR> struct Dft {
   static __device__ __forceinline__ void run(float2 (&a)[R]) {
     constexpr int P = SmallestFactor<R>::value;
@@ -132,6 +133,10 @@ template <> struct Factor<64> { static constexpr int N1 = 8, N2 = 8; };
 #endif
 template <> struct Factor<96> { static constexpr int N1 = PM_FFT96_N1, N2 = 96 / PM_FFT96_N1; };
 template <> struct Factor<128> { static constexpr int N1 = 8, N2 = 16; };
+// large periodic meshes (row / column passes, solve.cu)
+template <> struct Factor<192> { static constexpr int N1 = 16, N2 = 12; };
+template <> struct Factor<256> { static constexpr int N1 = 16, N2 = 16; };
+template <> struct Factor<384> { static constexpr int N1 = 16, N2 = 24; };
 
 template <int N> __host__ __device__ constexpr int slot_of(int k) {
   return Factor<N>::N2 * (k % Factor<N>::N1) + k / Factor<N>::N1;

@@ -170,17 +170,19 @@ constexpr auto solve_a_kernel() {
   else return k_solve_a<N, FIXED>;
 }
 
-// Pass B works on one ky row and one half of the kx columns (KC = ceil(NH/2)
-// columns, the second half starting at column KC): forward z FFT, the three
+// Pass B works on one ky row and one chunk of KC kx columns (KC = ceil(NH/2),
+// i.e. two chunks, up to N = 128): forward z FFT, the three
 // kernel products i K_d F written side by side, then one batched inverse z
 // FFT over all 3 KC columns, so a block needs only a few barriers.
+// Large meshes (N > 128) take 16 columns per block, so their z columns fit.
 template <int N> struct PassB {
   static constexpr int NH = N / 2 + 1;
-  static constexpr int KC = (NH + 1) / 2;
+  static constexpr int KC = N > 128 ? 16 : (NH + 1) / 2;
+  static constexpr int nchunk = (NH + KC - 1) / KC;
 #ifndef PM_PASSB_THREADS
 #define PM_PASSB_THREADS 512
 #endif
-  static constexpr int threads = (N >= 96) ? PM_PASSB_THREADS : 256;
+  static constexpr int threads = N > 128 ? 256 : ((N >= 96) ? PM_PASSB_THREADS : 256);
   // twiddles + [z][3 KC]: the forward transform runs in the first KC columns
   static constexpr size_t smem = sizeof(float2) * (N + 3 * (size_t)N * KC);
 };
@@ -197,7 +199,7 @@ __device__ __forceinline__ void solve_b_body(const SolveArgs& a) {
   float2* F = G;
   for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = a.tw[i];
   const int ys = blockIdx.x;      // ky in slot order
-  const int half = blockIdx.y;    // which half of the kx columns
+  const int half = blockIdx.y;    // which chunk of the kx columns
   const int pb = blockIdx.z;
   const int kx0 = half * KC;
   const int ncol = (NH - kx0) < KC ? (NH - kx0) : KC;
@@ -399,6 +401,178 @@ __global__ void __launch_bounds__(SolveCfg<N>::threads_c) k_solve_c(SolveArgs a)
   }
 }
 
+// ---- Large periodic meshes (N > 128: the coarse mesh of the largest
+// two-level runs).  A z plane of N^2 complex values no longer fits in shared
+// memory, so passes A and C are each split into a row pass along x and a
+// column pass along y, in place in the spectrum buffers:
+//   AX  per (z, R rows): real-to-complex along x, two rows packed as one
+//       complex row -> spec[z][y][kx] (natural order);
+//   AY  per (z, KC columns): FFT along y -> spec[z][ky slot][kx], the layout
+//       pass B reads;
+//   B   the pass above, KC columns per block;
+//   CY  per (component, z, KC columns): inverse FFT along y -> natural y;
+//   CX  per (component, z, R rows): complex-to-real along x -> dst, with the
+//       running max |a| when asked.
+// The window is the whole mesh (one problem, origin 0).
+template <int N> struct Large {
+  static constexpr int NH = N / 2 + 1;
+  static constexpr int R = 32;      // rows per block of the x passes
+  static constexpr int KC = 16;     // columns per block of the y passes
+  static constexpr int threads = 256;
+  static constexpr int nchunk = (NH + KC - 1) / KC;
+  static constexpr size_t smem_ax = sizeof(float2) * (N + (size_t)(R / 2) * N);
+  static constexpr size_t smem_y = sizeof(float2) * (N + (size_t)N * KC);
+  static constexpr size_t smem_cx = sizeof(float2) * (N + (size_t)R * NH + (size_t)(R / 2) * N);
+};
+
+template <int N, bool FIXED>
+__global__ void __launch_bounds__(Large<N>::threads) k_large_ax(SolveArgs a) {
+  constexpr int NH = Large<N>::NH, R = Large<N>::R;
+  extern __shared__ float2 sm[];
+  float2* tw = sm;
+  float2* W = sm + N;   // R/2 packed rows of N
+  for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = a.tw[i];
+  const int y0 = blockIdx.x * R, z = blockIdx.y;
+  PM_ROWS(r, R) {
+    const int64_t rowbase = ((int64_t)z * N + y0 + r) * N;
+    float* w = reinterpret_cast<float*>(W + (r >> 1) * N) + (r & 1);
+    if (FIXED) {
+      PM_COLS(x, N) w[2 * x] = src_value<FIXED>(a.src, rowbase + x);
+    } else {
+      const float* srow = static_cast<const float*>(a.src) + rowbase;
+      PM_COLS(x, N) async_copy4(w + 2 * x, srow + x);
+    }
+  }
+  if (!FIXED) async_wait();
+  __syncthreads();
+  fft_fwd<N, R / 2, N, 1>(W, tw);
+  // unpack the two real rows of each packed row (as in pass A), natural kx order
+  float2* out = a.spec + ((size_t)z * N + y0) * NH;
+  PM_ROWS(j, R / 2) {
+    const float2* Wj = W + j * N;
+    float2* o0 = out + (size_t)(2 * j) * NH;
+    float2* o1 = o0 + NH;
+    PM_COLS(k, NH) {
+      const float2 zk = Wj[slot_of<N>(k)];
+      const float2 zm = Wj[slot_of<N>(k == 0 ? 0 : N - k)];
+      o0[k] = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
+      o1[k] = make_float2(0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));
+    }
+  }
+}
+
+// FFT along y of KC columns of plane (blockIdx.z N + blockIdx.y) of buf
+// [plane][N][NH], in place: DIR -1 natural -> slot order, +1 slot -> natural.
+template <int N, int DIR>
+__global__ void __launch_bounds__(Large<N>::threads) k_large_y(float2* buf, const float2* twg) {
+  constexpr int NH = Large<N>::NH, KC = Large<N>::KC;
+  extern __shared__ float2 sm[];
+  float2* tw = sm;
+  float2* F = sm + N;   // [y][KC]
+  for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = twg[i];
+  const int kx0 = blockIdx.x * KC;
+  const int ncol = (NH - kx0) < KC ? (NH - kx0) : KC;
+  float2* pl = buf + ((size_t)blockIdx.z * N + blockIdx.y) * N * NH + kx0;
+  for (int i = threadIdx.x; i < N * KC; i += blockDim.x) {
+    const int y = i / KC, c = i - y * KC;
+    if (c < ncol) async_copy8(F + i, pl + (size_t)y * NH + c);
+    else F[i] = make_float2(0.f, 0.f);
+  }
+  async_wait();
+  __syncthreads();
+  if (DIR < 0) fft_fwd<N, KC, 1, KC>(F, tw);
+  else fft_inv<N, KC, 1, KC>(F, tw);
+  for (int i = threadIdx.x; i < N * KC; i += blockDim.x) {
+    const int y = i / KC, c = i - y * KC;
+    if (c < ncol) pl[(size_t)y * NH + c] = F[i];
+  }
+}
+
+template <int N>
+__global__ void __launch_bounds__(Large<N>::threads) k_large_cx(SolveArgs a) {
+  constexpr int NH = Large<N>::NH, R = Large<N>::R;
+  extern __shared__ float2 sm[];
+  float2* tw = sm;
+  float2* P = sm + N;          // [R][NH], natural order
+  float2* W = P + R * NH;      // R/2 packed rows of N
+  for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = a.tw[i];
+  const int y0 = blockIdx.x * R, z = blockIdx.y, d = blockIdx.z;
+  const float2* in = a.spec3 + (((size_t)d * N + z) * N + y0) * NH;
+  for (int i = threadIdx.x; i < R * NH; i += blockDim.x) async_copy8(P + i, in + i);
+  async_wait();
+  __syncthreads();
+  PM_ROWS(j, R / 2) {
+    const float2* Pa = P + (2 * j) * NH;
+    const float2* Pb = Pa + NH;
+    float2* Wj = W + j * N;
+    PM_COLS(k, N) {
+      float2 A, B;
+      if (k <= N / 2) {
+        A = Pa[k];
+        B = Pb[k];
+      } else {
+        A = conjf2(Pa[N - k]);
+        B = conjf2(Pb[N - k]);
+      }
+      Wj[slot_of<N>(k)] = make_float2(A.x - B.y, A.y + B.x);   // A + i B
+    }
+  }
+  __syncthreads();
+  fft_inv_rows<N, N>(W, R / 2, tw);
+  float* dst = a.dst + (size_t)d * N * N * N + ((size_t)z * N + y0) * N;
+  float m = 0.f;
+  PM_ROWS(yl, R) {
+    const float* w = reinterpret_cast<const float*>(W + (yl >> 1) * N) + (yl & 1);
+    float* drow = dst + (size_t)yl * N;
+    PM_COLS(x, N) {
+      const float val = w[2 * x];
+      m = fmaxf(m, fabsf(val));
+      drow[x] = val;
+    }
+  }
+  if (a.amax) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0 && m > __uint_as_float(*(volatile unsigned int*)a.amax))
+      atomicMax(a.amax, __float_as_uint(m));
+  }
+}
+
+template <int N>
+static cudaError_t solve_large_n(const SolvePlan& p, const void* src, bool fixed, float* dst, cudaStream_t st,
+                                 Timer* tm, unsigned int* amax) {
+  using L = Large<N>;
+  if (p.nts != 1 || p.b != 0 || p.t != N || p.src_n != N) return cudaErrorInvalidValue;
+  static bool attr_done = false;
+  if (!attr_done) {
+    cudaFuncSetAttribute(k_large_ax<N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::smem_ax);
+    cudaFuncSetAttribute(k_large_ax<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::smem_ax);
+    cudaFuncSetAttribute(k_large_y<N, -1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::smem_y);
+    cudaFuncSetAttribute(k_large_y<N, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::smem_y);
+    cudaFuncSetAttribute(solve_b_kernel<N>(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PassB<N>::smem);
+    cudaFuncSetAttribute(k_large_cx<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::smem_cx);
+    attr_done = true;
+  }
+  SolveArgs a{src, fixed ? 1 : 0, N, 1, N, 0, 0, p.spec, p.spec3, p.kern, p.tw, dst, 0, amax, nullptr, 0, 1};
+  {
+    TimedScope ts(tm, "fft_a_mesh", st);
+    if (fixed) k_large_ax<N, true><<<dim3(N / L::R, N), L::threads, L::smem_ax, st>>>(a);
+    else k_large_ax<N, false><<<dim3(N / L::R, N), L::threads, L::smem_ax, st>>>(a);
+    k_large_y<N, -1><<<dim3(L::nchunk, N, 1), L::threads, L::smem_y, st>>>(p.spec, p.tw);
+  }
+  {
+    TimedScope ts(tm, "fft_b_mesh", st);
+    solve_b_kernel<N>()<<<dim3(N, PassB<N>::nchunk, 1), PassB<N>::threads, PassB<N>::smem, st>>>(a);
+  }
+  {
+    TimedScope ts(tm, "fft_c_mesh", st);
+    k_large_y<N, 1><<<dim3(L::nchunk, N, 3), L::threads, L::smem_y, st>>>(p.spec3, p.tw);
+    k_large_cx<N><<<dim3(N / L::R, N, 3), L::threads, L::smem_cx, st>>>(a);
+  }
+  note_launches(5);
+  return cudaGetLastError();
+}
+
 template <int N>
 __global__ void k_tile_window(const float* src, int src_n, int nts, int t, int b, int64_t tile, float* out) {
   int px = (int)(tile % nts), py = (int)((tile / nts) % nts), pz = (int)(tile / ((int64_t)nts * nts));
@@ -435,7 +609,7 @@ static cudaError_t solve_n(const SolvePlan& p, const void* src, bool fixed, floa
     }
     {
       TimedScope ts(tm, N == p.src_n && p.b == 0 ? "fft_b_mesh" : "fft_b_tiles", st);
-      solve_b_kernel<N>()<<<dim3(N, 2, nb), PassB<N>::threads, PassB<N>::smem, st>>>(a);
+      solve_b_kernel<N>()<<<dim3(N, PassB<N>::nchunk, nb), PassB<N>::threads, PassB<N>::smem, st>>>(a);
     }
     if (pro && pro->ready && p0 == 0) {
       cudaError_t e = cudaStreamWaitEvent(st, pro->ready, 0);   // the coarse force must be complete
@@ -462,6 +636,9 @@ cudaError_t solve_launch(const SolvePlan& p, const void* src, bool fixed, float*
     case 64: return solve_n<64>(p, src, fixed, dst, st, tm, amax, pro);
     case 96: return solve_n<96>(p, src, fixed, dst, st, tm, amax, pro);
     case 128: return solve_n<128>(p, src, fixed, dst, st, tm, amax, pro);
+    case 192: return pro ? cudaErrorInvalidValue : solve_large_n<192>(p, src, fixed, dst, st, tm, amax);
+    case 256: return pro ? cudaErrorInvalidValue : solve_large_n<256>(p, src, fixed, dst, st, tm, amax);
+    case 384: return pro ? cudaErrorInvalidValue : solve_large_n<384>(p, src, fixed, dst, st, tm, amax);
     default: return cudaErrorInvalidValue;
   }
 }

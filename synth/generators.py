@@ -168,6 +168,9 @@ WORKLOADS = {
     # 128^3 single mesh; 64^3 Zel'dovich CDM + 128^3 nu (differentiable runs).
     "diff128": dict(n_fine=128, coarse_ratio=1, tile=128, buffer=0, cdm="zeldovich", n_cdm=64, n_nu=128,
                     vel_bits=16, r_cut=0.0, seed=1615),
+    # 768^3 fine mesh (192^3 coarse: the row / column coarse transforms), 1728 tiles; 96^3 + 192^3.
+    "two_level768": dict(n_fine=768, coarse_ratio=4, tile=64, buffer=16, cdm="zeldovich", n_cdm=96,
+                         n_nu=192, vel_bits=16, r_cut=14.0, seed=1618),
     # Small two-level cases that the oracle finishes in seconds.
     "two_level64": dict(n_fine=64, coarse_ratio=4, tile=16, buffer=8, cdm="zeldovich", n_cdm=16, n_nu=32,
                         vel_bits=16, r_cut=6.0, seed=1616),

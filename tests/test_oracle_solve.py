@@ -34,6 +34,44 @@ def test_plane_wave_closed_form(n, h, m_vec, r_s):
         np.testing.assert_allclose(a[d], amp * k[d] / kk * np.sin(phase), atol=1e-12 * abs(amp) + 1e-14)
 
 
+def test_dft_mode_matches_definition_and_transform():
+    rng = np.random.default_rng(4)
+    n = 12
+    F = rng.standard_normal((n, n, n))
+    full = offt.fft3(F)
+    z, y, x = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    for m in [(0, 0, 0), (1, 0, 0), (2, 5, 7), (6, 6, 1), (11, 3, 6)]:
+        got = solve.dft_mode(F, m)
+        brute = np.sum(F * np.exp(-2j * np.pi * (m[0] * x + m[1] * y + m[2] * z) / n))
+        assert abs(got - brute) <= 1e-10 * np.abs(F).sum()
+        assert abs(got - full[m[2], m[1], m[0]]) <= 1e-10 * np.abs(F).sum()
+
+
+@pytest.mark.parametrize("r_s", [0.0, 1.7])
+def test_accel_mode_matches_full_solve(r_s):
+    rng = np.random.default_rng(5)
+    n, h = 16, 4.0
+    M = rng.standard_normal((n, n, n))
+    a = solve.accel_periodic(M, h, G, r_s)
+    scale = np.abs(a).sum()     # bounds every DFT coefficient of a
+    for m in [(1, 0, 0), (0, 2, 3), (8, 1, 2), (5, 8, 8), (15, 9, 4), (0, 0, 0)]:
+        got = solve.accel_mode(M, h, G, r_s, m)
+        ref = np.array([solve.dft_mode(a[d], m) for d in range(3)])
+        assert np.all(np.abs(got - ref) <= 1e-12 * scale), (m, got, ref)
+        assert np.abs(ref).max() > 1e-6 * scale or m == (0, 0, 0) or r_s > 0
+
+
+def test_accel_mode_plane_wave():
+    # M = A h^3 cos(k.x): DFT[M](m) = n^3 A h^3 / 2, so a_d(m) = n^3 i k_d g(k) n^3 A h^3 / 2
+    n, h, A, r_s = 16, 4.0, 0.7, 2.5
+    m = (3, 1, 2)
+    k, _, M = _plane_wave_mesh(n, h, m, A)
+    kk2 = float(np.sum(k * k))
+    g = 4 * np.pi * G * math.exp(-kk2 * r_s * r_s) / (kk2 * (n * h) ** 3)
+    expect = n ** 3 * 1j * k * g * (n ** 3 * A * h ** 3 / 2)
+    np.testing.assert_allclose(solve.accel_mode(M, h, G, r_s, m), expect, rtol=1e-10)
+
+
 def test_gaussian_split_identity():
     # 1 - S(r) is the mass fraction of a Gaussian cloud of variance 2 r_s^2 per axis
     # (the real-space image of exp(-k^2 r_s^2)) inside radius r.
