@@ -8,6 +8,7 @@ One step = decompress + deposit, coarse and tile solves, interpolate + kick
 + drift + recompress of both species (pm_step), codes -> codes.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+  python bench.py --workload largest1536 --tuning JSON   # 1536^3, 4.08e9 particles
 
 Under torchrun each rank runs an independent replica of the workload (the
 path shards by independent problems; no data-path collective): value is the
