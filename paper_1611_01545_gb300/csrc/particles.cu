@@ -778,6 +778,23 @@ __device__ __forceinline__ bool run_reduce(unsigned key, T (&v)[K]) {
   return tail;
 }
 
+// Compile-time cell-block shape: RX_ > 0 fixes RX, RY, RZ and the fine cells per
+// compression cell (the shapes the autotuner picks on the benchmark meshes), so
+// the staged region's strides and the row search are constants; 0 reads them
+// from the arguments.
+#ifndef PM_SHAPE_INSTANCES
+#define PM_SHAPE_INSTANCES 1
+#endif
+template <int RX_, int RY_, int RZ_, int R_>
+__device__ __forceinline__ void fix_shape(Geo& g, Blk& bk) {
+  if (RX_ > 0) {
+    bk.RX = RX_;
+    bk.RY = RY_;
+    bk.RZ = RZ_;
+    g.rcmp = R_;
+  }
+}
+
 // Mass of each CIC corner: float mode m w_x w_y w_z in float32; fixed mode
 // the conservative integer split of the fixed-point deposit (2^-32 units).
 __device__ __forceinline__ void corner_masses(float m, long long, const float w1[3], float out[8]) {
@@ -816,10 +833,13 @@ __device__ __forceinline__ void corner_masses(float, long long M, const float w1
 #else
 #define PM_DEPOSIT_BOUNDS
 #endif
-template <typename Acc>
-__global__ void PM_DEPOSIT_BOUNDS k_deposit_codes(PCodes c0, PCodes c1, const int64_t* off0, const int64_t* off1, Geo g, Blk bk,
+template <typename Acc, int RX_, int RY_, int RZ_, int R_>
+__global__ void PM_DEPOSIT_BOUNDS k_deposit_codes(PCodes c0, PCodes c1, const int64_t* off0, const int64_t* off1, Geo g_arg, Blk bk_arg,
                                 float m0, float m1, long long M0, long long M1, Acc* rho_c, Acc* rho_f) {
   extern __shared__ __align__(16) unsigned char smraw[];
+  Geo g = g_arg;
+  Blk bk = bk_arg;
+  fix_shape<RX_, RY_, RZ_, R_>(g, bk);
   for_each_block(bk, [&](const int bid) {
     const int r = g.rcmp;
     const int fx = bk.RX * r + 1, fy = bk.RY * r + 1, fz = bk.RZ * r + 1;
@@ -1070,11 +1090,15 @@ __device__ __forceinline__ uint32_t window_x(const Geo& g, const Win& w, int lx)
 #define PM_SCATTER_MIN_BLOCKS 5
 #endif
 
-__global__ void __launch_bounds__(PM_IKD_THREADS, PM_IKD_MIN_BLOCKS) k_ikd_count(PCodes c0, PCodes c1, const int64_t* off0, const int64_t* off1, Geo g, Blk bk,
+template <int RX_, int RY_, int RZ_, int R_>
+__global__ void __launch_bounds__(PM_IKD_THREADS, PM_IKD_MIN_BLOCKS) k_ikd_count(PCodes c0, PCodes c1, const int64_t* off0, const int64_t* off1, Geo g_arg, Blk bk_arg,
                             const float* acc_c, const float* acc_f, float ck, float cd, uint32_t* counts0,
                             uint32_t* counts1, uint32_t* vmax_bits, uint32_t* tkey, uint4* tpv,
                             const float* vq0, const float* vq1, const float4* app, int coarse) {
   extern __shared__ __align__(16) unsigned char smraw[];
+  Geo g = g_arg;
+  Blk bk = bk_arg;
+  fix_shape<RX_, RY_, RZ_, R_>(g, bk);
   // coarse: gather the coarse force separately (0 when the fine force mesh
   // already carries the prolongated coarse force)
   const bool two_c = g.two && coarse != 0;
@@ -1237,11 +1261,15 @@ __global__ void __launch_bounds__(PM_IKD_THREADS, PM_IKD_MIN_BLOCKS) k_ikd_count
 // counted down to zero); phase 3 hands out slots from those ranges with
 // shared-memory atomics (far movers take single global slots), quantises the
 // velocity with the new v_max and writes the codes.
-__global__ void __launch_bounds__(PM_SCATTER_THREADS, PM_SCATTER_MIN_BLOCKS) k_ikd_scatter(int64_t n0, int64_t n1, const int64_t* off0, const int64_t* off1, Geo g, Blk bk,
+template <int RX_, int RY_, int RZ_, int R_>
+__global__ void __launch_bounds__(PM_SCATTER_THREADS, PM_SCATTER_MIN_BLOCKS) k_ikd_scatter(int64_t n0, int64_t n1, const int64_t* off0, const int64_t* off1, Geo g_arg, Blk bk_arg,
                               uint32_t* counts0, uint32_t* counts1, const int64_t* newoff0, const int64_t* newoff1,
                               PCodesOut o0, PCodesOut o1, const uint32_t* tkey, const uint4* tpv, int coded,
                               int* status) {
   extern __shared__ __align__(16) unsigned char smraw[];
+  Geo g = g_arg;
+  Blk bk = bk_arg;
+  fix_shape<RX_, RY_, RZ_, R_>(g, bk);
   for_each_block(bk, [&](const int bid) {
     const int nrow = bk.RY * bk.RZ;
     const CellBlock cb = block_of(bk, bid);
@@ -1483,16 +1511,18 @@ cudaError_t launch_deposit_codes(const PCodes& c0, const PCodes& c1, const int64
                                  void* rho_c, void* rho_f, bool fixed, cudaStream_t st) {
   size_t smem = deposit_codes_smem(g, bk, fixed);
   int nblk = bk.nbx * bk.nby * bk.nbz;
+  const bool tuned = PM_SHAPE_INSTANCES && bk.RX == 32 && bk.RY == 2 && bk.RZ == 1 && g.rcmp == 4;
   if (fixed) {
-    cudaFuncSetAttribute(k_deposit_codes<long long>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    nblk = block_grid(k_deposit_codes<long long>, bk, PM_DEPOSIT_THREADS, smem);
-    k_deposit_codes<long long><<<nblk, PM_DEPOSIT_THREADS, smem, st>>>(c0, c1, off0, off1, g, bk, m0, m1, M0, M1,
+    cudaFuncSetAttribute(k_deposit_codes<long long, 0, 0, 0, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    nblk = block_grid(k_deposit_codes<long long, 0, 0, 0, 0>, bk, PM_DEPOSIT_THREADS, smem);
+    k_deposit_codes<long long, 0, 0, 0, 0><<<nblk, PM_DEPOSIT_THREADS, smem, st>>>(c0, c1, off0, off1, g, bk, m0, m1, M0, M1,
                                                        static_cast<long long*>(rho_c), static_cast<long long*>(rho_f));
   } else {
-    cudaFuncSetAttribute(k_deposit_codes<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    nblk = block_grid(k_deposit_codes<float>, bk, PM_DEPOSIT_THREADS, smem);
-    k_deposit_codes<float><<<nblk, PM_DEPOSIT_THREADS, smem, st>>>(c0, c1, off0, off1, g, bk, m0, m1, M0, M1,
-                                                   static_cast<float*>(rho_c), static_cast<float*>(rho_f));
+    const auto k = tuned ? k_deposit_codes<float, 32, 2, 1, 4> : k_deposit_codes<float, 0, 0, 0, 0>;
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    nblk = block_grid(k, bk, PM_DEPOSIT_THREADS, smem);
+    k<<<nblk, PM_DEPOSIT_THREADS, smem, st>>>(c0, c1, off0, off1, g, bk, m0, m1, M0, M1, static_cast<float*>(rho_c),
+                                              static_cast<float*>(rho_f));
   }
   note_launches(1);
   return cudaGetLastError();
@@ -1504,9 +1534,11 @@ cudaError_t launch_ikd_count(const PCodes& c0, const PCodes& c1, const int64_t* 
                              uint4* tpv, const float* vq0, const float* vq1, const float4* app, bool coarse, cudaStream_t st) {
   size_t smem = ikd_count_smem(g, bk);
   int nblk = bk.nbx * bk.nby * bk.nbz;
-  cudaFuncSetAttribute(k_ikd_count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  nblk = block_grid(k_ikd_count, bk, PM_IKD_THREADS, smem);
-  k_ikd_count<<<nblk, PM_IKD_THREADS, smem, st>>>(c0, c1, off0, off1, g, bk, acc_c, acc_f, ck, cd, counts0, counts1, vmax_bits,
+  const bool tuned = PM_SHAPE_INSTANCES && bk.RX == 64 && bk.RY == 1 && bk.RZ == 1 && g.rcmp == 4;
+  const auto k = tuned ? k_ikd_count<64, 1, 1, 4> : k_ikd_count<0, 0, 0, 0>;
+  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  nblk = block_grid(k, bk, PM_IKD_THREADS, smem);
+  k<<<nblk, PM_IKD_THREADS, smem, st>>>(c0, c1, off0, off1, g, bk, acc_c, acc_f, ck, cd, counts0, counts1, vmax_bits,
                                        tkey, tpv, vq0, vq1, app, coarse ? 1 : 0);
   note_launches(1);
   return cudaGetLastError();
@@ -1518,9 +1550,11 @@ cudaError_t launch_ikd_scatter(int64_t n0, int64_t n1, const int64_t* off0, cons
                                const uint4* tpv, bool coded, int* status, cudaStream_t st) {
   size_t smem = ikd_scatter_smem(g, bk);
   int nblk = bk.nbx * bk.nby * bk.nbz;
-  cudaFuncSetAttribute(k_ikd_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  nblk = block_grid(k_ikd_scatter, bk, PM_SCATTER_THREADS, smem);
-  k_ikd_scatter<<<nblk, PM_SCATTER_THREADS, smem, st>>>(n0, n1, off0, off1, g, bk, counts0, counts1, newoff0, newoff1, o0, o1, tkey,
+  const bool tuned = PM_SHAPE_INSTANCES && bk.RX == 64 && bk.RY == 1 && bk.RZ == 1 && g.rcmp == 4;
+  const auto k = tuned ? k_ikd_scatter<64, 1, 1, 4> : k_ikd_scatter<0, 0, 0, 0>;
+  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  nblk = block_grid(k, bk, PM_SCATTER_THREADS, smem);
+  k<<<nblk, PM_SCATTER_THREADS, smem, st>>>(n0, n1, off0, off1, g, bk, counts0, counts1, newoff0, newoff1, o0, o1, tkey,
                                          tpv, coded ? 1 : 0, status);
   note_launches(1);
   return cudaGetLastError();
