@@ -140,6 +140,26 @@ def algorithmic_bytes(cfg, counts, vel_bits):
     }
 
 
+def step_model_bytes(cfg, counts, vel_bits):
+    """Whole-step byte model of the method (per step): 3 B of position codes
+    read by the deposit plus the codes read and written by the update (15 B
+    per particle with 8-bit velocities, 21 B with 16-bit); 40 B per cell of
+    every buffered tile and of the coarse mesh (density write + read,
+    spectrum write + read, force write + read); the kernels read once (2 B per
+    coarse cell, 3 x 4 x T^2 (T/2 + 1) B for the tile kernel)."""
+    nf, t, b = cfg["n_fine"], cfg["tile"], cfg["buffer"]
+    T = t + 2 * b
+    per_particle = 3 + 2 * (3 + 3 * (2 if vel_bits == 16 else 1))
+    if cfg.get("coarse_ratio", 1) > 1:
+        nc = nf // cfg["coarse_ratio"]
+        cells = (nf // t) ** 3 * T ** 3 + nc ** 3
+        kernels = 2 * nc ** 3 + 3 * 4 * T * T * (T // 2 + 1)
+    else:
+        cells = nf ** 3
+        kernels = 3 * 4 * nf * nf * (nf // 2 + 1)
+    return sum(counts) * per_particle + 40 * cells + kernels
+
+
 def csrc_digest():
     """Digest of the CUDA sources; ncu traffic figures apply only to the sources they were taken on."""
     import glob
@@ -497,6 +517,10 @@ def run_gb300(args):
                     "traffic": recorded_traffic(dom),
                     "alg_bytes_per_launch": alg[dom], "avg_launch_ms": round(avg_ms, 5)}
     step_ms = ms_max / args.steps
+    model = step_model_bytes(cfg, counts, w.vel_bits)
+    step_roofline = {"bound": "hbm", "bytes_per_step": model, "achieved": round(model / (step_ms / 1e3) / 1e9, 1),
+                     "peak": hbm, "unit": "GB/s", "frac": round(model / (step_ms / 1e3) / 1e9 / hbm, 4),
+                     "model": "whole step: 15 or 21 B per particle + 40 B per tile and coarse cell + kernels"}
     result = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
@@ -513,6 +537,7 @@ def run_gb300(args):
                            "host_form": "padded in-memory words (pm_step_host)"}},
         "gpu_launches": int(launches),
         "roofline": roofline,
+        "step_roofline": step_roofline,
         "tuning": tuning,
         "launch_forms": {"graph_ms_per_step": round(ms_max / args.steps, 5),
                          "direct_ms_per_step": round(direct_ms, 5),

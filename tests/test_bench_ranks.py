@@ -45,3 +45,17 @@ def test_job_rate_is_max_over_ranks():
 def test_job_rate_single_rank():
     import bench
     assert bench.job_rate(0.25, 100, 1) == (400.0, 0.25)
+
+
+def test_step_byte_model():
+    """The whole-step byte model: 15 B per particle (8-bit velocities) + 40 B per
+    cell of 64 tiles of 96^3 and of the 64^3 coarse mesh + kernels = 2.56 GB on
+    the 256^3 workload; 21 B per particle with 16-bit velocities."""
+    import bench
+    cfg = dict(n_fine=256, coarse_ratio=4, tile=64, buffer=16)
+    n = (128 ** 3, 256 ** 3)
+    cells = 64 * 96 ** 3 + 64 ** 3
+    kernels = 2 * 64 ** 3 + 3 * 4 * 96 * 96 * 49
+    assert bench.step_model_bytes(cfg, n, 8) == sum(n) * 15 + 40 * cells + kernels
+    assert bench.step_model_bytes(cfg, n, 16) == sum(n) * 21 + 40 * cells + kernels
+    assert abs(bench.step_model_bytes(cfg, n, 8) / 1e9 - 2.56) < 0.01
