@@ -4,10 +4,12 @@ forward step and its reverse mode (single periodic mesh).
 The loss is L = sum_c (rho_K(c) - target(c))^2 of the density after K steps,
 the variable the initial CDM displacement field psi (x0 = q + psi wrapped
 into the box, v0 = beta psi); neutrinos start from fixed phase-space
-positions.  The forward pass keeps the state every `every` steps; the
-backward pass recomputes each segment from its checkpoint up to the
-positions before its last step (the fixed-point deposit makes the
-recompute bit-identical) and runs pm_step_adjoint in reverse.  All mesh and particle arithmetic runs in libpm's kernels; torch
+positions.  The forward pass keeps the state every `every` steps, and with
+it the force mesh of the segment's last step; the backward pass recomputes
+each segment from its checkpoint up to the positions before its last step
+(the fixed-point deposit makes the recompute bit-identical), keeping the
+recomputed steps' force meshes, and runs the reverse steps with those
+meshes.  All mesh and particle arithmetic runs in libpm's kernels; torch
 supplies memory and the loss's elementwise terms.
 """
 from __future__ import annotations
@@ -40,8 +42,10 @@ class PMTrajectoryLoss(torch.autograd.Function):
         checkpoints = []
         for k in range(steps):
             if k % every == 0:
-                checkpoints.append((k, [t.clone() for t in x], [t.clone() for t in v]))
-            pm.step_plain(x, v, c_kick, c_drift, fixed=True)
+                checkpoints.append([k, [t.clone() for t in x], [t.clone() for t in v], None])
+            acc = pm.step_plain(x, v, c_kick, c_drift, fixed=True)
+            if k % every == every - 1 or k == steps - 1:
+                checkpoints[-1][3] = acc     # the force mesh of the segment's last step
         rho = final_density(pm, x)
         diff = rho - target.to(torch.float64)
         ctx.pm, ctx.beta, ctx.steps, ctx.every = pm, beta, steps, every
@@ -60,13 +64,13 @@ class PMTrajectoryLoss(torch.autograd.Function):
         for s, xk in enumerate((xK0, xK1)):
             pm.deposit_adjoint(s, xk, lam_rho, lam_x[s])
         for idx in range(len(ctx.checkpoints) - 1, -1, -1):
-            k0, x0, v0 = ctx.checkpoints[idx]
+            k0, x0, v0, acc_last = ctx.checkpoints[idx]
             k1 = ctx.checkpoints[idx + 1][0] if idx + 1 < len(ctx.checkpoints) else ctx.steps
             # pre-step positions of steps k0 .. k1-1: the checkpoint and k1-k0-1
             # recomputed steps (the segment's last step is never re-run: its
-            # adjoint needs only the positions before it).  A recomputed step
-            # keeps its acceleration mesh for its reverse step; the last one's
-            # is recomputed by pm_step_adjoint.
+            # adjoint needs only the positions before it, and its force mesh
+            # was kept by the forward pass).  A recomputed step keeps its force
+            # mesh for its reverse step, so no reverse step recomputes one.
             pre = [[x0, None]]
             if k1 - k0 > 1:
                 x = [t.clone() for t in x0]
@@ -74,6 +78,7 @@ class PMTrajectoryLoss(torch.autograd.Function):
                 for _ in range(k0, k1 - 1):
                     pre[-1][1] = pm.step_plain(x, v, ctx.ck, ctx.cd, fixed=True)
                     pre.append([[t.clone() for t in x], None])
+            pre[-1][1] = acc_last
             for xs, acc in reversed(pre):
                 pm.step_adjoint(xs, lam_x, lam_v, ctx.ck, ctx.cd, acc_fine=acc)
         grad = lam_x[0] + ctx.beta * lam_v[0]
