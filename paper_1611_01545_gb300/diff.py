@@ -52,7 +52,7 @@ class PMTrajectoryLoss(torch.autograd.Function):
         ctx.ck, ctx.cd = c_kick, c_drift
         ctx.checkpoints = checkpoints
         ctx.save_for_backward(diff.to(torch.float32), x[0], x[1])
-        return torch.sum(diff * diff).to(psi.dtype)
+        return torch.sum(diff * diff)     # float64: a sum of many squares
 
     @staticmethod
     def backward(ctx, gout):
@@ -86,6 +86,7 @@ class PMTrajectoryLoss(torch.autograd.Function):
 
 
 def trajectory_loss(pm: PM, psi, q, x_nu, v_nu, target, beta=0.0, steps=10, every=2, c_kick=1.0, c_drift=1.0):
-    """L(psi) = sum (rho_K - target)^2 after `steps` PM steps; differentiable in psi."""
+    """L(psi) = sum (rho_K - target)^2 after `steps` PM steps (a float64 scalar);
+    differentiable in psi."""
     return PMTrajectoryLoss.apply(psi, pm, q, x_nu, v_nu, target, float(beta), int(steps), int(every),
                                   float(c_kick), float(c_drift))

@@ -117,3 +117,40 @@ def test_trajectory_gradient_matches_oracle(beta, every):
     assert abs(float(L.detach()) - ref_loss) <= 1e-4 * ref_loss
     ref_grad = lx[0] + beta * lv[0]
     assert rel_rms(psi_t.grad.cpu().numpy(), ref_grad) < ADJ_TOL
+
+
+def test_trajectory_gradient_matches_central_differences_gpu():
+    """The GPU gradient against central differences of the GPU forward pass
+    itself (eps = 1e-3 cells along random directions; the fixed-point deposit
+    makes the forward deterministic, float32 positions and the CIC kinks limit
+    the agreement to about a percent)."""
+    from paper_1611_01545_gb300.diff import trajectory_loss
+    w = make_workload("diff128", n_cdm=8, n_nu=16)
+    n = 32
+    w.x = [np.mod(x * (n / 128.0), n).astype(np.float32) for x in w.x]
+    cfg = _cfg(n, counts=(8 ** 3, 16 ** 3))
+    pm = _pm(cfg)
+    rng = np.random.default_rng(11)
+    q = torch.from_numpy(w.x[0]).cuda()
+    psi = torch.from_numpy((rng.standard_normal(w.x[0].shape) * 0.3).astype(np.float32)).cuda()
+    xnu = torch.from_numpy(w.x[1]).cuda()
+    vnu = torch.from_numpy((w.v[1] * 0.2).astype(np.float32)).cuda()
+    target = torch.from_numpy((rng.random((n, n, n)) * 0.02).astype(np.float32)).cuda()
+    args = (q, xnu, vnu, target, 0.3, 4, 2, 0.5, 0.5)
+    p = psi.clone().requires_grad_(True)
+    trajectory_loss(pm, p, *args).backward()
+    g = p.grad.double()
+    eps = 1e-3
+    # along the gradient itself, then along random directions, whose directional
+    # derivative sums terms of both signs: the tolerance scales with sum |g_i d_i|
+    dirs = [p.grad.detach().clone()] + [torch.from_numpy(rng.standard_normal(w.x[0].shape).astype(np.float32)).cuda()
+                                        for _ in range(2)]
+    for k, d in enumerate(dirs):
+        d /= d.abs().max()        # every coordinate moves by up to eps: far above float32 rounding
+        lp = float(trajectory_loss(pm, psi + eps * d, *args).detach())
+        lm = float(trajectory_loss(pm, psi - eps * d, *args).detach())
+        fd = (lp - lm) / (2 * eps)
+        an = float((g * d.double()).sum())
+        scale = float((g * d.double()).abs().sum())
+        assert abs(fd - an) <= 2e-2 * scale, (k, fd, an, scale)
+    pm.check()
