@@ -125,18 +125,3 @@ def accel_tile(rho_tile: np.ndarray, K: np.ndarray) -> np.ndarray:
     for d in range(3):
         out[d] = fft3(fft3(K[d]) * rk, inverse=True).real / T ** 3
     return out
-
-
-def accel_direct(x, m, G: float, n_box: float) -> np.ndarray:
-    """Newtonian pairwise acceleration (Eq. 4 without softening) by direct
-    sum over nearest periodic images.  Small N only."""
-    x = np.asarray(x, dtype=np.float64).reshape(-1, 3)
-    m = np.broadcast_to(np.asarray(m, dtype=np.float64), (x.shape[0],))
-    a = np.zeros_like(x)
-    for i in range(x.shape[0]):
-        d = x - x[i]
-        d -= n_box * np.round(d / n_box)
-        r2 = np.sum(d * d, axis=1)
-        r2[i] = np.inf
-        a[i] = G * np.sum((m / r2 ** 1.5)[:, None] * d, axis=0)
-    return a
