@@ -1,20 +1,22 @@
 """Benchmark of the fused two-species PM step (particle-steps per second).
 
-Workload (default): two-level PM, 256^3 fine mesh, coarse ratio 4 (64^3
-coarse mesh), 64 fine tiles of 64^3 interior + 16-cell buffer (96^3 FFTs),
-128^3 Zel'dovich CDM + 256^3 Fermi-Dirac neutrinos (18.9M particles),
-compressed state with 8-bit offsets and 8-bit velocities, float32 math.
-One step = decompress + deposit, coarse and tile solves, interpolate + kick
-+ drift + recompress of both species (pm_step), codes -> codes.
+Workload (default): the largest one-GPU configuration, two-level PM on a
+1536^3 fine mesh (384^3 coarse mesh, 13,824 tiles of 64^3 + 16-cell buffer,
+96^3 FFTs), 768^3 Zel'dovich CDM + 1536^3 Fermi-Dirac neutrinos (4.08e9
+particles, 16-bit velocity codes, about 37 GB of record bytes), drawn on the
+device.  One step = decompress + deposit, coarse and tile solves,
+interpolate + kick + drift + recompress of both species (pm_step), codes ->
+codes.  The 256^3 workload (128^3 + 256^3 particles, 8-bit velocity codes)
+is reported beside it under "two_level256".
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
-  python bench.py --workload largest1536 --tuning JSON   # 1536^3, 4.08e9 particles
+  python bench.py --workload two_level256        # the 256^3 workload alone
 
 Under torchrun each rank runs an independent replica of the workload (the
 path shards by independent problems; no data-path collective): value is the
 particle-steps of all ranks divided by the slowest rank's time.
 --impl reference times the oracle (plain float64 numpy restatement of the
-method) on a bounded sample of the same workload on the host cores.
+method) on the host cores, one bounded sample of the workload per step.
 """
 from __future__ import annotations
 
@@ -173,20 +175,29 @@ def csrc_digest():
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(kind):
-    """DRAM bytes per launch of a kernel kind from the committed ncu summary, or
-    None when the kernels changed since that capture."""
-    path = os.path.join(ROOT, "profiles", "step_kernels_two_level256_ncu.md")
+def recorded_traffic(kind, workload, particles):
+    """DRAM bytes (read + write) per launch of a kernel kind from the committed
+    ncu record (profiles/traffic.json), or None when the kernels changed since
+    that capture.  A record taken on a smaller workload of the same recipe is
+    scaled to this one by the particles processed (the particle passes move a
+    fixed number of bytes per particle plus per-cell tables that grow with
+    the mesh, i.e. in the same proportion for these workloads)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
-        lines = open(path).read().splitlines()
-    except OSError:
+        rec = json.load(open(path))
+    except (OSError, ValueError):
         return None
     digest = csrc_digest()
-    for ln in lines:
-        parts = ln.split()
-        if len(parts) == 4 and parts[0] == "traffic" and parts[1] == kind and parts[3] == f"csrc={digest}":
-            return int(parts[2])
-    return None
+    best = None
+    for e in rec.get("entries", []):
+        if e.get("kind") != kind or e.get("csrc") != digest:
+            continue
+        if e.get("workload") == workload:
+            return {"bytes": int(e["bytes_per_launch"]), "captured_on": workload, "scaled": False}
+        if e.get("scale") == "particles" and e.get("particles"):
+            best = {"bytes": int(round(e["bytes_per_launch"] * particles / e["particles"])),
+                    "captured_on": e["workload"], "scaled": True}
+    return best
 
 
 def build_state(pm, w, torch):
@@ -306,36 +317,197 @@ def plain_step_ms(pm, w, codes, spare, torch, stream, steps: int) -> float:
     return ms
 
 
+# Launch tuning of the largest workload: the shapes the autotuner picks on
+# the 256^3 workload of the same recipe (persistent 32x2x1-cell deposit
+# blocks, 64x1x1 kick blocks with a new-cell window half-width of 1), 64
+# tiles per solve batch.  The autotuner itself would spend minutes at this
+# size (each candidate is timed on whole steps).
+LARGEST_TUNING = {"deposit_block": [32, 2, 1], "deposit_persistent": 1, "kick_block": [64, 1, 1],
+                  "kick_window": 1, "kick_persistent": 0, "tile_batch": 64}
+
+
+def measured_hbm():
+    """HBM roofline denominator: the measured copy rate of this GPU pool, else the fallback figure."""
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        peaks = {}
+    hbm = peaks.get("hbm_gbs")
+    return (float(hbm), "measured") if hbm else (6800.0, "fallback")
+
+
+def kernel_roofline(stages, alg, workload, particles):
+    """Roofline of the dominant kernel kind (largest total time among the kinds
+    with an algorithmic byte model): algorithmic bytes per launch / its mean
+    CUDA-event launch duration, against the HBM copy peak."""
+    hbm, src = measured_hbm()
+    dom = None
+    for k, (avg, cnt) in stages.items():
+        if k in alg and (dom is None or avg * cnt > stages[dom][0] * stages[dom][1]):
+            dom = k
+    if dom is None:
+        return None
+    avg_ms = stages[dom][0]
+    achieved = alg[dom] / (avg_ms / 1e3) / 1e9
+    tr = recorded_traffic(dom, workload, particles)
+    return {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": hbm, "peak_source": src,
+            "unit": "GB/s", "frac": round(achieved / hbm, 4), "traffic": tr["bytes"] if tr else None,
+            "traffic_source": tr, "alg_bytes_per_launch": alg[dom], "avg_launch_ms": round(avg_ms, 5),
+            "note": f"frac of {src} HBM copy rate"}
+
+
+def step_roofline(model_bytes, step_ms):
+    hbm, src = measured_hbm()
+    gbs = model_bytes / (step_ms / 1e3) / 1e9
+    return {"bound": "hbm", "bytes_per_step": model_bytes, "achieved": round(gbs, 1), "peak": hbm,
+            "peak_source": src, "unit": "GB/s", "frac": round(gbs / hbm, 4),
+            "model": "whole step: 15 or 21 B per particle + 40 B per tile and coarse cell + kernels"}
+
+
+def host_mem_available():
+    """MemAvailable of this host in bytes (None where /proc/meminfo is absent)."""
+    try:
+        for ln in open("/proc/meminfo"):
+            if ln.startswith("MemAvailable:"):
+                return int(ln.split()[1]) * 1024
+    except OSError:
+        pass
+    return None
+
+
+def cpu_model():
+    """The host CPU's model name (lscpu), else /proc/cpuinfo's model or part field."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        for ln in open("/proc/cpuinfo"):
+            low = ln.lower()
+            if low.startswith("model name") or low.startswith("cpu part"):
+                return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def pinned_like(t, torch):
+    """An uninitialised pinned host tensor of t's shape and dtype."""
+    return torch.empty(t.shape, dtype=t.dtype, pin_memory=True)
+
+
+def to_pinned(codes, torch):
+    """Device codes copied into freshly allocated pinned host tensors."""
+    from paper_1611_01545_gb300.pm import Codes
+    f = {k: pinned_like(getattr(codes, k), torch) for k in ("cnt", "esc", "n_esc", "pos", "vel", "vmax")}
+    for k, t in f.items():
+        t.copy_(getattr(codes, k))
+    return Codes(codes.n, **f)
+
+
+def empty_pinned_packed(pm, n, esc_cap, torch):
+    from paper_1611_01545_gb300.pm import Codes
+    vdt = torch.int16 if pm.vel_bits == 16 else torch.uint8
+    ncell = pm.n_cmp ** 3
+    return Codes(n=n, cnt=torch.empty(ncell, dtype=torch.uint8, pin_memory=True),
+                 esc=torch.zeros((esc_cap, 2), dtype=torch.int32).pin_memory(),
+                 n_esc=torch.zeros(1, dtype=torch.int32).pin_memory(),
+                 pos=torch.empty((n, 3), dtype=torch.uint8, pin_memory=True),
+                 vel=torch.empty((n, 3), dtype=vdt, pin_memory=True),
+                 vmax=torch.zeros(1, dtype=torch.float32).pin_memory())
+
+
+def e2e_packed(pm, codes, spare, torch, steps, world, dist, n_total):
+    """End to end through the C ABI (pm_step_packed) with the state in pinned
+    host memory: each step copies the packed record bytes (3 B position + 3 or
+    6 B velocity codes per particle, plus counts, escapes and v_max) host ->
+    device, steps, and copies the new packed state device -> host; the first
+    call (staging allocation, graph capture) is not timed.  The device codes
+    `codes` / `spare` are released first (the library's own staging holds the
+    state during the call), so the lists are emptied."""
+    vb = 2 if pm.vel_bits == 16 else 1
+    rec = sum(c.n for c in codes) * 3 * (1 + vb)
+    avail = host_mem_available()
+    if avail is not None and avail < 2.3 * rec * world:
+        return {"value": None, "unit": UNIT, "skipped": f"host memory: {avail / 1e9:.0f} GB available, "
+                f"{2 * rec * world / 1e9:.0f} GB of pinned buffers needed"}
+    spare.clear()
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    t0 = time.perf_counter()
+    hin = []
+    for i in range(len(codes)):
+        pk = pm.pack(codes[i])
+        hin.append(to_pinned(pk, torch))
+        del pk
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+    ncodes = [(c.n, c.esc.shape[0]) for c in codes]
+    codes.clear()
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    hout = [empty_pinned_packed(pm, n, cap, torch) for n, cap in ncodes]
+    setup_s = time.perf_counter() - t0
+    pm.set_graphs(True)
+    pm.step_packed(hin, hout, 1.0, 1.0)       # allocates the library's staging, captures the graph
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        pm.step_packed(hin, hout, 1.0, 1.0)   # ends with pm_check: the step's copies are complete
+    el = time.perf_counter() - t0
+    pm.set_graphs(False)
+    value, worst = job_rate(el, n_total * steps, world, "cuda", dist)
+    nbytes = sum(codes_bytes(c, pm.vel_bits, packed=True) for c in hin)
+    return {"value": value, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
+            "steps": steps, "ms_per_step": round(worst / steps * 1e3, 3),
+            "host_form": "packed record bytes in pinned host memory (pm_step_packed)",
+            "setup_s": round(setup_s, 1)}
+
+
 def run_largest(args):
     """The largest one-GPU workload (1536^3, 4.08e9 particles): the fused step
-    replayed from a graph, then per-stage CUDA-event times.  Inputs are built
-    on the device; no host copy of the state is made, so there is no
-    end-to-end number for this workload."""
+    replayed from a graph (the headline), per-stage CUDA-event times, the
+    dominant kernel's roofline, end to end through pm_step_packed, and the
+    oracle's CPU baseline on a bounded sample."""
     import torch
+    import torch.distributed as dist
 
     from paper_1611_01545_gb300 import PM, _lib
 
     rank, world, local = dist_env()
-    if world > 1:
-        return None if rank else {"workload": "largest1536", "skipped": "one-GPU workload"}
     torch.cuda.set_device(local)
-    cfg = largest_config(args.tile_batch or 64)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    tuning = dict(LARGEST_TUNING)
+    if args.tuning:
+        tuning.update(json.loads(args.tuning))
+    if args.tile_batch:
+        tuning["tile_batch"] = args.tile_batch
+    cfg = largest_config(tuning["tile_batch"])
     cfg["vmax_mode"] = args.vmax_mode
     t0 = time.perf_counter()
     pm = PM(cfg)
     a = build_largest_codes(pm, torch)
     b = [pm.empty_codes(c.n, esc_cap=c.esc.shape[0]) for c in a]
     build_s = time.perf_counter() - t0
-    if args.tuning:
-        pm.set_tuning(json.loads(args.tuning))
+    pm.set_tuning(tuning)
     tuning = pm.get_tuning()
-    n_total = sum(c.n for c in a)
+    counts = [c.n for c in a]
+    n_total = sum(counts)
     lib = _lib.load()
     stream = torch.cuda.current_stream()
 
     def one_step():
         pm.step(a, b, 1.0, 1.0)
 
+    # headline: the step replayed from a captured CUDA graph; inputs (4.08e9
+    # particles, 49 GB of codes, 58 GB of meshes) are far larger than L2
     pm.set_graphs(True)
     for _ in range(args.warmup):
         one_step()
@@ -343,6 +515,8 @@ def run_largest(args):
     sampler = ClockSampler(local)
     sampler.start()
     time.sleep(0.3)
+    if world > 1:
+        dist.barrier()
     torch.cuda.synchronize()
     launches0 = lib.pm_launch_count()
     e0 = torch.cuda.Event(enable_timing=True)
@@ -352,28 +526,40 @@ def run_largest(args):
         one_step()
     e1.record(stream)
     torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
     launches = lib.pm_launch_count() - launches0
     sampler.stop()
     ms = e0.elapsed_time(e1)
     pm.check()
+    value, worst_s = job_rate(ms / 1e3, n_total * args.steps, world, "cuda", dist)
+    step_ms = worst_s * 1e3 / args.steps
     pm.set_graphs(False)
+    # per-stage CUDA events on the launching stream (direct launches)
     pm.set_timing(True)
-    for _ in range(max(1, min(args.steps, 3))):
+    for _ in range(2):
         one_step()
     torch.cuda.synchronize()
     pm.check()
     stages = pm.stage_times()
     pm.set_timing(False)
     free, total = torch.cuda.mem_get_info()
-    alg = algorithmic_bytes(dict(cfg, tile_batch=tuning["tile_batch"]), [c.n for c in a], cfg["vel_bits"])
+    alg = algorithmic_bytes(dict(cfg, tile_batch=tuning["tile_batch"]), counts, cfg["vel_bits"])
+    e2e = None
+    if not args.no_e2e:
+        e2e = e2e_packed(pm, a, b, torch, max(1, min(args.steps, 3)), world, dist, n_total)
     result = {
-        "metric": METRIC, "value": n_total * args.steps / (ms / 1e3), "unit": UNIT, "n_gpus": 1,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic (device-generated)",
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic (device-generated)",
         "config": {"workload": "largest1536", "n_fine": cfg["n_fine"], "coarse_ratio": 4, "tile": 64, "buffer": 16,
-                   "tile_batch": tuning["tile_batch"], "particles": {"cdm": a[0].n, "nu": a[1].n},
-                   "vel_bits": 16, "vmax_mode": args.vmax_mode, "l2": "working set > L2"},
-        "e2e": None, "gpu_launches": int(launches), "tuning": tuning,
+                   "tile_batch": tuning["tile_batch"], "particles": {"cdm": counts[0], "nu": counts[1]},
+                   "vel_bits": 16, "vmax_mode": args.vmax_mode, "global_batch": n_total * world,
+                   "parallelism": f"replicas{world}", "l2": "inputs larger than L2: 49 GB of codes, 58 GB of meshes"},
+        "e2e": e2e, "gpu_launches": int(launches),
+        "roofline": kernel_roofline(stages, alg, "largest1536", n_total),
+        "step_roofline": step_roofline(step_model_bytes(cfg, counts, cfg["vel_bits"]), step_ms),
+        "tuning": tuning,
         "stages_ms": {k: round(v[0], 4) for k, v in stages.items()},
         "stage_launches": {k: v[1] for k, v in stages.items()},
         "stage_gbs": {k: round(alg[k] / (v[0] / 1e3) / 1e9, 1) for k, v in stages.items() if k in alg},
@@ -381,24 +567,31 @@ def run_largest(args):
         "clocks": sampler.summary(),
     }
     pm.close()
-    return result
+    del a, b
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    if world > 1:
+        dist.destroy_process_group()
+    return result if rank == 0 else None
 
 
-def run_gb300(args):
+def run_workload(args, workload, adjoint=True, cpu=True):
+    """One of the smaller workloads (two_level256 and the others of
+    synth.generators): autotuned launch tuning, the graph-replayed step, the
+    direct and plain forms, per-stage times, end to end (packed and padded
+    host forms), the adjoint/forward ratio and the oracle's CPU baseline."""
     import torch
     import torch.distributed as dist
-
-    if args.workload == "largest1536":
-        return run_largest(args)
 
     from paper_1611_01545_gb300 import PM, _lib
     from synth import make_workload
 
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
-    if world > 1:
+    own_group = world > 1 and not dist.is_initialized()
+    if own_group:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    w = make_workload(args.workload, seed=None)
+    w = make_workload(workload, seed=None)
     cfg = w.config()
     cfg["tile_batch"] = args.tile_batch
     cfg["vmax_mode"] = args.vmax_mode
@@ -484,62 +677,36 @@ def run_gb300(args):
             fn(hin, hout, 1.0, 1.0)
         return time.perf_counter() - t0
 
-    pk_in = [pm.pack(c).to("cpu", pin=True) for c in a]
-    pk_out = [pm.pack(c).to("cpu", pin=True) for c in b]
+    pk_in = [to_pinned(pm.pack(c), torch) for c in a]
+    pk_out = [to_pinned(pm.pack(c), torch) for c in b]
     e2e_s = e2e_run(pm.step_packed, pk_in, pk_out)
-    pad_s = e2e_run(pm.step_host, [c.to("cpu", pin=True) for c in a], [c.to("cpu", pin=True) for c in b])
+    pad_s = e2e_run(pm.step_host, [to_pinned(c, torch) for c in a], [to_pinned(c, torch) for c in b])
     pm.set_graphs(False)
     e2e_value, _ = job_rate(e2e_s, n_total * k_e2e, world, "cuda", dist)
     pad_value, _ = job_rate(pad_s, n_total * k_e2e, world, "cuda", dist)
     h2d = sum(codes_bytes(c, w.vel_bits, packed=True) for c in a)
-    d2h = h2d
 
     alg = algorithmic_bytes(dict(cfg, tile_batch=tuning["tile_batch"]), counts, w.vel_bits)
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except (OSError, ValueError):
-        pass
-    hbm = peaks.get("hbm_gbs")
-    peak_src = "measured" if hbm else "fallback"
-    hbm = hbm or 6800.0
-    # dominant kernel: largest total time among kinds with an algorithmic byte model
-    dom = None
-    for k, (avg, cnt) in stages.items():
-        if k in alg and (dom is None or avg * cnt > stages[dom][0] * stages[dom][1]):
-            dom = k
-    roofline = None
-    if dom:
-        avg_ms = stages[dom][0]
-        achieved = alg[dom] / (avg_ms / 1e3) / 1e9
-        roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": hbm,
-                    "peak_source": peak_src, "unit": "GB/s", "frac": round(achieved / hbm, 4),
-                    "traffic": recorded_traffic(dom),
-                    "alg_bytes_per_launch": alg[dom], "avg_launch_ms": round(avg_ms, 5)}
     step_ms = ms_max / args.steps
-    model = step_model_bytes(cfg, counts, w.vel_bits)
-    step_roofline = {"bound": "hbm", "bytes_per_step": model, "achieved": round(model / (step_ms / 1e3) / 1e9, 1),
-                     "peak": hbm, "unit": "GB/s", "frac": round(model / (step_ms / 1e3) / 1e9 / hbm, 4),
-                     "model": "whole step: 15 or 21 B per particle + 40 B per tile and coarse cell + kernels"}
     result = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": args.workload, "n_fine": w.n_fine, "coarse_ratio": w.coarse_ratio,
+        "config": {"workload": workload, "n_fine": w.n_fine, "coarse_ratio": w.coarse_ratio,
                    "tile": w.tile, "buffer": w.buffer, "tile_batch": args.tile_batch,
                    "vmax_mode": args.vmax_mode, "pp": int(args.pp),
                    "particles": {"cdm": counts[0], "nu": counts[1]}, "vel_bits": w.vel_bits,
                    "global_batch": n_total * world, "parallelism": f"replicas{world}",
-                   "l2": "working set > L2 (126 MB): codes 113 MB + meshes > 400 MB per step"},
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                   "l2": "working set > L2 (126 MB): codes + meshes > 400 MB per step"},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": h2d,
                 "steps": k_e2e, "host_form": "packed record bytes (pm_step_packed)",
                 "padded": {"value": pad_value, "bytes_per_step_each_way": sum(codes_bytes(c, w.vel_bits) for c in a),
                            "host_form": "padded in-memory words (pm_step_host)"}},
         "gpu_launches": int(launches),
-        "roofline": roofline,
-        "step_roofline": step_roofline,
+        "roofline": kernel_roofline(stages, alg, workload, n_total),
+        "step_roofline": step_roofline(step_model_bytes(cfg, counts, w.vel_bits), step_ms),
         "tuning": tuning,
-        "launch_forms": {"graph_ms_per_step": round(ms_max / args.steps, 5),
+        "launch_forms": {"graph_ms_per_step": round(step_ms, 5),
                          "direct_ms_per_step": round(direct_ms, 5),
                          "plain_ms_per_step": round(plain_ms, 5),
                          "plain_value": n_total * world / (plain_ms / 1e3),
@@ -548,14 +715,37 @@ def run_gb300(args):
         "stage_launches": {k: v[1] for k, v in stages.items()},
         "clocks": sampler.summary(),
     }
-    if not args.no_adjoint:
+    if "tile_count_max" in w.notes:
+        result["config"]["tile_count"] = {"max": w.notes["tile_count_max"], "min": w.notes["tile_count_min"]}
+    if adjoint and not args.no_adjoint:
         result["adjoint"] = adjoint_ratio(args.adjoint_workload)
-    if rank == 0 and not args.no_cpu_baseline:
-        result["cpu_baseline"] = cpu_baseline(w, 1.0 / 64)
-    if world > 1:
-        dist.destroy_process_group()
     pm.close()
+    del a, b, codes, spare, pk_in, pk_out
+    torch.cuda.empty_cache()
+    if cpu and rank == 0 and not args.no_cpu_baseline:
+        result["cpu_baseline"] = cpu_baseline(workload)
+    if own_group:
+        dist.destroy_process_group()
     return result if rank == 0 else None
+
+
+def run_gb300(args):
+    if args.workload != "largest1536":
+        return run_workload(args, args.workload)
+    res = run_largest(args)
+    rank = dist_env()[0]
+    if rank == 0 and res is not None and not args.no_cpu_baseline:
+        res["cpu_baseline"] = cpu_baseline("largest1536")
+    if not args.no_extra:
+        # the 256^3 workload beside the headline (its own autotuned launch tuning)
+        small = argparse.Namespace(**vars(args))
+        small.tuning, small.tile_batch = "", 0
+        extra = run_workload(small, "two_level256", adjoint=True, cpu=False)
+        if res is not None and extra is not None:
+            keep = ("value", "ms_per_step", "e2e", "roofline", "step_roofline", "tuning", "launch_forms",
+                    "stages_ms", "adjoint", "clocks", "gpu_launches", "config")
+            res["two_level256"] = {k: extra[k] for k in keep if k in extra}
+    return res
 
 
 def adjoint_ratio(workload: str, steps: int = 10, every: int = 2, reps: int = 3):
@@ -600,91 +790,242 @@ def adjoint_ratio(workload: str, steps: int = 10, every: int = 2, reps: int = 3)
             "note": "adjoint time includes the checkpointed recompute of each segment"}
 
 
-def cpu_baseline(workload, frac: float = 1.0 / 64):
-    """Times the oracle, as it stands, on a bounded sample of the workload.
 
-    Sample: the oracle's particle stages (CIC deposit onto the coarse and the
-    fine mesh, interpolation, kick-drift, codec) on a random subset of both
-    species, one buffered fine-tile solve and the full coarse-mesh solve;
-    the full-step time is extrapolated per particle and per tile.
-    """
-    from oracle import codec, mesh, solve, step
+
+# ---------------------------------------------------------------- oracle --
+# The oracle's own stages, timed on the host cores on a bounded sample: whole
+# fine tiles of the two-level step (decompress the tile's home particles,
+# deposit them on the coarse mesh, deposit the tile's buffered window, solve
+# the tile, interpolate the fine and coarse force at the home particles,
+# kick, drift, recompress them).  Every tile of a two-level workload of this
+# recipe (64^3 interior + 16-cell buffer, one CDM particle per 8 fine cells,
+# one neutrino per fine cell) carries the same work, so the per-tile rate
+# times the tile count gives the step; the coarse solve (one per step) is
+# added from its own timing.
+
+# workload -> (realisation of the recipe the sample tiles are cut from,
+#              velocity bits, coarse mesh edge, tiles per step)
+ORACLE_SAMPLES = {
+    "largest1536": ("two_level256", 16, 384, 13824),
+    "two_level256": ("two_level256", 8, 64, 64),
+}
+
+
+def _oracle_tile_inputs(workload, n_jobs, seed=5):
+    """Per-tile inputs of the oracle sample, written to pickles in a temporary
+    directory: the tile's home particles as codes, the decoded positions of the
+    other particles of its buffered window, the tile kernel and the coarse
+    force mesh (both precomputed once per run by the oracle).  Returns
+    (paths, info)."""
+    import pickle
+    import tempfile
+
+    from oracle import codec, solve
+    from oracle import mesh as omesh
     from synth import make_workload
 
-    w = make_workload(workload) if isinstance(workload, str) else workload
-    nf, t, b = w.n_fine, w.tile, w.buffer
-    T = t + 2 * b
-    n_tiles = (nf // t) ** 3 if w.coarse_ratio > 1 else 0
-    rng = np.random.default_rng(5)
-    sub = []
-    for s in range(2):
-        n = w.x[s].shape[0]
-        idx = rng.choice(n, max(1, int(n * frac)), replace=False)
-        sub.append((w.x[s][idx], w.v[s][idx]))
+    recipe, vel_bits, nc_target, tiles_target = ORACLE_SAMPLES[workload]
+    w = make_workload(recipe)
+    n, t, b, rc = w.n_fine, w.tile, w.buffer, w.coarse_ratio
+    T, nc, ncmp = t + 2 * b, n // rc, n // w.cmp_ratio
+    nt = n // t
+    cfg = dict(w.config(), vel_bits=vel_bits)
+    K = solve.fine_kernel(T, w.G, w.r_split, w.r_cut)
+    rng = np.random.default_rng(seed)
+    picks = rng.choice(nt ** 3, size=min(n_jobs, nt ** 3), replace=False)
+    # the coarse force the tiles interpolate from: the oracle's coarse solve of
+    # the sampled tiles' home particles, timed (one coarse solve per step)
+    cells = [np.floor(x).astype(np.int32) for x in w.x]          # fine cell of every particle
+    tids = [(c[:, 0] // t) + nt * ((c[:, 1] // t) + nt * (c[:, 2] // t)) for c in cells]
+    homes = []
+    rho_c = np.zeros((nc, nc, nc))
+    for tid in picks:
+        idx = np.array([tid % nt, (tid // nt) % nt, tid // (nt * nt)])
+        hs = []
+        for s in range(2):
+            sel = tids[s] == tid
+            hs.append(sel)
+            rho_c += omesh.cic_deposit(w.x[s][sel].astype(np.float64) / rc, w.mass[s], nc)
+        homes.append((idx, hs))
     t0 = time.perf_counter()
-    nc = nf // 4
-    xs = []
-    for s, (x, v) in enumerate(sub):
-        c = codec.compress(x, v, nf, nc, w.vel_bits)
-        xd, vd = codec.decompress(c, nf)
-        xs.append((xd, vd))
-    rho_f = sum(mesh.cic_deposit(x, m, nf) for (x, _), m in zip(xs, w.mass))
-    if w.coarse_ratio > 1:
-        rho_c = sum(mesh.cic_deposit(x.astype(np.float64) / w.coarse_ratio, m, nf // w.coarse_ratio)
-                    for (x, _), m in zip(xs, w.mass))
-    zero3 = np.zeros((3,) + rho_f.shape)
-    for (x, v) in xs:
-        a = mesh.cic_interp(zero3, x, nf)
-        x1, v1 = step.kick_drift(x, v, a, 1.0, 1.0, nf)
-        codec.compress(step.to_f32_positions(x1, nf), v1.astype(np.float32), nf, nc, w.vel_bits)
-    t_particles = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    if w.coarse_ratio > 1:
-        solve.accel_periodic(rho_c, float(w.coarse_ratio), w.G, w.r_split)
-    else:
-        solve.accel_periodic(rho_f, 1.0, w.G)
+    acc_c = solve.accel_periodic(rho_c, float(rc), w.G, w.r_split)
     t_coarse = time.perf_counter() - t0
-    t_tile = 0.0
-    if n_tiles:
-        K = solve.fine_kernel(T, w.G, w.r_split, w.r_cut)
+    d = tempfile.mkdtemp(prefix="pm_oracle_sample_")
+    paths = []
+    for j, (idx, hs) in enumerate(homes):
+        origin = idx * t - b
+        job = {"cfg": cfg, "origin": origin.astype(np.float64), "K": K, "acc_c": acc_c, "home": [], "buf": []}
+        for s in range(2):
+            x, v = w.x[s], w.v[s]
+            # window membership of the tile deposit: floor((x - origin) mod n) in [0, T - 2]
+            win = np.ones(x.shape[0], dtype=bool)
+            for ax in range(3):
+                win &= ((cells[s][:, ax] - int(origin[ax])) % n) <= T - 2
+            buf = win & ~hs[s]
+            job["home"].append(codec.compress(x[hs[s]], v[hs[s]], n, ncmp, vel_bits))
+            cb = codec.compress(x[buf], v[buf], n, ncmp, vel_bits)
+            job["buf"].append(codec.decompress(cb, n)[0])
+        p = os.path.join(d, f"tile{j}.pkl")
+        with open(p, "wb") as fh:
+            pickle.dump(job, fh, protocol=pickle.HIGHEST_PROTOCOL)
+        paths.append(p)
+    # the coarse solve at the target coarse mesh: measured here at nc^3 and
+    # scaled by N^3 log N (the oracle's transforms are O(N^3 log N))
+    scale = (nc_target / nc) ** 3 * np.log(nc_target ** 3) / np.log(nc ** 3)
+    info = {"recipe": recipe, "vel_bits": vel_bits, "tiles_per_step": tiles_target, "coarse_edge": nc_target,
+            "coarse_solve_s": t_coarse * scale, "coarse_measured_edge": nc, "coarse_measured_s": t_coarse,
+            "dir": d}
+    return paths, info
+
+
+def _oracle_tile_step(path):
+    """One tile of the oracle's step (the stages listed above); returns
+    (seconds, home particles, window particles)."""
+    import pickle
+
+    from oracle import codec, solve
+    from oracle import mesh as omesh
+    from oracle import step as ostep
+
+    with open(path, "rb") as fh:
+        job = pickle.load(fh)
+    cfg = job["cfg"]
+    n, rc = cfg["n_fine"], cfg["coarse_ratio"]
+    T = cfg["tile"] + 2 * cfg["buffer"]
+    nc, ncmp = n // rc, n // cfg["cmp_ratio"]
+    origin = job["origin"]
+    t0 = time.perf_counter()
+    xv = [codec.decompress(c, n) for c in job["home"]]
+    rho_c = sum(omesh.cic_deposit(x.astype(np.float64) / rc, m, nc) for (x, _), m in zip(xv, cfg["mass"]))
+    rho = sum(omesh.tile_deposit(np.concatenate([x, xb]), m, origin, T, n)
+              for (x, _), xb, m in zip(xv, job["buf"], cfg["mass"]))
+    a_t = solve.accel_tile(rho, job["K"])
+    nh = 0
+    for x, v in xv:
+        a = omesh.tile_interp(a_t, np.mod(x.astype(np.float64) - origin, n)) + \
+            omesh.cic_interp(job["acc_c"], x.astype(np.float64) / rc, nc)
+        x1, v1 = ostep.kick_drift(x, v, a, 1.0, 1.0, n)
+        codec.compress(ostep.to_f32_positions(x1, n), v1.astype(np.float32), n, ncmp, cfg["vel_bits"])
+        nh += x.shape[0]
+    el = time.perf_counter() - t0
+    del rho_c
+    return el, nh, nh + sum(xb.shape[0] for xb in job["buf"])
+
+
+def _single_thread_env():
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[k] = "1"
+
+
+class OracleSampler:
+    """The oracle's tile sample: inputs built once, then timed on one thread
+    (in this process) or on every host core (a spawn pool, one tile per
+    worker)."""
+
+    def __init__(self, workload, n_jobs=None):
+        self.cores = os.cpu_count() or 1
+        n_jobs = n_jobs or max(2, self.cores)
+        self.paths, self.info = _oracle_tile_inputs(workload, n_jobs)
+        self.pool = None
+        self.next = 0
+
+    def one_thread(self, tiles):
+        out = []
+        for _ in range(tiles):
+            out.append(_oracle_tile_step(self.paths[self.next % len(self.paths)]))
+            self.next += 1
+        return out
+
+    def all_cores(self):
+        import multiprocessing as mp
+        if self.pool is None:
+            self.pool = mp.get_context("spawn").Pool(self.cores, initializer=_single_thread_env)
+            self.pool.map(_oracle_tile_step, self.paths[:self.cores])    # imports, first-touch
         t0 = time.perf_counter()
-        solve.accel_tile(rho_f[:T, :T, :T], K)
-        t_tile = time.perf_counter() - t0
-    n_total = sum(w.counts)
-    est = t_particles / frac + t_coarse + t_tile * n_tiles
-    return {"value": n_total / est, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": (f"oracle particle stages on {frac:.4f} of both species ({sum(len(x) for x, _ in sub)} "
-                       f"particles, {t_particles:.1f} s), 1 of {n_tiles} tile solves ({t_tile:.1f} s), full coarse "
-                       f"solve ({t_coarse:.1f} s); full step extrapolated to {est:.0f} s"),
-            "seconds_measured": round(t_particles + t_coarse + t_tile, 2), "n_total": n_total}
+        res = self.pool.map(_oracle_tile_step, [self.paths[i % len(self.paths)] for i in range(self.cores)])
+        return time.perf_counter() - t0, res
+
+    def close(self):
+        import shutil
+        if self.pool is not None:
+            self.pool.close()
+            self.pool.join()
+        shutil.rmtree(self.info["dir"], ignore_errors=True)
+
+
+def cpu_baseline(workload):
+    """The oracle, as it stands, timed on the host cores on a bounded sample
+    of the workload (whole tiles, see ORACLE_SAMPLES): one thread and all
+    cores.  value = the all-cores rate in particle-steps/s."""
+    if workload not in ORACLE_SAMPLES:
+        return None
+    t0 = time.perf_counter()
+    smp = OracleSampler(workload)
+    setup_s = time.perf_counter() - t0
+    try:
+        one = smp.one_thread(2)
+        wall, many = smp.all_cores()
+    finally:
+        smp.close()
+    info = smp.info
+    tiles, coarse = info["tiles_per_step"], info["coarse_solve_s"]
+    home = np.mean([r[1] for r in one + many])
+    n_step = home * tiles
+    t1 = np.mean([r[0] for r in one])
+    step1 = tiles * t1 + coarse
+    stepN = tiles * wall / len(many) + coarse
+    return {"value": n_step / stepN, "unit": UNIT, "cores": smp.cores, "kind": "oracle",
+            "cpu": cpu_model(), "nproc": smp.cores,
+            "one_thread": {"value": n_step / step1, "cores": 1, "tile_s": round(t1, 3)},
+            "all_cores": {"value": n_step / stepN, "cores": smp.cores, "tiles": len(many), "wall_s": round(wall, 3)},
+            "sample": (f"oracle stages of whole 96^3 tiles (64^3 + 16 buffer; decompress, coarse deposit, window "
+                       f"deposit, tile solve, fine + coarse interpolation, kick-drift, recompress of the home "
+                       f"particles, {vel_bits_note(info)}) cut from the {info['recipe']} realisation of the recipe "
+                       f"({home:.0f} home particles per tile): {len(one)} tiles on 1 thread, {len(many)} tiles on "
+                       f"{smp.cores} processes at once; per step x {tiles} tiles + the {info['coarse_edge']}^3 coarse "
+                       f"solve ({coarse:.1f} s: measured at {info['coarse_measured_edge']}^3, scaled N^3 log N)"),
+            "seconds_measured": round(sum(r[0] for r in one) + wall, 1), "setup_s": round(setup_s, 1)}
+
+
+def vel_bits_note(info):
+    return f"{info['vel_bits']}-bit velocity codes"
 
 
 def run_reference(args):
-    """Reference arm: the oracle timed on the host cores, one bounded sample per step."""
-    from synth import make_workload
-
+    """Reference arm: the oracle timed on all host cores, one bounded sample per
+    step (one tile per core of the workload's two-level recipe, plus the
+    coarse solve's share of a step)."""
     rank, world, _ = dist_env()
     if rank != 0:
         return None
-    w = make_workload(args.workload)
-    frac = 1.0 / 256
-    samples = []
+    wl = args.workload if args.workload in ORACLE_SAMPLES else "two_level256"
     t0 = time.perf_counter()
-    for _ in range(args.warmup):
-        cpu_baseline(w, frac)
-    for _ in range(args.steps):
-        samples.append(cpu_baseline(w, frac))
-    wall = time.perf_counter() - t0
-    value = statistics.median(s["value"] for s in samples)
-    cb = dict(samples[-1])
-    cb["value"] = value
+    smp = OracleSampler(wl)
+    setup_s = time.perf_counter() - t0
+    info = smp.info
+    share = info["coarse_solve_s"] / info["tiles_per_step"]
+    steps = []
+    try:
+        for _ in range(args.warmup):
+            smp.all_cores()
+        for _ in range(args.steps):
+            wall, res = smp.all_cores()
+            steps.append((wall + share * len(res), sum(r[1] for r in res)))
+    finally:
+        smp.close()
+    sec = statistics.median(s[0] for s in steps)
+    units = statistics.median(s[1] for s in steps)
+    value = units / sec
+    cb = {"value": value, "unit": UNIT, "cores": smp.cores, "kind": "oracle", "cpu": cpu_model(), "nproc": smp.cores,
+          "sample": (f"per step: {smp.cores} whole 96^3 tiles of the {info['recipe']} realisation of the recipe "
+                     f"({info['vel_bits']}-bit velocity codes), one per process, through the oracle's stages, "
+                     f"plus their share of the {info['coarse_edge']}^3 coarse solve ({share * 1e3:.1f} ms per tile)")}
     return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": cb["n_total"] / value * 1e3,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "impl": "reference",
-            "config": {"workload": args.workload}, "cpu_baseline": cb,
+            "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": args.workload, "sample_particles_per_step": int(units)}, "cpu_baseline": cb,
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-            "wall_s": round(wall, 1)}
+            "setup_s": round(setup_s, 1)}
 
 
 def main():
@@ -693,15 +1034,17 @@ def main():
     p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    p.add_argument("--workload", default="two_level256")
+    p.add_argument("--workload", default="largest1536")
     p.add_argument("--tile-batch", type=int, default=0)
     p.add_argument("--vmax-mode", type=int, default=0, choices=[0, 1],
                    help="0: exact v_max' (the paper's definition); 1: bound from the force meshes")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-adjoint", action="store_true")
     p.add_argument("--no-autotune", action="store_true")
+    p.add_argument("--no-e2e", action="store_true", help="largest workload: skip the end-to-end run")
+    p.add_argument("--no-extra", action="store_true", help="largest workload: skip the 256^3 workload beside it")
     p.add_argument("--pp", action="store_true", help="add the particle-particle force of Eq. 4 to the step")
-    p.add_argument("--tuning", default="", help="launch tuning as JSON (as printed under 'tuning'); skips the autotuner")
+    p.add_argument("--tuning", default="", help="launch tuning as JSON (as printed under 'tuning')")
     p.add_argument("--adjoint-workload", default="diff128")
     args = p.parse_args()
     res = run_reference(args) if args.impl == "reference" else run_gb300(args)

@@ -58,7 +58,7 @@ struct pm_handle {
   pm_codes_t stage_in[2]{}, stage_out[2]{};
   bool staged = false;
   // packed record bytes for pm_step_packed (pos 3 B, vel 3 or 6 B per particle)
-  uint8_t* pk_pos[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};   // [in/out][species]
+  uint8_t* pk_pos[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};   // [in/out][species]; in and out share buffers
   uint8_t* pk_vel[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
   bool pk_staged = false;
   // pm_step_packed: velocity bytes come over on their own stream while the
@@ -1259,12 +1259,38 @@ int pm_step_packed(pm_handle_t* h, const pm_host_codes_t in[2], pm_host_codes_t 
     h->staged = true;
   }
   if (!h->pk_staged) {
-    for (int io = 0; io < 2; ++io)
+    // The packed input bytes are dead once the count pass starts (positions
+    // are unpacked before the deposit, velocities before the count pass,
+    // which waits for them), and the packed output is written after the
+    // scatter has read the step's scratch for the last time.  So input and
+    // output share one set of buffers, carved from the per-particle scratch
+    // when it is large enough (it is 16 B per particle, the records 9 B at
+    // most): a packed step then needs no device memory beyond the padded
+    // staging codes.
+    auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    size_t need = 0;
+    for (int s = 0; s < 2; ++s) {
+      const size_t n = (size_t)h->stage_in[s].n;
+      need += up(3 * n + 16) + up(3 * n * (vel16 ? 2 : 1) + 16);
+    }
+    uint8_t* carve = reinterpret_cast<uint8_t*>(h->tpv);
+    if (need <= (size_t)h->scratch_n * sizeof(uint4)) {
       for (int s = 0; s < 2; ++s) {
         const size_t n = (size_t)h->stage_in[s].n;
-        CK(h, dalloc(h, &h->pk_pos[io][s], 3 * n + 16));
-        CK(h, dalloc(h, &h->pk_vel[io][s], 3 * n * (vel16 ? 2 : 1) + 16));
+        h->pk_pos[0][s] = h->pk_pos[1][s] = carve;
+        carve += up(3 * n + 16);
+        h->pk_vel[0][s] = h->pk_vel[1][s] = carve;
+        carve += up(3 * n * (vel16 ? 2 : 1) + 16);
       }
+    } else {
+      for (int s = 0; s < 2; ++s) {
+        const size_t n = (size_t)h->stage_in[s].n;
+        CK(h, dalloc(h, &h->pk_pos[0][s], 3 * n + 16));
+        CK(h, dalloc(h, &h->pk_vel[0][s], 3 * n * (vel16 ? 2 : 1) + 16));
+        h->pk_pos[1][s] = h->pk_pos[0][s];
+        h->pk_vel[1][s] = h->pk_vel[0][s];
+      }
+    }
     h->pk_staged = true;
   }
   if (!h->copy_stream) {
