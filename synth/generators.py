@@ -171,6 +171,10 @@ WORKLOADS = {
     # 768^3 fine mesh (192^3 coarse: the row / column coarse transforms), 1728 tiles; 96^3 + 192^3.
     "two_level768": dict(n_fine=768, coarse_ratio=4, tile=64, buffer=16, cdm="zeldovich", n_cdm=96,
                          n_nu=192, vel_bits=16, r_cut=14.0, seed=1618),
+    # The clustered, batched recipe at a size the oracle finishes in seconds: 64^3 fine mesh, 64 tiles of
+    # 16^3 + 8; 32^3 lognormal CDM (per-tile counts 24 .. 2024) + 64^3 nu, 16-bit velocities.
+    "clustered64": dict(n_fine=64, coarse_ratio=4, tile=16, buffer=8, cdm="lognormal", n_cdm=32, n_nu=64,
+                        vel_bits=16, r_cut=6.0, seed=1620),
     # Small two-level cases that the oracle finishes in seconds.
     "two_level64": dict(n_fine=64, coarse_ratio=4, tile=16, buffer=8, cdm="zeldovich", n_cdm=16, n_nu=32,
                         vel_bits=16, r_cut=6.0, seed=1616),

@@ -68,3 +68,105 @@ def cfg_of(w, **kw):
     c = w.config()
     c.update(kw)
     return c
+
+
+def _record_keys(c: codec.Codes):
+    """Per record: absolute position codes P_d = cell_d * 256 + p_d (1/256 of a
+    compression cell per unit, so a move across a cell face is one unit) and
+    the velocity codes, as tuples."""
+    n = c.n_cmp
+    cell = codec.cell_of_particles(c)
+    cxyz = np.stack([cell % n, (cell // n) % n, cell // (n * n)], axis=1)
+    P = cxyz * 256 + c.pos.astype(np.int64)
+    return [tuple(r) for r in np.concatenate([P, c.vel.astype(np.int64)], axis=1).tolist()]
+
+
+def code_pairing(got: codec.Codes, ref: codec.Codes):
+    """Compare one species' codes with the oracle's as multisets of records.
+
+    Records found in only one of the two must pair one to one with a record of
+    the other that differs by one quantisation step of one coordinate: one
+    velocity code by +-1, or one position coordinate by +-1/256 of a
+    compression cell, counted across cell faces (byte 255 of a cell beside
+    byte 0 of the next, periodic).  Those are the particles whose float32
+    update lands on the other side of a bin edge than the float64 one.
+    Returns (exact, paired, unpaired_got, unpaired_ref)."""
+    from collections import Counter
+    period = got.n_cmp * 256
+    ka, kb = Counter(_record_keys(got)), Counter(_record_keys(ref))
+    exact = sum(min(v, kb[k]) for k, v in ka.items())
+    left_a = ka - kb
+    left_b = kb - ka
+    paired = 0
+    for key, cnt in list(left_a.items()):
+        for _ in range(cnt):
+            hit = None
+            for j in range(6):
+                for dlt in (-1, 1):
+                    k2 = list(key)
+                    k2[j] += dlt
+                    if j < 3:
+                        k2[j] %= period
+                    k2 = tuple(k2)
+                    if left_b.get(k2, 0) > 0:
+                        hit = k2
+                        break
+                if hit:
+                    break
+            if hit is None:
+                continue
+            left_b[hit] -= 1
+            if left_b[hit] == 0:
+                del left_b[hit]
+            left_a[key] -= 1
+            paired += 1
+    return exact, paired, sum(v for v in left_a.values() if v > 0), sum(v for v in left_b.values() if v > 0)
+
+
+STRADDLE_MAX = 0.02   # records allowed to sit one quantisation step from the oracle's
+
+
+def assert_codes_match(got: codec.Codes, ref: codec.Codes, label: str = "", max_frac: float = STRADDLE_MAX):
+    """Same particle count and cell counts' total; every record equal to an
+    oracle record or one quantisation step from one (code_pairing), those at
+    most max_frac of the records.  Prints the fraction; returns it."""
+    assert got.n == ref.n and got.counts().sum() == ref.counts().sum() == ref.n
+    exact, paired, ua, ub = code_pairing(got, ref)
+    frac = paired / max(ref.n, 1)
+    print(f"{label}: {exact} records equal, {paired} one step apart ({frac:.4%}), "
+          f"{ua}/{ub} unpaired")
+    assert ua == 0 and ub == 0, f"{label}: {ua} GPU / {ub} oracle records have no partner within one step"
+    assert frac <= max_frac, f"{label}: {frac:.4%} of records one step apart"
+    return frac
+
+
+def device_records_equal(a, b, n_cmp: int) -> bool:
+    """Two species' library codes (device tensors) hold the same multiset of
+    records per cell: equal count bytes and escape entries, and equal records
+    after sorting both streams by (cell, position bytes, velocity codes) on
+    the device (for particle counts where host-side sorting is slow)."""
+    import torch
+    if a.n != b.n or not torch.equal(a.cnt, b.cnt) or not torch.equal(a.n_esc, b.n_esc):
+        return False
+    ne = int(a.n_esc.item())
+    if ne and not torch.equal(a.esc[:ne], b.esc[:ne]):
+        return False
+    counts = a.cnt.to(torch.int64)
+    if ne:
+        e = a.esc[:ne].to(torch.int64) & 0xFFFFFFFF
+        counts[e[:, 0]] = e[:, 1]
+    cell = torch.repeat_interleave(torch.arange(n_cmp ** 3, device=a.cnt.device), counts)
+
+    def keys(c):
+        p = c.pos.to(torch.int64)
+        hi = (cell << 24) | p[:, 0] | (p[:, 1] << 8) | (p[:, 2] << 16)
+        v = c.vel.to(torch.int64) & (0xFFFF if c.vel.dtype == torch.int16 else 0xFF)
+        sh = 16 if c.vel.dtype == torch.int16 else 8
+        lo = v[:, 0] | (v[:, 1] << sh) | (v[:, 2] << (2 * sh))
+        i1 = torch.sort(lo, stable=True).indices
+        i2 = torch.sort(hi[i1], stable=True).indices
+        o = i1[i2]
+        return hi[o], lo[o]
+    ha, la = keys(a)
+    hb, lb = keys(b)
+    return bool(torch.equal(ha, hb) and torch.equal(la, lb))

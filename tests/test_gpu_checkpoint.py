@@ -1,14 +1,16 @@
 """Asynchronous checkpoint: the codes copied to pinned host memory while the
 state keeps stepping are those of the checkpointed step, the fence keeps a
-later step from overwriting them before the copy, and the serialized
-checkpoint restores the state bit for bit."""
+later step from overwriting them before the copy, the serialized
+checkpoint restores the state bit for bit, its byte stream is the oracle's
+serialisation of the same codes, and the checkpointed state matches the
+oracle's own step."""
 import numpy as np
 import pytest
 import torch
 
-from oracle import codec
+from oracle import codec, step
 from synth import make_workload
-from tests.helpers import cfg_of, lib_codes_from_oracle, oracle_codes_from_lib, records
+from tests.helpers import assert_codes_match, cfg_of, lib_codes_from_oracle, oracle_codes_from_lib, records
 
 pytestmark = pytest.mark.gpu
 
@@ -37,6 +39,7 @@ def test_async_checkpoint_while_stepping():
     b2 = [pm2.empty_codes(c.n, esc_cap=64) for c in codes]
     pm2.step(a2, b2, 0.5, 0.5)
     pm2.check()
+    oracle_s1, _ = step.step(codes, cfg, 0.5, 0.5)
     for s in range(2):
         got = oracle_codes_from_lib(host[s], nc, w.vel_bits)
         ref = oracle_codes_from_lib(b2[s], nc, w.vel_bits)
@@ -45,6 +48,12 @@ def test_async_checkpoint_while_stepping():
         np.testing.assert_array_equal(records(got), records(ref))
         # the byte stream of the checkpoint restores the same codes
         blob = serialize(host[s], nc, w.vel_bits)
+        # ... and is the oracle's Sec. 2.4 stream of those codes, byte for byte
+        assert blob == codec.serialize(got)
+        # the checkpointed state against the oracle's own step from the same codes:
+        # the oracle's deserializer reads the library's stream, and every record
+        # equals the oracle's or sits one quantisation step from it
+        assert_codes_match(codec.deserialize(blob), oracle_s1[s], f"checkpoint species {s}")
         back = deserialize(blob, host[s].n, nc, w.vel_bits, esc_cap=64)
         assert torch.equal(back.pos[:, :3], host[s].pos[:, :3]) and torch.equal(back.cnt, host[s].cnt)
         assert torch.equal(back.vel[:, :3], host[s].vel[:, :3]) and torch.equal(back.vmax, host[s].vmax)

@@ -7,7 +7,8 @@ import torch
 
 from oracle import codec, step
 from synth import make_workload
-from tests.helpers import cfg_of, lib_codes_from_oracle, multiset_overlap, oracle_codes_from_lib, records, rel_rms
+from tests.helpers import (assert_codes_match, cfg_of, lib_codes_from_oracle, oracle_codes_from_lib, records,
+                           rel_rms)
 
 pytestmark = pytest.mark.gpu
 
@@ -86,8 +87,7 @@ def test_fused_step_matches_oracle_codes(name, n_cdm, n_nu):
         assert g.counts().sum() == ref[s].n
         assert abs(float(g.vmax) - float(ref[s].vmax)) <= 1e-5 * float(ref[s].vmax)
         # identical except for records straddling a bin edge in float32 vs float64
-        frac = multiset_overlap(records(g), records(ref[s])) / ref[s].n
-        assert frac > 0.98, frac
+        assert_codes_match(g, ref[s], f"{name} species {s}")
 
 
 @pytest.mark.parametrize("name,n_cdm,n_nu", CASES)
@@ -200,5 +200,4 @@ def test_fused_step_vmax_bound_mode(name, n_cdm, n_nu):
         x1, v1 = states[s]
         assert float(g.vmax) >= np.max(np.abs(v1)) * (1 - 1e-5)
         mine = codec.compress(step.to_f32_positions(x1, n), v1.astype(np.float32), n, nc, w.vel_bits, vmax=g.vmax)
-        frac = multiset_overlap(records(g), records(mine)) / mine.n
-        assert frac > 0.98, frac
+        assert_codes_match(g, mine, f"{name} bound mode species {s}")
