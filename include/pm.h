@@ -192,8 +192,11 @@ int pm_decompress(pm_handle_t* h, int species, const pm_codes_t* in, float* x, f
  *                               not exceed 64^3, else PM_ERR_ARG;
  *  in, x, v                     as in pm_decompress (device memory, caller-owned).
  * The first call on each device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture starts.  Every call shares the one array and
+ * (cudaGetSymbolAddress) with that device current and keeps it for the
+ * process; make that first call before any stream capture starts.  The
+ * address belongs to the device's primary context: after cudaDeviceReset it
+ * is stale, so do not call this entry point again on a device that has been
+ * reset.  Every call shares the one array and
  * leaves its contents behind; calls that overlap on the GPU (other streams,
  * other host threads) race on it, so the caller must serialise them.  The
  * call synchronises `stream` before returning and reports a corrupt stream
@@ -216,6 +219,14 @@ int pm_compress(pm_handle_t* h, int species, const float* x, const float* v, con
  * (i t - b .. i t + t + b - 1, ...) mod n_fine (see pm_tile_density). */
 int pm_deposit(pm_handle_t* h, int species, const float* x, int64_t n, float* rho_coarse,
                float* rho_fine, void* stream);
+
+/* CIC deposit of per-particle weights onto the fine mesh (the convention of
+ * pm_deposit, periodic): w [n][nw] float32 (1 <= nw <= 4) on device, out
+ * [nw][n_fine^3] float32, ADDED to.  The compression study of Sec. 2.4
+ * measures number and momentum densities with it (weights 1, v_x, v_y, v_z).
+ * x [n][3] in fine cells, [0, n_fine).  PM_ERR_ARG for nw outside 1..4. */
+int pm_deposit_weights(pm_handle_t* h, const float* x, int64_t n, const float* w, int32_t nw, float* out,
+                       void* stream);
 
 /* Same, int64 fixed point: each particle's mass llrint(m 2^32) is split
  * exactly over its 8 CIC corners, one dimension at a time, with weights

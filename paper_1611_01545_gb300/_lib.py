@@ -50,7 +50,7 @@ class pm_codes_t(ctypes.Structure):
 
 
 EXPORTED = ["pm_init", "pm_destroy", "pm_geometry", "pm_decompress", "pm_compress", "pm_deposit",
-            "pm_deposit_fixed", "pm_deposit_codes", "pm_tile_density", "pm_solve", "pm_solve_fixed", "pm_interpolate",
+            "pm_deposit_weights", "pm_deposit_fixed", "pm_deposit_codes", "pm_tile_density", "pm_solve", "pm_solve_fixed", "pm_interpolate",
             "pm_kick_drift", "pm_step", "pm_step_host", "pm_check", "pm_last_error", "pm_set_timing", "pm_set_graphs",
             "pm_get_tuning", "pm_set_tuning", "pm_autotune", "pm_pp_accel",
             "pm_checkpoint_begin", "pm_checkpoint_fence", "pm_checkpoint_wait", "pm_pack_codes", "pm_unpack_codes",
@@ -70,6 +70,7 @@ _PROTOS = {
     "pm_decompress": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(pm_codes_t), _P, _P, _P]),
     "pm_compress": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P, ctypes.POINTER(pm_codes_t), _P]),
     "pm_deposit": (ctypes.c_int, [_P, ctypes.c_int, _P, _I64, _P, _P, _P]),
+    "pm_deposit_weights": (ctypes.c_int, [_P, _P, _I64, _P, ctypes.c_int32, _P, _P]),
     "pm_deposit_fixed": (ctypes.c_int, [_P, ctypes.c_int, _P, _I64, _P, _P, _P]),
     "pm_deposit_codes": (ctypes.c_int, [_P, ctypes.POINTER(pm_codes_t), _P, _P, _P]),
     "pm_tile_density": (ctypes.c_int, [_P, _P, _I64, _P, _P]),

@@ -13,14 +13,14 @@ density and velocity power spectra at the final step:
   * "resident": the state kept compressed throughout, one fused pm_step per
     step (this library's own mode: a compression every step).
 
-Spectra are measured on an n^3 CIC mesh per species (n = the fine mesh):
-density contrast delta = rho / mean - 1, and the momentum density
-sum_p v_d W / mean summed over d for the velocity power (the paper does not
-define its velocity field; momentum density avoids empty-cell division).
-P(k) is averaged over unit-width shells of |k| (fundamental units), as in
-oracle/power.py, which pins the estimator; tests/test_analysis_cpu.py
-checks this torch version against it.  This is analysis tooling: the PM
-step itself never calls it.
+Spectra are measured on an n^3 CIC mesh per species (n = the fine mesh),
+deposited by the library (pm_deposit_weights): density contrast delta =
+rho / mean - 1, and the momentum density sum_p v_d W / mean summed over d
+for the velocity power (the paper does not define its velocity field;
+momentum density avoids empty-cell division).  P(k) is averaged over
+unit-width shells of |k| (fundamental units), as in oracle/power.py, which
+pins the estimator; tests/test_analysis_cpu.py checks this torch version
+against it.  This is analysis tooling: the PM step itself never calls it.
 """
 from __future__ import annotations
 
@@ -29,30 +29,6 @@ import json
 from typing import Dict, Sequence
 
 import torch
-
-
-def cic_field(x: torch.Tensor, w: torch.Tensor, n: int) -> torch.Tensor:
-    """Periodic CIC sum of weights w [N] (or [N, C]) at positions x [N, 3] on n^3 ([z][y][x])."""
-    x = x.double()
-    i0 = torch.floor(x).long()
-    f = x - i0
-    w = w.double()
-    if w.dim() == 1:
-        w = w[:, None]
-    out = torch.zeros((w.shape[1], n * n * n), dtype=torch.float64, device=x.device)
-    for dz in (0, 1):
-        wz = f[:, 2] if dz else 1 - f[:, 2]
-        iz = (i0[:, 2] + dz) % n
-        for dy in (0, 1):
-            wy = f[:, 1] if dy else 1 - f[:, 1]
-            iy = (i0[:, 1] + dy) % n
-            for dx in (0, 1):
-                wx = f[:, 0] if dx else 1 - f[:, 0]
-                ix = (i0[:, 0] + dx) % n
-                idx = (iz * n + iy) * n + ix
-                c = (wx * wy * wz)[:, None] * w
-                out.index_add_(1, idx, c.t())
-    return out.reshape(w.shape[1], n, n, n)
 
 
 def power_spectrum(field: torch.Tensor):
@@ -76,15 +52,17 @@ def power_spectrum(field: torch.Tensor):
     return torch.arange(1, nsh + 1), (tot / cnt).cpu()
 
 
-def spectra(x: torch.Tensor, v: torch.Tensor, n: int) -> Dict[str, torch.Tensor]:
-    """Density and velocity (momentum-density) power of one species."""
+def spectra(pm, x: torch.Tensor, v: torch.Tensor) -> Dict[str, torch.Tensor]:
+    """Density and velocity (momentum-density) power of one species: number
+    and momentum densities deposited by the library (pm_deposit_weights,
+    weights 1, v_x, v_y, v_z), spectra in float64."""
+    n = pm.n_fine
     N = x.shape[0]
     mean = N / n ** 3
-    ones = torch.ones(N, dtype=torch.float64, device=x.device)
-    rho = cic_field(x, ones, n)[0]
-    mom = cic_field(x, v.double(), n)
-    _, pd = power_spectrum(rho / mean - 1.0)
-    pv = sum(power_spectrum(mom[d] / mean)[1] for d in range(3))
+    w = torch.cat([torch.ones((N, 1), dtype=torch.float32, device=x.device), v.float()], dim=1)
+    f = pm.deposit_weights(x, w).double()
+    _, pd = power_spectrum(f[0] / mean - 1.0)
+    pv = sum(power_spectrum(f[1 + d] / mean)[1] for d in range(3))
     return {"density": pd, "velocity": pv}
 
 
@@ -134,9 +112,9 @@ def compression_study(workload: str = "two_level64", steps: int = 22, restarts: 
     result = {"workload": workload, "steps": steps, "restarts": n_restarts, "c_kick": c, "c_drift": c,
               "n_mesh": n, "vel_bits": cfg["vel_bits"], "species": {}}
     for s, name in enumerate(("cdm", "nu")):
-        ref = spectra(xu[s], vu[s], n)
-        arms = {"restarts": spectra(xr[s], vr[s], n), "single": spectra(xs1[s], vs1[s], n),
-                "resident": spectra(xf[s], vf[s], n)}
+        ref = spectra(pm, xu[s], vu[s])
+        arms = {"restarts": spectra(pm, xr[s], vr[s]), "single": spectra(pm, xs1[s], vs1[s]),
+                "resident": spectra(pm, xf[s], vf[s])}
         sp = {"P_density": ref["density"].tolist(), "P_velocity": ref["velocity"].tolist(),
               "shot_noise": n ** 3 / x0[s].shape[0]}
         for arm, p in arms.items():

@@ -441,6 +441,8 @@ int pm_init(const pm_config_t* cfg, pm_handle_t** out) {
   auto make_plan = [&](SolvePlan& p, int N, int nts, int t, int b, int src_n, int batch, const std::vector<float>& kern) {
     p.N = N;
     p.NH = N / 2 + 1;
+    p.NP = spec_pitch(N);
+    p.status = h->status;
     p.nts = nts;
     p.t = t;
     p.b = b;
@@ -448,8 +450,8 @@ int pm_init(const pm_config_t* cfg, pm_handle_t** out) {
     p.batch = batch;
     A(&p.kern, kern.size() * 4);
     A(&p.tw, (size_t)N * sizeof(float2));
-    A(&p.spec, (size_t)batch * N * N * p.NH * sizeof(float2));
-    A(&p.spec3, (size_t)batch * 3 * t * N * p.NH * sizeof(float2));
+    A(&p.spec, (size_t)batch * N * N * p.NP * sizeof(float2));
+    A(&p.spec3, (size_t)batch * 3 * t * N * p.NP * sizeof(float2));
     if (rc != PM_OK) return;
     std::vector<float2> tw = twiddles(N);
     if (cudaMemcpy(p.kern, kern.data(), kern.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
@@ -475,7 +477,7 @@ int pm_init(const pm_config_t* cfg, pm_handle_t** out) {
   }
   if (!g.two) {
     A(&h->lam_acc, 4 * nf3 * 4);
-    A(&h->adj_spec, (size_t)3 * g.nf * g.nf * (g.nf / 2 + 1) * sizeof(float2));
+    A(&h->adj_spec, (size_t)3 * g.nf * g.nf * spec_pitch(g.nf) * sizeof(float2));
   }
   h->blk_dep = choose_blk(g, fixed, true);
   h->blk_ikd = choose_blk(g, fixed, false);
@@ -553,6 +555,14 @@ int pm_deposit(pm_handle_t* h, int species, const float* x, int64_t n, float* rh
   if (int r = check_species(h, species)) return r;
   CK(h, launch_deposit(x, n, (float)h->cfg.mass[species], h->geo, h->gm.two ? rho_coarse : nullptr, rho_fine,
                        (cudaStream_t)stream));
+  return PM_OK;
+}
+
+int pm_deposit_weights(pm_handle_t* h, const float* x, int64_t n, const float* w, int32_t nw, float* out,
+                       void* stream) {
+  if (!h || !out || (n && (!x || !w))) return fail(h, PM_ERR_ARG, "null argument");
+  if (nw < 1 || nw > 4 || n < 0) return fail(h, PM_ERR_ARG, "nw must be 1..4, n >= 0");
+  CK(h, launch_deposit_weights(x, n, w, nw, h->geo, out, (cudaStream_t)stream));
   return PM_OK;
 }
 

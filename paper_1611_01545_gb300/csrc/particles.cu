@@ -379,6 +379,30 @@ __global__ void k_deposit_global(const float* x, int64_t n, float m, Geo g, floa
   }
 }
 
+// Periodic CIC deposit of nw per-particle weights (w[p nw + c], c < nw <= 4)
+// onto nw fine meshes out[c][nf^3] (float32, the mesh convention of the
+// deposit above): number and momentum densities for the power spectra of
+// the compression study.
+__global__ void k_deposit_weights(const float* x, int64_t n, const float* w, int nw, Geo g, float* out) {
+  const int64_t nf3 = (int64_t)g.nf * g.nf * g.nf;
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+    int ix[2], iy[2], iz[2];
+    float wx[2], wy[2], wz[2];
+    cic_axis(x[3 * p], g.nf, ix[0], ix[1], wx[0], wx[1]);
+    cic_axis(x[3 * p + 1], g.nf, iy[0], iy[1], wy[0], wy[1]);
+    cic_axis(x[3 * p + 2], g.nf, iz[0], iz[1], wz[0], wz[1]);
+    float q[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int c = 0; c < nw; ++c) q[c] = w[p * nw + c];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int dx = k & 1, dy = (k >> 1) & 1, dz = k >> 2;
+      const float wt = __fmul_rn(__fmul_rn(wx[dx], wy[dy]), wz[dz]);
+      float* cell = out + ((int64_t)iz[dz] * g.nf + iy[dy]) * g.nf + ix[dx];
+      for (int c = 0; c < nw; ++c) atomicAdd(cell + c * nf3, __fmul_rn(q[c], wt));
+    }
+  }
+}
+
 // Fixed point: weights a1 = floor(f 2^20), mass split hi = (M a1 + 2^19) >> 20, lo = M - hi.
 __device__ __forceinline__ void fixed_axis(float x, int n, int& i0, int& i1, long long& a1) {
   float f = floorf(x);
@@ -685,9 +709,29 @@ __global__ void k_vmax_bound(const float* vin0, const float* vin1, const uint32_
 struct CellBlock {
   int ix0, iy0, iz0;
 };
+// Blocks are handed out x fastest, then in bricks of PM_BLOCK_BRICK x
+// PM_BLOCK_BRICK (y, z) block rows (when the block grid divides into them),
+// so that the blocks running at the same time cover a compact region: the
+// partial writes that neighbouring blocks make to the same cells (fine
+// density halos, new-cell ranges of the recompressed codes) then meet in L2
+// before the lines are evicted.
+#ifndef PM_BLOCK_BRICK
+#define PM_BLOCK_BRICK 1
+#endif
 __device__ __forceinline__ CellBlock block_of(const Blk& bk, int bid) {
-  int nbx = bk.nbx, nby = bk.nby;
-  int bx = bid % nbx, by = (bid / nbx) % nby, bz = bid / (nbx * nby);
+  const int nbx = bk.nbx, nby = bk.nby, nbz = bk.nbz;
+  const int bx = bid % nbx, r = bid / nbx;
+  int by, bz;
+  constexpr int B = PM_BLOCK_BRICK;
+  if (B > 1 && nby % B == 0 && nbz % B == 0) {
+    const int in = r % (B * B), brick = r / (B * B);
+    const int nyb = nby / B;
+    by = (brick % nyb) * B + in % B;
+    bz = (brick / nyb) * B + in / B;
+  } else {
+    by = r % nby;
+    bz = r / nby;
+  }
   return CellBlock{bx * bk.RX, by * bk.RY, bz * bk.RZ};
 }
 
@@ -1418,6 +1462,14 @@ cudaError_t launch_decompress(const PCodes& in, const int64_t* off, const Geo& g
 cudaError_t launch_deposit(const float* x, int64_t n, float m, const Geo& g, float* rho_c, float* rho_f, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
   k_deposit_global<<<grid_for(n, 256), 256, 0, st>>>(x, n, m, g, rho_c, rho_f);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_deposit_weights(const float* x, int64_t n, const float* w, int nw, const Geo& g, float* out,
+                                  cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  k_deposit_weights<<<grid_for(n, 256), 256, 0, st>>>(x, n, w, nw, g, out);
   note_launches(1);
   return cudaGetLastError();
 }

@@ -52,6 +52,8 @@ size_t scan_partial_bytes(int64_t ncell);
 cudaError_t launch_decompress(const PCodes& in, const int64_t* off, const Geo& g, float* x, float* v, cudaStream_t st);
 cudaError_t launch_deposit(const float* x, int64_t n, float m, const Geo& g, float* rho_c, float* rho_f,
                            cudaStream_t st);
+cudaError_t launch_deposit_weights(const float* x, int64_t n, const float* w, int nw, const Geo& g, float* out,
+                                  cudaStream_t st);
 cudaError_t launch_deposit_fixed(const float* x, int64_t n, long long M, const Geo& g, long long* rho_c,
                                  long long* rho_f, cudaStream_t st);
 cudaError_t launch_interpolate(const float* x, int64_t n, const Geo& g, const float* acc_c, const float* acc_f,

@@ -30,18 +30,26 @@ struct Geom {
   int ntiles() const { return nts * nts * nts; }
 };
 
+// Row pitch (complex values) of the spectrum buffers of an N^3 transform:
+// N/2 + 1, padded to 50 for N = 96 so that every spectrum row starts on a
+// 16-byte boundary (the tensor-map copies of the 96^3 passes need row
+// strides that are multiples of 16 bytes).
+__host__ __device__ constexpr int spec_pitch(int N) { return N == 96 ? 50 : N / 2 + 1; }
+
 // One periodic-window FFT solve family (coarse mesh, single mesh or fine tiles).
 struct SolvePlan {
   int N = 0;          // transform edge
   int NH = 0;         // N/2 + 1
+  int NP = 0;         // spectrum row pitch, spec_pitch(N)
+  int* status = nullptr;   // library status word (bounded copy waits report ST_TIMEOUT)
   int nts = 1;        // problems per side
   int t = 0, b = 0;   // output interior and offset of the window
   int src_n = 0;      // periodic source / destination mesh edge
   int batch = 1;      // problems per batch
   float* kern = nullptr;   // device [3][N slot][N slot][NH]
   float2* tw = nullptr;    // device [N]
-  float2* spec = nullptr;  // device [batch][N][N][NH]
-  float2* spec3 = nullptr; // device [batch][3][t][N][NH]
+  float2* spec = nullptr;  // device [batch][N][N][NP]
+  float2* spec3 = nullptr; // device [batch][3][t][N][NP]
 };
 
 // Counts kernel launches made by the library (all handles); read by pm_launch_count.

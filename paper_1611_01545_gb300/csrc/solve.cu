@@ -14,15 +14,18 @@
 // The kernel tables already contain the 1/N^3 (tiles) or 1/V (periodic)
 // normalisation, so both transform directions are unnormalised.
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>
 
 #include "fft.cuh"
 #include "pm_common.cuh"
+#include "tma.cuh"
 
 namespace pm {
 using namespace pmfft;
 
 template <int N> struct SolveCfg {
   static constexpr int NH = N / 2 + 1;
+  static constexpr int NP = spec_pitch(N);   // row pitch (complex values) of the spectrum buffers
 // Threads per block of passes A and C (compile-time tunables; measured on the
 // 96^3 tiles: 512 for A, 384 for C).
 #ifndef PM_SOLVE_THREADS
@@ -33,8 +36,7 @@ template <int N> struct SolveCfg {
 #endif
   static constexpr int threads = (N >= 96) ? PM_SOLVE_THREADS : 256;
   static constexpr int threads_c = (N >= 96) ? PM_SOLVE_C_THREADS : 256;
-  static constexpr size_t smem_a = sizeof(float2) * (N + (size_t)N * N / 2 + (size_t)N * NH);
-  static constexpr size_t smem_b = sizeof(float2) * (N + 2 * (size_t)N * NH);
+  static constexpr size_t smem_a = sizeof(float2) * (N + (size_t)N * N / 2 + (size_t)N * NP);
 };
 
 struct SolveArgs {
@@ -53,6 +55,7 @@ struct SolveArgs {
   unsigned int* amax;   // pass C: if set, atomicMax of max |output| (float bits; values are >= 0)
   const float* pc;      // pass C: if set, add this coarse force [3][pnc^3] trilinearly prolongated to the fine nodes
   int pnc, prc;         // its edge and the fine cells per coarse cell (a power of two dividing t)
+  int* status;          // library status word: ST_TIMEOUT when a bounded copy wait gives up
 };
 
 __device__ __forceinline__ int pmod(int a, int n) {
@@ -100,11 +103,11 @@ __device__ __forceinline__ int wrap1(int g, int n) { return g < 0 ? g + n : (g >
 // component pb at src[i * CS + pb] (the adjoint's float4 accumulation mesh).
 template <int N, bool FIXED, int CS = 1>
 __device__ __forceinline__ void solve_a_body(const SolveArgs& a) {
-  constexpr int NH = SolveCfg<N>::NH;
+  constexpr int NH = SolveCfg<N>::NH, NP = SolveCfg<N>::NP;
   extern __shared__ float2 sm[];
   float2* tw = sm;
   float2* W = sm + N;               // N/2 packed rows of N
-  float2* P = W + N * N / 2;        // N rows (y) of NH
+  float2* P = W + N * N / 2;        // N rows (y) of NH, pitch NP
   for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = a.tw[i];
   const int z = blockIdx.x;
   const int pb = blockIdx.y;
@@ -137,16 +140,17 @@ __device__ __forceinline__ void solve_a_body(const SolveArgs& a) {
     PM_COLS(k, NH) {
       float2 zk = Wj[slot_of<N>(k)];
       float2 zm = Wj[slot_of<N>(k == 0 ? 0 : N - k)];
-      P[(2 * j) * NH + k] = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
-      P[(2 * j + 1) * NH + k] = make_float2(0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));
+      P[(2 * j) * NP + k] = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
+      P[(2 * j + 1) * NP + k] = make_float2(0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));
     }
   }
   __syncthreads();
-  fft_fwd<N, NH, 1, NH>(P, tw);
-  // N * NH is even for every supported N: copy two complex values per access.
-  float4* out = reinterpret_cast<float4*>(a.spec + ((size_t)pb * N + z) * N * NH);
+  fft_fwd<N, NH, 1, NP>(P, tw);
+  // N * NP is even for every supported N: copy two complex values per access
+  // (the pitch's pad columns are copied too and never read).
+  float4* out = reinterpret_cast<float4*>(a.spec + ((size_t)pb * N + z) * N * NP);
   const float4* P4 = reinterpret_cast<const float4*>(P);
-  for (int i = threadIdx.x; i < N * NH / 2; i += blockDim.x) out[i] = P4[i];
+  for (int i = threadIdx.x; i < N * NP / 2; i += blockDim.x) out[i] = P4[i];
 }
 
 template <int N, bool FIXED, int CS = 1>
@@ -189,7 +193,7 @@ template <int N> struct PassB {
 
 template <int N>
 __device__ __forceinline__ void solve_b_body(const SolveArgs& a) {
-  constexpr int NH = PassB<N>::NH, KC = PassB<N>::KC;
+  constexpr int NH = PassB<N>::NH, KC = PassB<N>::KC, NP = SolveCfg<N>::NP;
   extern __shared__ float2 sm[];
   float2* tw = sm;
   // [z][3 KC]: component d of the products in columns d KC .. d KC + KC - 1; the
@@ -203,10 +207,10 @@ __device__ __forceinline__ void solve_b_body(const SolveArgs& a) {
   const int pb = blockIdx.z;
   const int kx0 = half * KC;
   const int ncol = (NH - kx0) < KC ? (NH - kx0) : KC;
-  const float2* in = a.spec + (size_t)pb * N * N * NH + (size_t)ys * NH + kx0;
+  const float2* in = a.spec + (size_t)pb * N * N * NP + (size_t)ys * NP + kx0;
   for (int i = threadIdx.x; i < N * KC; i += blockDim.x) {
     const int z = i / KC, c = i - z * KC;
-    if (c < ncol) async_copy8(F + z * 3 * KC + c, in + (size_t)z * N * NH + c);
+    if (c < ncol) async_copy8(F + z * 3 * KC + c, in + (size_t)z * N * NP + c);
     else F[z * 3 * KC + c] = make_float2(0.f, 0.f);
   }
   async_wait();
@@ -233,10 +237,10 @@ __device__ __forceinline__ void solve_b_body(const SolveArgs& a) {
   __syncthreads();
   fft_inv<N, 3 * KC, 1, 3 * KC>(G, tw);
   for (int d = 0; d < 3; ++d) {
-    float2* out = a.spec3 + ((size_t)pb * 3 + d) * a.t * N * NH + (size_t)ys * NH + kx0;
+    float2* out = a.spec3 + ((size_t)pb * 3 + d) * a.t * N * NP + (size_t)ys * NP + kx0;
     for (int i = threadIdx.x; i < a.t * KC; i += blockDim.x) {
       const int zo = i / KC, c = i - zo * KC;
-      if (c < ncol) out[(size_t)zo * N * NH + c] = G[(zo + a.b) * 3 * KC + d * KC + c];
+      if (c < ncol) out[(size_t)zo * N * NP + c] = G[(zo + a.b) * 3 * KC + d * KC + c];
     }
   }
 }
@@ -268,7 +272,7 @@ constexpr auto solve_b_kernel() {
 // gives the scalar result.
 template <int N>
 __global__ void __launch_bounds__(PassB<N>::threads) k_solve_b_adj(SolveArgs a) {
-  constexpr int NH = PassB<N>::NH, KC = PassB<N>::KC;
+  constexpr int NH = PassB<N>::NH, KC = PassB<N>::KC, NP = SolveCfg<N>::NP;
   extern __shared__ float2 sm[];
   float2* tw = sm;
   float2* F = sm + N;             // [z][KC]
@@ -280,10 +284,10 @@ __global__ void __launch_bounds__(PassB<N>::threads) k_solve_b_adj(SolveArgs a) 
   const size_t kstride = (size_t)N * N * NH;
   for (int i = threadIdx.x; i < N * KC; i += blockDim.x) G[i] = make_float2(0.f, 0.f);
   for (int d = 0; d < 3; ++d) {
-    const float2* in = a.spec + (size_t)d * N * N * NH + (size_t)ys * NH + kx0;
+    const float2* in = a.spec + (size_t)d * N * N * NP + (size_t)ys * NP + kx0;
     for (int i = threadIdx.x; i < N * KC; i += blockDim.x) {
       const int z = i / KC, c = i - z * KC;
-      F[i] = c < ncol ? in[(size_t)z * N * NH + c] : make_float2(0.f, 0.f);
+      F[i] = c < ncol ? in[(size_t)z * N * NP + c] : make_float2(0.f, 0.f);
     }
     __syncthreads();
     fft_fwd<N, KC, 1, KC>(F, tw);
@@ -299,34 +303,49 @@ __global__ void __launch_bounds__(PassB<N>::threads) k_solve_b_adj(SolveArgs a) 
     __syncthreads();
   }
   fft_inv<N, KC, 1, KC>(G, tw);
-  float2* out = a.spec3 + (size_t)ys * NH + kx0;
+  float2* out = a.spec3 + (size_t)ys * NP + kx0;
   for (int i = threadIdx.x; i < N * KC; i += blockDim.x) {
     const int z = i / KC, c = i - z * KC;
-    if (c < ncol) out[(size_t)z * N * NH + c] = G[i];
+    if (c < ncol) out[(size_t)z * N * NP + c] = G[i];
   }
 }
 
 template <int N>
+__device__ __forceinline__ void solve_c_body(const SolveArgs& a, float2* tw, float2* P, float2* W);
+
+template <int N>
 __global__ void __launch_bounds__(SolveCfg<N>::threads_c) k_solve_c(SolveArgs a) {
-  constexpr int NH = SolveCfg<N>::NH;
+  constexpr int NP = SolveCfg<N>::NP;
   extern __shared__ float2 sm[];
   float2* tw = sm;
-  float2* P = sm + N;          // [y][kx]
-  float2* W = P + N * NH;      // t/2 packed rows of N
+  float2* P = sm + N;          // [y][kx], pitch NP
+  float2* W = P + N * NP;      // t/2 packed rows of N
   for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = a.tw[i];
   const int zo = blockIdx.x;
   const int d = blockIdx.y;
   const int pb = blockIdx.z;
-  const float4* in = reinterpret_cast<const float4*>(a.spec3 + (((size_t)pb * 3 + d) * a.t + zo) * N * NH);
+  const float4* in = reinterpret_cast<const float4*>(a.spec3 + (((size_t)pb * 3 + d) * a.t + zo) * N * NP);
   float4* P4 = reinterpret_cast<float4*>(P);
-  for (int i = threadIdx.x; i < N * NH / 2; i += blockDim.x) async_copy16(P4 + i, in + i);
+  for (int i = threadIdx.x; i < N * NP / 2; i += blockDim.x) async_copy16(P4 + i, in + i);
   async_wait();
   __syncthreads();
-  fft_inv<N, NH, 1, NH>(P, tw);
+  solve_c_body<N>(a, tw, P, W);
+}
+
+// Pass C after its input plane is in P: inverse y transform, the packed
+// inverse x transform of the output rows, the prolongated coarse force, the
+// output store and the running max |a|.
+template <int N>
+__device__ __forceinline__ void solve_c_body(const SolveArgs& a, float2* tw, float2* P, float2* W) {
+  constexpr int NH = SolveCfg<N>::NH, NP = SolveCfg<N>::NP;
+  const int zo = blockIdx.x;
+  const int d = blockIdx.y;
+  const int pb = blockIdx.z;
+  fft_inv<N, NH, 1, NP>(P, tw);
   const int half_rows = a.t / 2;
   PM_ROWS(j, half_rows) {
-    const float2* Pa = P + (a.b + 2 * j) * NH;
-    const float2* Pb = Pa + NH;
+    const float2* Pa = P + (a.b + 2 * j) * NP;
+    const float2* Pb = Pa + NP;
     float2* Wj = W + j * N;
     PM_COLS(k, N) {
       float2 A, B;
@@ -399,6 +418,276 @@ __global__ void __launch_bounds__(SolveCfg<N>::threads_c) k_solve_c(SolveArgs a)
     if ((threadIdx.x & 31) == 0 && m > __uint_as_float(*(volatile unsigned int*)a.amax))
       atomicMax(a.amax, __float_as_uint(m));
   }
+}
+
+// ---- 96^3 passes staged by the tensor memory accelerator ----------------
+//
+// The 96^3 transforms (the buffered fine tiles, and a 96^3 periodic mesh)
+// move their shared-memory pencils with TMA bulk copies instead of
+// per-thread copies:
+//   A  the window plane arrives as 36 boxes of 16 x 16 cells (a tensor map
+//      of the source mesh; window origins are multiples of 16 cells, so no
+//      box crosses the periodic boundary), is repacked into two-row complex
+//      rows and transformed as before; the half-spectrum plane leaves as one
+//      bulk store;
+//   B  the z pencils of KT = 26 kx columns arrive as one 52 x 1 x 96 box of
+//      the spectrum (columns past kx = N/2 read as zeros); the second step of
+//      the forward z transform, the three kernel products and the first step
+//      of each inverse transform run in registers per (column, k1) item; the
+//      output z range of each component leaves as one box store;
+//   C  the input plane arrives as one bulk copy.
+// Spectrum rows are padded to spec_pitch(96) = 50 complex values (400
+// bytes), so rows, boxes and planes start on 16-byte boundaries.
+
+constexpr int kTmaAlign = 128;   // shared-memory alignment of every TMA destination and source
+constexpr int kBox = 16;         // edge (cells) of the pass-A window boxes
+
+__device__ __forceinline__ unsigned char* tma_align(unsigned char* p) {
+  const unsigned a = tma::smem_u32(p);
+  return p + ((kTmaAlign - (a & (kTmaAlign - 1))) & (kTmaAlign - 1));
+}
+
+// Bounded wait of the whole block for phase 0 of `bar`.  When it gives up
+// (the copies did not complete in time) the block records ST_TIMEOUT, waits
+// once more (bounded) for copies still in flight, and the caller returns.
+__device__ __forceinline__ bool block_wait(uint64_t* bar, int* status) {
+  int bad = tma::mbar_wait(bar, 0) ? 0 : 1;
+  bad = __syncthreads_or(bad);
+  if (bad) {
+    if (threadIdx.x == 0 && status) atomicOr(status, ST_TIMEOUT);
+    tma::mbar_wait(bar, 0);
+  }
+  return !bad;
+}
+
+template <int N> struct PassAT {
+  static constexpr int NH = N / 2 + 1, NP = spec_pitch(N), NB = N / kBox;
+  // P [N][NP] (first the staged boxes), W [N/2][N], twiddles
+  static constexpr size_t smem = kTmaAlign + sizeof(float2) * ((size_t)N * NP + (size_t)N / 2 * N + N);
+};
+
+template <int N>
+__global__ void __launch_bounds__(SolveCfg<N>::threads, PM_SOLVE_A_MINB)
+    k_solve_a_tma(SolveArgs a, const __grid_constant__ CUtensorMap src_map) {
+  using C = PassAT<N>;
+  constexpr int NH = C::NH, NP = C::NP, NB = C::NB;
+  static_assert((size_t)NB * NB * kBox * kBox <= (size_t)2 * N * NP, "staged window must fit in P");
+  extern __shared__ unsigned char smraw_a[];
+  __shared__ uint64_t bar;
+  float2* P = reinterpret_cast<float2*>(tma_align(smraw_a));   // [y][NP]; first the staged window boxes
+  float2* W = P + N * NP;                                        // N/2 packed rows of N
+  float2* tw = W + N * N / 2;
+  float* S = reinterpret_cast<float*>(P);                        // box (yb, xb) at S + (yb NB + xb) 256
+  const int z = blockIdx.x, pb = blockIdx.y;
+  int ox, oy, oz;
+  problem_origin(a, a.p0 + pb, ox, oy, oz);
+  const int n = a.src_n;
+  if (threadIdx.x == 0) {
+    tma::mbar_init(&bar, 1);
+    tma::fence_barrier_init();
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    if (threadIdx.x == 0) tma::mbar_arrive_expect_tx(&bar, NB * NB * kBox * kBox * (unsigned)sizeof(float));
+    __syncwarp();
+    const int gz = wrap1(oz + z, n);
+    for (int k = threadIdx.x; k < NB * NB; k += 32) {
+      const int yb = k / NB, xb = k - yb * NB;
+      tma::tensor_load_3d(S + k * kBox * kBox, &src_map, wrap1(ox + kBox * xb, n), wrap1(oy + kBox * yb, n), gz,
+                          &bar);
+    }
+  }
+  for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = a.tw[i];
+  if (!block_wait(&bar, a.status)) return;
+  // W[j][x] = (row 2j, row 2j + 1) at x; both rows lie in the same box row pair
+  for (int i = threadIdx.x; i < (N / 2) * (N / 4); i += blockDim.x) {
+    const int j = i / (N / 4), x = 4 * (i - j * (N / 4));
+    const int y0 = 2 * j;
+    const float* s0 = S + ((y0 / kBox) * NB + x / kBox) * kBox * kBox + (y0 % kBox) * kBox + x % kBox;
+    const float4 r0 = *reinterpret_cast<const float4*>(s0);
+    const float4 r1 = *reinterpret_cast<const float4*>(s0 + kBox);
+    float4* w = reinterpret_cast<float4*>(W + j * N + x);
+    w[0] = make_float4(r0.x, r1.x, r0.y, r1.y);
+    w[1] = make_float4(r0.z, r1.z, r0.w, r1.w);
+  }
+  __syncthreads();
+  fft_fwd<N, N / 2, N, 1>(W, tw);
+  PM_ROWS(j, N / 2) {
+    const float2* Wj = W + j * N;
+    PM_COLS(k, NH) {
+      float2 zk = Wj[slot_of<N>(k)];
+      float2 zm = Wj[slot_of<N>(k == 0 ? 0 : N - k)];
+      P[(2 * j) * NP + k] = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
+      P[(2 * j + 1) * NP + k] = make_float2(0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));
+    }
+  }
+  __syncthreads();
+  fft_fwd<N, NH, 1, NP>(P, tw);
+  tma::fence_proxy_async();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    tma::bulk_store(a.spec + ((size_t)pb * N + z) * N * NP, P, (unsigned)(N * NP * sizeof(float2)));
+    tma::bulk_commit();
+    tma::bulk_wait_all();
+  }
+}
+
+template <int N> struct PassBT {
+  static constexpr int NH = N / 2 + 1, NP = spec_pitch(N);
+  static constexpr int KT = 26;                        // kx columns per block: KT * 8 bytes is a multiple of 16
+  static constexpr int nchunk = (NH + KT - 1) / KT;
+  static constexpr int threads = 256;
+  // G [3][N][KT] (component, z, column), twiddles
+  static constexpr size_t smem = kTmaAlign + sizeof(float2) * (3 * (size_t)N * KT + N);
+};
+
+template <int N>
+__global__ void __launch_bounds__(PassBT<N>::threads, 3)
+    k_solve_b_tma(SolveArgs a, const __grid_constant__ CUtensorMap spec_map,
+                  const __grid_constant__ CUtensorMap spec3_map) {
+  using B = PassBT<N>;
+  constexpr int NH = B::NH, KT = B::KT;
+  constexpr int N1 = Factor<N>::N1, N2 = Factor<N>::N2;
+  extern __shared__ unsigned char smraw_b[];
+  __shared__ uint64_t bar;
+  float2* G = reinterpret_cast<float2*>(tma_align(smraw_b));   // [3][N][KT]
+  float2* tw = G + 3 * N * KT;
+  const int ys = blockIdx.x, kx0 = blockIdx.y * KT, pb = blockIdx.z;
+  if (threadIdx.x == 0) {
+    tma::mbar_init(&bar, 1);
+    tma::fence_barrier_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    tma::mbar_arrive_expect_tx(&bar, N * KT * (unsigned)sizeof(float2));
+    tma::tensor_load_3d(G, &spec_map, 2 * kx0, ys, pb * N, &bar);
+  }
+  for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = a.tw[i];
+  if (!block_wait(&bar, a.status)) return;
+  // forward z transform, step 1 (items (j2, column)), in component 0
+  for (int w = threadIdx.x; w < KT * N2; w += blockDim.x) {
+    const int j2 = w / KT, c = w - j2 * KT;
+    float2* base = G + c;
+    float2 v[N1];
+#pragma unroll
+    for (int j1 = 0; j1 < N1; ++j1) v[j1] = base[(N2 * j1 + j2) * KT];
+    Dft<N1, -1>::run(v);
+#pragma unroll
+    for (int k1 = 1; k1 < N1; ++k1) v[k1] = cmul(v[k1], tw[j2 * k1]);
+#pragma unroll
+    for (int k1 = 0; k1 < N1; ++k1) base[(N2 * k1 + j2) * KT] = v[k1];
+  }
+  __syncthreads();
+  // forward step 2, the products i K_d F and step 1 of each inverse
+  // transform, per (k1, column) item: F(kz = k1 + N1 k2) sits at slot N2 k1 + k2
+  const float* Kb = a.kern + (size_t)ys * NH + kx0;
+  const size_t kstride = (size_t)N * N * NH;
+  for (int w = threadIdx.x; w < KT * N1; w += blockDim.x) {
+    const int k1 = w / KT, c = w - k1 * KT;
+    const bool live = kx0 + c < NH;
+    float2 f[N2];
+#pragma unroll
+    for (int j2 = 0; j2 < N2; ++j2) f[j2] = G[(N2 * k1 + j2) * KT + c];
+    Dft<N2, -1>::run(f);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const float* Kd = Kb + d * kstride + (size_t)(N2 * k1) * N * NH + c;
+      float2 g[N2];
+#pragma unroll
+      for (int k2 = 0; k2 < N2; ++k2) {
+        const float k = live ? __ldg(Kd + (size_t)k2 * N * NH) : 0.f;
+        g[k2] = make_float2(-f[k2].y * k, f[k2].x * k);   // i K f
+      }
+      Dft<N2, 1>::run(g);
+#pragma unroll
+      for (int j2 = 1; j2 < N2; ++j2) g[j2] = cmul(g[j2], conjf2(tw[j2 * k1]));
+      float2* gd = G + (size_t)d * N * KT + c;
+#pragma unroll
+      for (int j2 = 0; j2 < N2; ++j2) gd[(N2 * k1 + j2) * KT] = g[j2];
+    }
+  }
+  __syncthreads();
+  // inverse step 2 of the three components -> natural z order
+  for (int w = threadIdx.x; w < 3 * KT * N2; w += blockDim.x) {
+    const int j2 = w / (3 * KT), q = w - j2 * 3 * KT;
+    const int d = q / KT, c = q - d * KT;
+    float2* base = G + (size_t)d * N * KT + c;
+    float2 v[N1];
+#pragma unroll
+    for (int k1 = 0; k1 < N1; ++k1) v[k1] = base[(N2 * k1 + j2) * KT];
+    Dft<N1, 1>::run(v);
+#pragma unroll
+    for (int j1 = 0; j1 < N1; ++j1) base[(N2 * j1 + j2) * KT] = v[j1];
+  }
+  tma::fence_proxy_async();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int d = 0; d < 3; ++d)
+      tma::tensor_store_3d(&spec3_map, 2 * kx0, ys, (pb * 3 + d) * a.t, G + ((size_t)d * N + a.b) * KT);
+    tma::bulk_commit();
+    tma::bulk_wait_all();
+  }
+}
+
+template <int N> struct PassCT {
+  // P [N][NP], W [N/2][N], twiddles
+  static constexpr size_t smem = kTmaAlign + sizeof(float2) * ((size_t)N * spec_pitch(N) + (size_t)N / 2 * N + N);
+};
+
+template <int N>
+__global__ void __launch_bounds__(SolveCfg<N>::threads_c) k_solve_c_tma(SolveArgs a) {
+  constexpr int NP = SolveCfg<N>::NP;
+  extern __shared__ unsigned char smraw_c[];
+  __shared__ uint64_t bar;
+  float2* P = reinterpret_cast<float2*>(tma_align(smraw_c));   // [y][NP]
+  float2* W = P + N * NP;                                        // t/2 packed rows of N
+  float2* tw = W + N * N / 2;
+  const int zo = blockIdx.x, d = blockIdx.y, pb = blockIdx.z;
+  if (threadIdx.x == 0) {
+    tma::mbar_init(&bar, 1);
+    tma::fence_barrier_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned bytes = N * NP * (unsigned)sizeof(float2);
+    tma::mbar_arrive_expect_tx(&bar, bytes);
+    tma::bulk_load(P, a.spec3 + (((size_t)pb * 3 + d) * a.t + zo) * N * NP, bytes, &bar);
+  }
+  for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = a.tw[i];
+  if (!block_wait(&bar, a.status)) return;
+  solve_c_body<N>(a, tw, P, W);
+}
+
+// Tensor maps (encoded on the host; cuTensorMapEncodeTiled reached through
+// the runtime's driver entry point, so the library links no driver library).
+static PFN_cuTensorMapEncodeTiled_v12000 encode_tiled() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+// 3-D float32 tensor: dims d0 (innermost) .. d2, byte strides s1, s2 of dims 1 and 2, box b0 x b1 x b2.
+static bool map_3d(CUtensorMap* m, const void* base, uint64_t d0, uint64_t d1, uint64_t d2, uint64_t s1, uint64_t s2,
+                   uint32_t b0, uint32_t b1, uint32_t b2) {
+  PFN_cuTensorMapEncodeTiled_v12000 fn = encode_tiled();
+  if (!fn || (reinterpret_cast<uintptr_t>(base) & 15) || (s1 & 15) || (s2 & 15) || (b0 * 4) % 16 || b0 > 256 ||
+      b1 > 256 || b2 > 256)
+    return false;
+  cuuint64_t dims[3] = {d0, d1, d2};
+  cuuint64_t strides[2] = {s1, s2};
+  cuuint32_t box[3] = {b0, b1, b2};
+  cuuint32_t es[3] = {1, 1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void*>(base), dims, strides, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 // ---- Large periodic meshes (N > 128: the coarse mesh of the largest
@@ -553,7 +842,7 @@ static cudaError_t solve_large_n(const SolvePlan& p, const void* src, bool fixed
     cudaFuncSetAttribute(k_large_cx<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::smem_cx);
     attr_done = true;
   }
-  SolveArgs a{src, fixed ? 1 : 0, N, 1, N, 0, 0, p.spec, p.spec3, p.kern, p.tw, dst, 0, amax, nullptr, 0, 1};
+  SolveArgs a{src, fixed ? 1 : 0, N, 1, N, 0, 0, p.spec, p.spec3, p.kern, p.tw, dst, 0, amax, nullptr, 0, 1, p.status};
   {
     TimedScope ts(tm, "fft_a_mesh", st);
     if (fixed) k_large_ax<N, true><<<dim3(N / L::R, N), L::threads, L::smem_ax, st>>>(a);
@@ -595,21 +884,51 @@ static cudaError_t solve_n(const SolvePlan& p, const void* src, bool fixed, floa
     cudaFuncSetAttribute(solve_a_kernel<N, true>(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem_a);
     cudaFuncSetAttribute(solve_b_kernel<N>(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PassB<N>::smem);
     cudaFuncSetAttribute(k_solve_c<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem_a);
+    if constexpr (N == 96) {
+      cudaFuncSetAttribute(k_solve_a_tma<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PassAT<N>::smem);
+      cudaFuncSetAttribute(k_solve_b_tma<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PassBT<N>::smem);
+      cudaFuncSetAttribute(k_solve_c_tma<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PassCT<N>::smem);
+    }
     attr_done = true;
+  }
+  // 96^3 passes staged by TMA: pass A wants window origins and the source
+  // mesh on 16-cell boundaries (float source), pass B its output z range on
+  // an 8-row boundary; pass C always applies.
+  bool tma_a = false, tma_b = false;
+  CUtensorMap src_map, spec_map, spec3_map;
+  if constexpr (N == 96) {
+    const int n = p.src_n;
+    tma_a = !fixed && n % kBox == 0 && p.t % kBox == 0 && p.b % kBox == 0 &&
+            map_3d(&src_map, src, n, n, n, (uint64_t)n * 4, (uint64_t)n * n * 4, kBox, kBox, 1);
+    tma_b = p.b % 8 == 0 &&
+            map_3d(&spec_map, p.spec, 2 * C::NH, N, (uint64_t)p.batch * N, (uint64_t)C::NP * 8,
+                   (uint64_t)N * C::NP * 8, 2 * PassBT<N>::KT, 1, N) &&
+            map_3d(&spec3_map, p.spec3, 2 * C::NH, N, (uint64_t)p.batch * 3 * p.t, (uint64_t)C::NP * 8,
+                   (uint64_t)N * C::NP * 8, 2 * PassBT<N>::KT, 1, p.t);
   }
   const int nprob = p.nts * p.nts * p.nts;
   for (int p0 = 0; p0 < nprob; p0 += p.batch) {
     int nb = (nprob - p0 < p.batch) ? (nprob - p0) : p.batch;
     SolveArgs a{src, fixed ? 1 : 0, p.src_n, p.nts, p.t, p.b, p0, p.spec, p.spec3, p.kern, p.tw, dst, 0, amax,
-                pro ? pro->coarse : nullptr, pro ? pro->nc : 0, pro ? pro->rc : 1};
+                pro ? pro->coarse : nullptr, pro ? pro->nc : 0, pro ? pro->rc : 1, p.status};
     {
       TimedScope ts(tm, N == p.src_n && p.b == 0 ? "fft_a_mesh" : "fft_a_tiles", st);
-      if (fixed) solve_a_kernel<N, true>()<<<dim3(N, nb), C::threads, C::smem_a, st>>>(a);
-      else solve_a_kernel<N, false>()<<<dim3(N, nb), C::threads, C::smem_a, st>>>(a);
+      if constexpr (N == 96) {
+        if (tma_a) k_solve_a_tma<N><<<dim3(N, nb), C::threads, PassAT<N>::smem, st>>>(a, src_map);
+      }
+      if (!tma_a) {
+        if (fixed) solve_a_kernel<N, true>()<<<dim3(N, nb), C::threads, C::smem_a, st>>>(a);
+        else solve_a_kernel<N, false>()<<<dim3(N, nb), C::threads, C::smem_a, st>>>(a);
+      }
     }
     {
       TimedScope ts(tm, N == p.src_n && p.b == 0 ? "fft_b_mesh" : "fft_b_tiles", st);
-      solve_b_kernel<N>()<<<dim3(N, PassB<N>::nchunk, nb), PassB<N>::threads, PassB<N>::smem, st>>>(a);
+      if constexpr (N == 96) {
+        if (tma_b)
+          k_solve_b_tma<N><<<dim3(N, PassBT<N>::nchunk, nb), PassBT<N>::threads, PassBT<N>::smem, st>>>(a, spec_map,
+                                                                                                       spec3_map);
+      }
+      if (!tma_b) solve_b_kernel<N>()<<<dim3(N, PassB<N>::nchunk, nb), PassB<N>::threads, PassB<N>::smem, st>>>(a);
     }
     if (pro && pro->ready && p0 == 0) {
       cudaError_t e = cudaStreamWaitEvent(st, pro->ready, 0);   // the coarse force must be complete
@@ -617,7 +936,8 @@ static cudaError_t solve_n(const SolvePlan& p, const void* src, bool fixed, floa
     }
     {
       TimedScope ts(tm, N == p.src_n && p.b == 0 ? "fft_c_mesh" : "fft_c_tiles", st);
-      k_solve_c<N><<<dim3(p.t, 3, nb), C::threads_c, C::smem_a, st>>>(a);
+      if constexpr (N == 96) k_solve_c_tma<N><<<dim3(p.t, 3, nb), C::threads_c, PassCT<N>::smem, st>>>(a);
+      else k_solve_c<N><<<dim3(p.t, 3, nb), C::threads_c, C::smem_a, st>>>(a);
     }
     note_launches(3);
     cudaError_t e = cudaGetLastError();
@@ -651,7 +971,8 @@ static cudaError_t solve_adjoint_n(const SolvePlan& p, const float* lam_acc, boo
   cudaFuncSetAttribute(ka, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem_a);
   cudaFuncSetAttribute(k_solve_b_adj<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sizeof(float2) * (N + 2 * (size_t)N * PassB<N>::KC)));
   cudaFuncSetAttribute(k_solve_c<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::smem_a);
-  SolveArgs a{lam_acc, 0, p.src_n, 1, N, 0, 0, spec3comp, p.spec3, p.kern, p.tw, lam_rho, 1};
+  SolveArgs a{lam_acc, 0, p.src_n, 1, N, 0, 0, spec3comp, p.spec3, p.kern, p.tw, lam_rho, 1, nullptr, nullptr, 0, 1,
+              p.status};
   ka<<<dim3(N, 3), C::threads, C::smem_a, st>>>(a);
   a.comp_mode = 0;
   k_solve_b_adj<N><<<dim3(N, 2, 1), PassB<N>::threads, sizeof(float2) * (N + 2 * (size_t)N * PassB<N>::KC), st>>>(a);

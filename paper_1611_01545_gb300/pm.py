@@ -186,6 +186,14 @@ class PM:
         self._err(self.lib.pm_deposit(self.h, species, _ptr(x), x.shape[0], _ptr(rho_coarse), _ptr(rho_fine),
                                       _stream(stream)))
 
+    def deposit_weights(self, x: torch.Tensor, w: torch.Tensor, stream=None) -> torch.Tensor:
+        """CIC deposit of per-particle weights w [n, nw] (nw <= 4) onto nw fine meshes [nw, n^3]."""
+        w = w.reshape(x.shape[0], -1).to(torch.float32).contiguous()
+        out = torch.zeros((w.shape[1],) + (self.n_fine,) * 3, dtype=torch.float32, device="cuda")
+        self._err(self.lib.pm_deposit_weights(self.h, _ptr(x.contiguous()), x.shape[0], _ptr(w), w.shape[1],
+                                              _ptr(out), _stream(stream)))
+        return out
+
     def deposit_fixed(self, species: int, x: torch.Tensor, rho_coarse, rho_fine, stream=None):
         self._err(self.lib.pm_deposit_fixed(self.h, species, _ptr(x), x.shape[0], _ptr(rho_coarse),
                                             _ptr(rho_fine), _stream(stream)))

@@ -81,37 +81,22 @@ def _record_keys(c: codec.Codes):
     return [tuple(r) for r in np.concatenate([P, c.vel.astype(np.int64)], axis=1).tolist()]
 
 
-def code_pairing(got: codec.Codes, ref: codec.Codes):
-    """Compare one species' codes with the oracle's as multisets of records.
-
-    Records found in only one of the two must pair one to one with a record of
-    the other that differs by one quantisation step of one coordinate: one
-    velocity code by +-1, or one position coordinate by +-1/256 of a
-    compression cell, counted across cell faces (byte 255 of a cell beside
-    byte 0 of the next, periodic).  Those are the particles whose float32
-    update lands on the other side of a bin edge than the float64 one.
-    Returns (exact, paired, unpaired_got, unpaired_ref)."""
-    from collections import Counter
-    period = got.n_cmp * 256
-    ka, kb = Counter(_record_keys(got)), Counter(_record_keys(ref))
-    exact = sum(min(v, kb[k]) for k, v in ka.items())
-    left_a = ka - kb
-    left_b = kb - ka
+def _pair_off(left_a, left_b, period, offsets):
+    """Pairs leftover records of a with leftover records of b at the given
+    coordinate offsets (position coordinates periodic); returns the count."""
     paired = 0
     for key, cnt in list(left_a.items()):
         for _ in range(cnt):
             hit = None
-            for j in range(6):
-                for dlt in (-1, 1):
-                    k2 = list(key)
+            for off in offsets:
+                k2 = list(key)
+                for j, dlt in off:
                     k2[j] += dlt
                     if j < 3:
                         k2[j] %= period
-                    k2 = tuple(k2)
-                    if left_b.get(k2, 0) > 0:
-                        hit = k2
-                        break
-                if hit:
+                k2 = tuple(k2)
+                if left_b.get(k2, 0) > 0:
+                    hit = k2
                     break
             if hit is None:
                 continue
@@ -120,22 +105,60 @@ def code_pairing(got: codec.Codes, ref: codec.Codes):
                 del left_b[hit]
             left_a[key] -= 1
             paired += 1
-    return exact, paired, sum(v for v in left_a.values() if v > 0), sum(v for v in left_b.values() if v > 0)
+    return paired
+
+
+_ONE = [((j, d),) for j in range(6) for d in (-1, 1)]
+_TWO = [((i, a), (j, b)) for i in range(6) for j in range(i + 1, 6) for a in (-1, 1) for b in (-1, 1)]
+
+
+def code_pairing(got: codec.Codes, ref: codec.Codes, detail: bool = False):
+    """Compare one species' codes with the oracle's as multisets of records.
+
+    Records found in only one of the two must pair one to one with a record of
+    the other that differs by one quantisation step of one coordinate: one
+    velocity code by +-1, or one position coordinate by +-1/256 of a
+    compression cell, counted across cell faces (byte 255 of a cell beside
+    byte 0 of the next, periodic).  Those are the particles whose float32
+    update lands on the other side of a bin edge than the float64 one.  The
+    records left after that may pair at one step in each of two coordinates
+    (a particle near an edge in two of its six coordinates at once).
+    Returns (exact, paired_one, paired_two, unpaired_got, unpaired_ref); with
+    detail=True also the unpaired records of each side as (P_x, P_y, P_z,
+    V_x, V_y, V_z)."""
+    from collections import Counter
+    period = got.n_cmp * 256
+    ka, kb = Counter(_record_keys(got)), Counter(_record_keys(ref))
+    exact = sum(min(v, kb[k]) for k, v in ka.items())
+    left_a = ka - kb
+    left_b = kb - ka
+    one = _pair_off(left_a, left_b, period, _ONE)
+    two = _pair_off(left_a, left_b, period, _TWO)
+    ua = sum(v for v in left_a.values() if v > 0)
+    ub = sum(v for v in left_b.values() if v > 0)
+    if detail:
+        return (exact, one, two, ua, ub, [k for k, v in left_a.items() if v > 0],
+                [k for k, v in left_b.items() if v > 0])
+    return exact, one, two, ua, ub
 
 
 STRADDLE_MAX = 0.02   # records allowed to sit one quantisation step from the oracle's
+DOUBLE_MAX = 1e-4     # ... and one step in each of two coordinates (plus one record)
 
 
 def assert_codes_match(got: codec.Codes, ref: codec.Codes, label: str = "", max_frac: float = STRADDLE_MAX):
     """Same particle count and cell counts' total; every record equal to an
     oracle record or one quantisation step from one (code_pairing), those at
-    most max_frac of the records.  Prints the fraction; returns it."""
+    most max_frac of the records, and at most 1 + 1e-4 n of them one step off
+    in two coordinates.  Prints the fractions; returns the one-step fraction."""
     assert got.n == ref.n and got.counts().sum() == ref.counts().sum() == ref.n
-    exact, paired, ua, ub = code_pairing(got, ref)
-    frac = paired / max(ref.n, 1)
-    print(f"{label}: {exact} records equal, {paired} one step apart ({frac:.4%}), "
-          f"{ua}/{ub} unpaired")
-    assert ua == 0 and ub == 0, f"{label}: {ua} GPU / {ub} oracle records have no partner within one step"
+    exact, one, two, ua, ub, la, lb = code_pairing(got, ref, detail=True)
+    frac = (one + two) / max(ref.n, 1)
+    print(f"{label}: {exact} records equal, {one} one step apart, {two} one step apart in two coordinates "
+          f"({frac:.4%}), {ua}/{ub} unpaired")
+    assert ua == 0 and ub == 0, (f"{label}: {ua} GPU / {ub} oracle records have no partner within one step: "
+                                 f"GPU {la[:5]} oracle {lb[:5]}")
+    assert two <= 1 + DOUBLE_MAX * ref.n, f"{label}: {two} records one step off in two coordinates"
     assert frac <= max_frac, f"{label}: {frac:.4%} of records one step apart"
     return frac
 

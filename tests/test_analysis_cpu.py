@@ -1,10 +1,11 @@
-"""The torch estimators of the compression study (paper_1611_01545_gb300/
-analysis.py) against the oracle on CPU tensors: CIC field against
-oracle/mesh.py, power spectrum against oracle/power.py."""
+"""The torch power-spectrum estimator of the compression study
+(paper_1611_01545_gb300/analysis.py) against oracle/power.py on CPU
+tensors (its CIC fields come from the library's pm_deposit_weights,
+checked against the oracle in tests/test_gpu_analysis.py)."""
 import numpy as np
 import torch
 
-from oracle import mesh, power
+from oracle import power
 
 
 def test_power_spectrum_matches_oracle():
@@ -16,13 +17,3 @@ def test_power_spectrum_matches_oracle():
         jt, Pt = power_spectrum(torch.from_numpy(f))
         np.testing.assert_array_equal(jt.numpy(), js)
         np.testing.assert_allclose(Pt.numpy(), P, rtol=1e-10)
-
-
-def test_cic_field_matches_oracle():
-    from paper_1611_01545_gb300.analysis import cic_field
-    rng = np.random.default_rng(4)
-    n = 10
-    x = rng.random((500, 3)) * n
-    w = rng.standard_normal(500)
-    got = cic_field(torch.from_numpy(x), torch.from_numpy(w), n)[0].numpy()
-    np.testing.assert_allclose(got, mesh.cic_deposit(x, w, n), rtol=1e-12, atol=1e-12)

@@ -1,9 +1,9 @@
 """The strict comparison of post-step codes (tests/helpers.code_pairing) on
 the CPU: records one quantisation step from the oracle's pair up (a bin edge
 inside a cell, a compression-cell face, the periodic box face, one velocity
-code), while planted mistakes in the oracle's codes (a particle in the
-neighbouring cell, a velocity two codes off, a dropped record) are left
-unpaired."""
+code; one step in each of two codes is counted apart), while planted
+mistakes in the oracle's codes (a particle in the neighbouring cell, a
+velocity two codes off, a dropped record) are left unpaired."""
 import numpy as np
 
 from oracle import codec
@@ -30,7 +30,7 @@ def _below(a):
 def test_identical_codes_pair_exactly():
     x, v = _base()
     a = _codes(x, v)
-    assert code_pairing(a, _codes(x, v, a.vmax)) == (x.shape[0], 0, 0, 0)
+    assert code_pairing(a, _codes(x, v, a.vmax)) == (x.shape[0], 0, 0, 0, 0)
 
 
 def test_bin_edge_cell_face_and_box_face_straddlers_pair():
@@ -46,7 +46,7 @@ def test_bin_edge_cell_face_and_box_face_straddlers_pair():
     z[1, 0] = _below(8.0)              # byte 255 of cell 1
     z[2, 0] = _below(float(N_FINE))    # byte 255 of the last cell
     got = _codes(z, v, ref.vmax)
-    assert code_pairing(got, ref) == (x.shape[0] - 3, 3, 0, 0)
+    assert code_pairing(got, ref) == (x.shape[0] - 3, 3, 0, 0, 0)
 
 
 def test_velocity_code_one_step_pairs_two_steps_do_not():
@@ -55,9 +55,12 @@ def test_velocity_code_one_step_pairs_two_steps_do_not():
     got = _codes(x, v, ref.vmax)
     got.vel = got.vel.copy()
     got.vel[10, 1] += 1
-    assert code_pairing(got, ref) == (x.shape[0] - 1, 1, 0, 0)
+    assert code_pairing(got, ref) == (x.shape[0] - 1, 1, 0, 0, 0)
     got.vel[10, 1] += 1
-    assert code_pairing(got, ref)[2:] == (1, 1)
+    assert code_pairing(got, ref)[3:] == (1, 1)
+    got.vel[10, 1] -= 1
+    got.vel[10, 2] += 1                               # one step in each of two velocity codes
+    assert code_pairing(got, ref) == (x.shape[0] - 1, 0, 1, 0, 0)
 
 
 def test_planted_cell_move_and_dropped_record_are_unpaired():
@@ -66,10 +69,10 @@ def test_planted_cell_move_and_dropped_record_are_unpaired():
     y = x.copy()
     y[7, 1] = np.mod(y[7, 1] + 4.0, N_FINE)      # the neighbouring compression cell, same in-cell byte
     got = _codes(y, v, ref.vmax)
-    exact, paired, ua, ub = code_pairing(got, ref)
-    assert (paired, ua, ub) == (0, 1, 1)
+    exact, one, two, ua, ub = code_pairing(got, ref)
+    assert (one, two, ua, ub) == (0, 0, 1, 1)
     got = _codes(x[1:], v[1:], ref.vmax)
-    assert code_pairing(got, ref)[2:] == (0, 1)
+    assert code_pairing(got, ref)[3:] == (0, 1)
 
 
 def test_device_record_comparison_ignores_order_within_cells_only():

@@ -62,3 +62,39 @@ def test_noalloc_rejects_oversized_mesh_and_reports_corruption():
     rc, x1, _ = _noalloc(lib, 32, 16, dc, stream)       # a clean call after a corrupt one
     assert rc == 0
     np.testing.assert_array_equal(x1.cpu().numpy(), codec.decompress(c, 32)[0])
+
+
+def test_noalloc_allocates_nothing_and_takes_the_largest_mesh():
+    """At the size limit (n_fine 256, cmp_ratio 4: exactly 64^3 compression
+    cells) the call succeeds, agrees with pm_decompress bit for bit, and
+    repeated calls leave the device's free memory unchanged."""
+    from paper_1611_01545_gb300 import PM, _lib
+    lib = _lib.load()
+    stream = torch.cuda.current_stream()
+    rng = np.random.default_rng(6)
+    n = 256
+    x = (rng.random((40000, 3)) * n).astype(np.float32)
+    c = codec.compress(x, rng.standard_normal((40000, 3)).astype(np.float32), n, n // 4, 16)
+    dc = lib_codes_from_oracle(c)
+    pm = PM(dict(n_fine=n, coarse_ratio=4, tile=64, buffer=16, cmp_ratio=4, vel_bits=16, G=1.0, mass=(1.0, 1.0),
+                 count=(c.n, 0), r_split=14.0 / 4.5, r_cut=14.0))
+    x0, v0 = pm.decompress(0, dc)
+    pm.check()
+    outs = [(torch.empty((c.n, 3), dtype=torch.float32, device="cuda"),
+             torch.empty((c.n, 3), dtype=torch.float32, device="cuda")) for _ in range(3)]
+    s = dc.struct()
+
+    def call(xo, vo):
+        return lib.pm_decompress_noalloc(n, 4, 16, ctypes.byref(s), ctypes.c_void_p(xo.data_ptr()),
+                                         ctypes.c_void_p(vo.data_ptr()), ctypes.c_void_p(stream.cuda_stream))
+    assert call(*outs[0]) == 0                      # warm-up: device address looked up
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for xo, vo in outs[1:]:
+        assert call(xo, vo) == 0
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+    for xo, vo in outs:
+        assert torch.equal(xo, x0) and torch.equal(vo, v0)
+    pm.close()
