@@ -302,6 +302,22 @@ int pm_unpack_codes(pm_handle_t* h, const pm_codes_t* in, pm_codes_t* out, void*
 int pm_step_packed(pm_handle_t* h, const pm_host_codes_t in[2], pm_host_codes_t out[2], double c_kick,
                    double c_drift, void* stream);
 
+/* pm_step_packed without waiting: queues the input copies (host -> device
+ * on a library stream, then unpacked there), the step on `stream`, and the
+ * output copies (device -> host on a second library stream), and returns.
+ * Consecutive calls overlap: a call's input copies start once the previous
+ * step has read its input (after its count pass), and its count pass waits
+ * for the previous step's output copies, so one step's output copies run
+ * beside the next step's input copies, deposit and solve.  `out` is complete,
+ * and `in` may be changed, only after pm_check (which synchronises `stream`
+ * and both library streams and reports the status); the host buffers must
+ * stay valid until then, and a caller that reuses one `out` for several
+ * calls keeps the last step's codes.  Needs device memory for one more
+ * packed copy of the input (9 or 6 bytes per particle) beyond
+ * pm_step_packed's.  Graph replay does not apply to this call. */
+int pm_step_packed_async(pm_handle_t* h, const pm_host_codes_t in[2], pm_host_codes_t out[2], double c_kick,
+                         double c_drift, void* stream);
+
 /* Reverse mode of the single-mesh step (coarse_ratio == 1), for gradients of
  * losses of the final positions or density with respect to initial
  * conditions.  The paper has no adjoint; these are the chain rule of the

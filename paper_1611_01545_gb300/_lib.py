@@ -54,7 +54,7 @@ EXPORTED = ["pm_init", "pm_destroy", "pm_geometry", "pm_decompress", "pm_compres
             "pm_kick_drift", "pm_step", "pm_step_host", "pm_check", "pm_last_error", "pm_set_timing", "pm_set_graphs",
             "pm_get_tuning", "pm_set_tuning", "pm_autotune", "pm_pp_accel",
             "pm_checkpoint_begin", "pm_checkpoint_fence", "pm_checkpoint_wait", "pm_pack_codes", "pm_unpack_codes",
-            "pm_step_packed", "pm_restrict",
+            "pm_step_packed", "pm_step_packed_async", "pm_restrict",
             "pm_stage_times", "pm_serialize", "pm_deserialize", "pm_error_string", "pm_launch_count",
             "pm_decompress_noalloc", "pm_deposit_adjoint", "pm_solve_adjoint", "pm_interpolate_adjoint",
             "pm_step_adjoint", "pm_step_adjoint_acc"]
@@ -92,6 +92,8 @@ _PROTOS = {
     "pm_pack_codes": (ctypes.c_int, [_P, ctypes.POINTER(pm_codes_t), ctypes.POINTER(pm_codes_t), _P]),
     "pm_unpack_codes": (ctypes.c_int, [_P, ctypes.POINTER(pm_codes_t), ctypes.POINTER(pm_codes_t), _P]),
     "pm_step_packed": (ctypes.c_int, [_P, ctypes.POINTER(pm_codes_t), ctypes.POINTER(pm_codes_t), _D, _D, _P]),
+    "pm_step_packed_async": (ctypes.c_int, [_P, ctypes.POINTER(pm_codes_t), ctypes.POINTER(pm_codes_t), _D, _D,
+                                            _P]),
     "pm_get_tuning": (ctypes.c_int, [_P, ctypes.POINTER(pm_tuning_t)]),
     "pm_set_tuning": (ctypes.c_int, [_P, ctypes.POINTER(pm_tuning_t)]),
     "pm_autotune": (ctypes.c_int, [_P, ctypes.POINTER(pm_codes_t), ctypes.POINTER(pm_codes_t), ctypes.c_double,

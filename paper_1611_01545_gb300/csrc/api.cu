@@ -66,6 +66,17 @@ struct pm_handle {
   cudaStream_t copy_stream = nullptr;
   cudaEvent_t pk_fork = nullptr, pk_vel_ready = nullptr;
   cudaEvent_t pre_count_wait = nullptr;   // set only while a packed step is being enqueued
+  // pm_step_packed_async: input copies on copy_stream, output copies on
+  // d2h_stream, so consecutive steps overlap their copies with each other's
+  // compute; separate packed input buffers (the output ones sit in the scratch)
+  cudaStream_t d2h_stream = nullptr;
+  cudaEvent_t as_in_free = nullptr, as_pos_ready = nullptr, as_vel_ready = nullptr, as_packed = nullptr,
+              as_out_done = nullptr;
+  uint8_t* as_pos[2] = {nullptr, nullptr};
+  uint8_t* as_vel[2] = {nullptr, nullptr};
+  bool as_ready = false;
+  cudaEvent_t pre_count_wait2 = nullptr;     // set only while an async packed step is being enqueued
+  cudaEvent_t post_count_record = nullptr;   // recorded after the count pass (the staged input is read)
   // pm_step replay: one instantiated graph per (codes descriptors, c_k, c_d)
   struct StepGraph {
     int kind;   // 0: pm_step (device codes); 1: pm_step_packed (host codes)
@@ -104,7 +115,10 @@ template <class T>
 cudaError_t dalloc(pm_handle* h, T** p, size_t bytes) {
   void* q = nullptr;
   cudaError_t e = cudaMalloc(&q, bytes ? bytes : 16);
-  if (e != cudaSuccess) return e;
+  if (e != cudaSuccess) {
+    cudaGetLastError();   // an allocation failure must not surface later as a launch error
+    return e;
+  }
   h->allocs.push_back(q);
   *p = static_cast<T*>(q);
   return cudaSuccess;
@@ -260,11 +274,13 @@ Geo to_geo(const Geom& g) { return Geo{g.nf, g.rc, g.nc, g.rcmp, g.ncmp, g.ncell
 Blk dep_blk(const pm_handle* h) {
   Blk b = h->blk_dep;
   b.work = h->persist_dep ? h->work : nullptr;
+  b.brick = block_brick(b);
   return b;
 }
 Blk ikd_blk(const pm_handle* h, int pass) {
   Blk b = h->blk_ikd;
   b.work = h->persist_ikd ? h->work + 1 + pass : nullptr;
+  b.brick = block_brick(b);
   return b;
 }
 cudaError_t zero_work(const pm_handle* h, cudaStream_t st) {
@@ -504,6 +520,9 @@ int pm_destroy(pm_handle_t* h) {
   if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
   if (h->pk_fork) cudaEventDestroy(h->pk_fork);
   if (h->pk_vel_ready) cudaEventDestroy(h->pk_vel_ready);
+  if (h->d2h_stream) cudaStreamDestroy(h->d2h_stream);
+  for (cudaEvent_t e : {h->as_in_free, h->as_pos_ready, h->as_vel_ready, h->as_packed, h->as_out_done})
+    if (e) cudaEventDestroy(e);
   if (h->side_stream) cudaStreamDestroy(h->side_stream);
   if (h->fork_ev) cudaEventDestroy(h->fork_ev);
   if (h->join_ev) cudaEventDestroy(h->join_ev);
@@ -1026,9 +1045,10 @@ int step_launch(pm_handle_t* h, const pm_codes_t in[2], pm_codes_t out[2], doubl
                     (float)h->cfg.mass[1], (float)h->cfg.G, (float)h->cfg.r_soft, h->app, bound ? h->amax + 2 : nullptr,
                     st));
   }
+  if (h->pre_count_wait) CK(h, cudaStreamWaitEvent(st, h->pre_count_wait, 0));   // packed step: velocities in
+  if (h->pre_count_wait2) CK(h, cudaStreamWaitEvent(st, h->pre_count_wait2, 0)); // async: previous output copied
   // bound mode: v_max' from the mesh maxima, before any particle is kicked
   if (bound) CK(h, launch_vmax_bound(in[0].vmax, in[1].vmax, h->amax, ck, out[0].vmax, out[1].vmax, st));
-  if (h->pre_count_wait) CK(h, cudaStreamWaitEvent(st, h->pre_count_wait, 0));   // packed step: velocities in
   {
     TimedScope ts(tm, "ikd_count", st);
     if (!bound) CK(h, cudaMemsetAsync(h->vmax_bits, 0, 8, st));
@@ -1038,6 +1058,7 @@ int step_launch(pm_handle_t* h, const pm_codes_t in[2], pm_codes_t out[2], doubl
                            bound ? out[0].vmax : nullptr, bound ? out[1].vmax : nullptr, h->cfg.pp ? h->app : nullptr,
                            !via_fine, st));
   }
+  if (h->post_count_record) CK(h, cudaEventRecord(h->post_count_record, st));
   {
     TimedScope ts(tm, "scan_out", st);
     if (!bound) CK(h, launch_set_vmax2(h->vmax_bits, out[0].vmax, out[1].vmax, st));
@@ -1249,10 +1270,90 @@ int packed_launch(pm_handle_t* h, const pm_host_codes_t in[2], pm_host_codes_t o
 }
 }  // namespace
 
+namespace {
+int packed_setup(pm_handle_t* h, const pm_host_codes_t in[2], pm_host_codes_t out[2]);
+}
+
 int pm_step_packed(pm_handle_t* h, const pm_host_codes_t in[2], pm_host_codes_t out[2], double c_kick,
                    double c_drift, void* stream) {
   if (!h || !in || !out) return fail(h, PM_ERR_ARG, "null argument");
   cudaStream_t st = (cudaStream_t)stream;
+  if (int r = packed_setup(h, in, out)) return r;
+  const int r = (h->graphs && !h->timer.on) ? step_graph(h, in, out, c_kick, c_drift, st, 1)
+                                            : packed_launch(h, in, out, c_kick, c_drift, st);
+  if (r != PM_OK) return r;
+  return pm_check(h, stream);
+}
+
+int pm_step_packed_async(pm_handle_t* h, const pm_host_codes_t in[2], pm_host_codes_t out[2], double c_kick,
+                         double c_drift, void* stream) {
+  if (!h || !in || !out) return fail(h, PM_ERR_ARG, "null argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (int r = packed_setup(h, in, out)) return r;
+  const bool vel16 = h->cfg.vel_bits == 16;
+  const int64_t ncell = h->gm.ncell();
+  const size_t vbytes = vel16 ? 6 : 3;
+  if (!h->as_ready) {
+    for (int s = 0; s < 2; ++s) {
+      const size_t n = (size_t)h->stage_in[s].n;
+      CK(h, dalloc(h, &h->as_pos[s], 3 * n + 16));
+      CK(h, dalloc(h, &h->as_vel[s], vbytes * n + 16));
+    }
+    CK(h, cudaStreamCreateWithFlags(&h->d2h_stream, cudaStreamNonBlocking));
+    for (cudaEvent_t* e : {&h->as_in_free, &h->as_pos_ready, &h->as_vel_ready, &h->as_packed, &h->as_out_done})
+      CK(h, cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+    CK(h, cudaEventRecord(h->as_in_free, st));
+    CK(h, cudaEventRecord(h->as_out_done, h->d2h_stream));
+    h->as_ready = true;
+  }
+  // input copies and unpacking, once the previous step's count pass has read its input
+  CK(h, cudaStreamWaitEvent(h->copy_stream, h->as_in_free, 0));
+  for (int s = 0; s < 2; ++s) {
+    const int64_t n = in[s].n;
+    if (int r = copy_meta(h, h->stage_in[s], in[s], ncell, cudaMemcpyHostToDevice, h->copy_stream)) return r;
+    if (n > 0) CK(h, cudaMemcpyAsync(h->as_pos[s], in[s].pos, (size_t)n * 3, cudaMemcpyHostToDevice, h->copy_stream));
+    CK(h, launch_unpack(h->as_pos[s], nullptr, vel16, n, reinterpret_cast<uint32_t*>(h->stage_in[s].pos), nullptr,
+                        h->copy_stream));
+  }
+  CK(h, cudaEventRecord(h->as_pos_ready, h->copy_stream));
+  for (int s = 0; s < 2; ++s) {
+    const int64_t n = in[s].n;
+    if (n > 0)
+      CK(h, cudaMemcpyAsync(h->as_vel[s], in[s].vel, (size_t)n * vbytes, cudaMemcpyHostToDevice, h->copy_stream));
+    CK(h, launch_unpack(nullptr, h->as_vel[s], vel16, n, nullptr, h->stage_in[s].vel, h->copy_stream));
+  }
+  CK(h, cudaEventRecord(h->as_vel_ready, h->copy_stream));
+  // the step: positions first; velocities and the previous step's output copies before the count pass
+  CK(h, cudaStreamWaitEvent(st, h->as_pos_ready, 0));
+  h->pre_count_wait = h->as_vel_ready;
+  h->pre_count_wait2 = h->as_out_done;
+  h->post_count_record = h->as_in_free;
+  const int r = step_launch(h, h->stage_in, h->stage_out, c_kick, c_drift, st);
+  h->pre_count_wait = h->pre_count_wait2 = h->post_count_record = nullptr;
+  if (r != PM_OK) return r;
+  for (int s = 0; s < 2; ++s)
+    CK(h, launch_pack(reinterpret_cast<const uint32_t*>(h->stage_out[s].pos), h->stage_out[s].vel, vel16,
+                      in[s].n, h->pk_pos[1][s], h->pk_vel[1][s], st));
+  CK(h, cudaEventRecord(h->as_packed, st));
+  // output copies
+  CK(h, cudaStreamWaitEvent(h->d2h_stream, h->as_packed, 0));
+  for (int s = 0; s < 2; ++s) {
+    const int64_t n = in[s].n;
+    if (int r2 = copy_meta(h, out[s], h->stage_out[s], ncell, cudaMemcpyDeviceToHost, h->d2h_stream)) return r2;
+    if (n > 0) {
+      CK(h, cudaMemcpyAsync(out[s].pos, h->pk_pos[1][s], (size_t)n * 3, cudaMemcpyDeviceToHost, h->d2h_stream));
+      CK(h, cudaMemcpyAsync(out[s].vel, h->pk_vel[1][s], (size_t)n * vbytes, cudaMemcpyDeviceToHost,
+                            h->d2h_stream));
+    }
+  }
+  CK(h, cudaEventRecord(h->as_out_done, h->d2h_stream));
+  return PM_OK;
+}
+
+namespace {
+// Checks and first-use allocations shared by the packed steps: staging codes,
+// packed buffers (in and out share the step scratch), copy stream and events.
+int packed_setup(pm_handle_t* h, const pm_host_codes_t in[2], pm_host_codes_t out[2]) {
   const bool vel16 = h->cfg.vel_bits == 16;
   for (int s = 0; s < 2; ++s) {
     if (out[s].n != in[s].n) return fail(h, PM_ERR_ARG, "out[s].n must equal in[s].n");
@@ -1313,11 +1414,9 @@ int pm_step_packed(pm_handle_t* h, const pm_host_codes_t in[2], pm_host_codes_t 
     if (in[s].esc_cap > h->stage_in[s].esc_cap)
       return fail(h, PM_ERR_ARG, "input escape capacity larger than at the first call");
   }
-  const int r = (h->graphs && !h->timer.on) ? step_graph(h, in, out, c_kick, c_drift, st, 1)
-                                            : packed_launch(h, in, out, c_kick, c_drift, st);
-  if (r != PM_OK) return r;
-  return pm_check(h, stream);
+  return PM_OK;
 }
+}  // namespace
 
 int pm_step_host(pm_handle_t* h, const pm_host_codes_t in[2], pm_host_codes_t out[2], double c_kick, double c_drift,
                  void* stream) {
@@ -1347,6 +1446,8 @@ int pm_check(pm_handle_t* h, void* stream) {
   if (!h) return PM_ERR_ARG;
   cudaStream_t st = (cudaStream_t)stream;
   CK(h, cudaStreamSynchronize(st));
+  if (h->d2h_stream) CK(h, cudaStreamSynchronize(h->d2h_stream));   // copies queued by pm_step_packed_async
+  if (h->copy_stream) CK(h, cudaStreamSynchronize(h->copy_stream));
   int s = 0;
   CK(h, cudaMemcpy(&s, h->status, 4, cudaMemcpyDeviceToHost));
   CK(h, cudaMemset(h->status, 0, 4));

@@ -19,6 +19,7 @@ struct Blk {
   int RX, RY, RZ;     // cells per block along x, y, z
   int nbx, nby, nbz;  // blocks along x, y, z
   int D;              // half-width (cells) of the new-cell histogram window
+  int brick;          // blocks are handed out in bricks of brick x brick (y, z) block rows (1: row order)
   int* work;          // persistent launch: device counter of cell blocks taken (zeroed before the launch); null: one CTA per block
 };
 
@@ -67,6 +68,8 @@ size_t deposit_codes_smem(const Geo& g, const Blk& bk, bool fixed);
 size_t ikd_count_smem(const Geo& g, const Blk& bk);
 size_t ikd_scatter_smem(const Geo& g, const Blk& bk);
 int window_cells(const Geo& g, const Blk& bk);
+// Brick edge (block rows) of the block order for a block grid (1: row order).
+int block_brick(const Blk& bk);
 cudaError_t launch_deposit_codes(const PCodes& c0, const PCodes& c1, const int64_t* off0, const int64_t* off1,
                                  const Geo& g, const Blk& bk, float m0, float m1, long long M0, long long M1,
                                  void* rho_c, void* rho_f, bool fixed, cudaStream_t st);

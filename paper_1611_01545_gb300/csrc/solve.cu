@@ -532,17 +532,24 @@ __global__ void __launch_bounds__(SolveCfg<N>::threads, PM_SOLVE_A_MINB)
   }
 }
 
+// Threads and resident blocks per SM of the TMA pass B (compile-time tunables).
+#ifndef PM_PASSB_TMA_THREADS
+#define PM_PASSB_TMA_THREADS 256
+#endif
+#ifndef PM_PASSB_TMA_MINB
+#define PM_PASSB_TMA_MINB 3
+#endif
 template <int N> struct PassBT {
   static constexpr int NH = N / 2 + 1, NP = spec_pitch(N);
   static constexpr int KT = 26;                        // kx columns per block: KT * 8 bytes is a multiple of 16
   static constexpr int nchunk = (NH + KT - 1) / KT;
-  static constexpr int threads = 256;
+  static constexpr int threads = PM_PASSB_TMA_THREADS;
   // G [3][N][KT] (component, z, column), twiddles
   static constexpr size_t smem = kTmaAlign + sizeof(float2) * (3 * (size_t)N * KT + N);
 };
 
 template <int N>
-__global__ void __launch_bounds__(PassBT<N>::threads, 3)
+__global__ void __launch_bounds__(PassBT<N>::threads, PM_PASSB_TMA_MINB)
     k_solve_b_tma(SolveArgs a, const __grid_constant__ CUtensorMap spec_map,
                   const __grid_constant__ CUtensorMap spec3_map) {
   using B = PassBT<N>;
@@ -634,8 +641,11 @@ template <int N> struct PassCT {
   static constexpr size_t smem = kTmaAlign + sizeof(float2) * ((size_t)N * spec_pitch(N) + (size_t)N / 2 * N + N);
 };
 
+#ifndef PM_SOLVE_C_MINB
+#define PM_SOLVE_C_MINB 1
+#endif
 template <int N>
-__global__ void __launch_bounds__(SolveCfg<N>::threads_c) k_solve_c_tma(SolveArgs a) {
+__global__ void __launch_bounds__(SolveCfg<N>::threads_c, PM_SOLVE_C_MINB) k_solve_c_tma(SolveArgs a) {
   constexpr int NP = SolveCfg<N>::NP;
   extern __shared__ unsigned char smraw_c[];
   __shared__ uint64_t bar;

@@ -329,6 +329,13 @@ class PM:
         arr_out = (pm_codes_t * 2)(codes_out[0].struct(), codes_out[1].struct())
         self._err(self.lib.pm_step_packed(self.h, arr_in, arr_out, c_kick, c_drift, _stream(stream)))
 
+    def step_packed_async(self, codes_in: Sequence[Codes], codes_out: Sequence[Codes], c_kick: float,
+                          c_drift: float, stream=None):
+        """pm_step_packed_async: queues copies and step; out is complete after check()."""
+        arr_in = (pm_codes_t * 2)(codes_in[0].struct(), codes_in[1].struct())
+        arr_out = (pm_codes_t * 2)(codes_out[0].struct(), codes_out[1].struct())
+        self._err(self.lib.pm_step_packed_async(self.h, arr_in, arr_out, c_kick, c_drift, _stream(stream)))
+
     def set_timing(self, on: bool):
         self._err(self.lib.pm_set_timing(self.h, 1 if on else 0))
 

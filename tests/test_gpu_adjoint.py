@@ -154,3 +154,64 @@ def test_trajectory_gradient_matches_central_differences_gpu():
         scale = float((g * d.double()).abs().sum())
         assert abs(fd - an) <= 2e-2 * scale, (k, fd, an, scale)
     pm.check()
+
+
+def _golden_diff128():
+    """The float64 oracle's gradient of the 128^3 differentiable workload
+    (tests/golden/diff128_gradient.txt, written by make_diff128_gradient.py
+    beside it, which calls only oracle/) and that script's input recipe."""
+    import importlib.util
+    import os
+    here = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+    spec = importlib.util.spec_from_file_location("make_diff128_gradient",
+                                                  os.path.join(here, "make_diff128_gradient.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    rec = {"sample": [], "proj": []}
+    with open(os.path.join(here, "diff128_gradient.txt")) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            key, *vals = line.split()
+            if key in ("sample", "proj"):
+                rec[key].append([float(v) for v in vals])
+            else:
+                rec[key] = float(vals[0])
+    return mod, rec
+
+
+def test_diff128_gradient_matches_oracle():
+    """The differentiable workload at its own shape: 128^3 mesh, 64^3 CDM +
+    128^3 neutrinos, 10 steps, checkpoints every 2 steps.  The GPU loss and
+    gradient (float32, fixed-point deposits) against the float64 oracle's:
+    the loss, 1024 sampled gradient components, and the projections of the
+    whole gradient on four random directions (relative to sum |g_i d_i|).
+    Over ten 128^3 steps the gradient is ill conditioned at the scale of
+    float32 rounding (CIC gradients change at cell faces): the tolerance is
+    three times the relative change of the oracle's own gradient when every
+    start coordinate moves by 1e-5 cells (stored beside the gradient), and
+    at least the 1e-3 of the small trajectories."""
+    from paper_1611_01545_gb300.diff import trajectory_loss
+    mod, rec = _golden_diff128()
+    cfg, q, psi, x_nu, v_nu, target = mod.diff128_inputs()
+    assert int(rec["steps"]) == mod.STEPS
+    pm = _pm(cfg)
+    psi_t = torch.from_numpy(psi).cuda().requires_grad_(True)
+    L = trajectory_loss(pm, psi_t, torch.from_numpy(q).cuda(), torch.from_numpy(x_nu).cuda(),
+                        torch.from_numpy(v_nu).cuda(), torch.from_numpy(target).cuda(), mod.BETA, mod.STEPS,
+                        mod.EVERY, mod.C_KICK, mod.C_DRIFT)
+    L.backward()
+    pm.check()
+    assert abs(float(L.detach()) - rec["loss"]) <= 1e-4 * rec["loss"]
+    g = psi_t.grad.double().cpu().numpy()
+    sample = np.array(rec["sample"])
+    idx = sample[:, 0].astype(np.int64)
+    np.testing.assert_array_equal(idx, mod.sample_index())
+    tol = max(ADJ_TOL, 3.0 * rec["sensitivity"])
+    err = rel_rms(g[idx], sample[:, 1:])
+    print(f"diff128 gradient: sampled relative RMS {err:.2e} (oracle sensitivity {rec['sensitivity']:.2e}, "
+          f"tolerance {tol:.2e})")
+    assert err < tol
+    for (k, proj, scale), d in zip(rec["proj"], mod.directions()):
+        got = float(np.sum(g * d))
+        assert abs(got - proj) <= tol * scale, (k, got, proj, scale)
