@@ -175,13 +175,14 @@ def csrc_digest():
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(kind, workload, particles):
+def recorded_traffic(kind, workload, particles, vel_bits):
     """DRAM bytes (read + write) per launch of a kernel kind from the committed
     ncu record (profiles/traffic.json), or None when the kernels changed since
-    that capture.  A record taken on a smaller workload of the same recipe is
-    scaled to this one by the particles processed (the particle passes move a
-    fixed number of bytes per particle plus per-cell tables that grow with
-    the mesh, i.e. in the same proportion for these workloads)."""
+    that capture.  A record taken on a smaller workload of the same recipe and
+    velocity width is scaled to this one by the particles processed (the
+    particle passes move a fixed number of bytes per particle plus per-cell
+    tables that grow with the mesh, i.e. in the same proportion for these
+    workloads, which all hold 1.125 particles per fine cell)."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         rec = json.load(open(path))
@@ -194,7 +195,7 @@ def recorded_traffic(kind, workload, particles):
             continue
         if e.get("workload") == workload:
             return {"bytes": int(e["bytes_per_launch"]), "captured_on": workload, "scaled": False}
-        if e.get("scale") == "particles" and e.get("particles"):
+        if e.get("scale") == "particles" and e.get("particles") and e.get("vel_bits") == vel_bits:
             best = {"bytes": int(round(e["bytes_per_launch"] * particles / e["particles"])),
                     "captured_on": e["workload"], "scaled": True}
     return best
@@ -319,11 +320,12 @@ def plain_step_ms(pm, w, codes, spare, torch, stream, steps: int) -> float:
 
 # Launch tuning of the largest workload: the shapes the autotuner picks on
 # the 256^3 workload of the same recipe (persistent 32x2x1-cell deposit
-# blocks, 64x1x1 kick blocks with a new-cell window half-width of 1), 64
-# tiles per solve batch.  The autotuner itself would spend minutes at this
-# size (each candidate is timed on whole steps).
+# blocks, 64x1x1 kick blocks with a new-cell window half-width of 1), and 256
+# tiles per solve batch (measured: 8, 16, 32, 64, 128, 256 tiles per batch
+# gave 392, 376, 365, 358, 355, 353 ms per step).  The autotuner itself would
+# spend minutes at this size (each candidate is timed on whole steps).
 LARGEST_TUNING = {"deposit_block": [32, 2, 1], "deposit_persistent": 1, "kick_block": [64, 1, 1],
-                  "kick_window": 1, "kick_persistent": 0, "tile_batch": 64}
+                  "kick_window": 1, "kick_persistent": 0, "tile_batch": 256}
 
 
 def measured_hbm():
@@ -336,7 +338,7 @@ def measured_hbm():
     return (float(hbm), "measured") if hbm else (6800.0, "fallback")
 
 
-def kernel_roofline(stages, alg, workload, particles):
+def kernel_roofline(stages, alg, workload, particles, vel_bits):
     """Roofline of the dominant kernel kind (largest total time among the kinds
     with an algorithmic byte model): algorithmic bytes per launch / its mean
     CUDA-event launch duration, against the HBM copy peak."""
@@ -349,7 +351,7 @@ def kernel_roofline(stages, alg, workload, particles):
         return None
     avg_ms = stages[dom][0]
     achieved = alg[dom] / (avg_ms / 1e3) / 1e9
-    tr = recorded_traffic(dom, workload, particles)
+    tr = recorded_traffic(dom, workload, particles, vel_bits)
     return {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": hbm, "peak_source": src,
             "unit": "GB/s", "frac": round(achieved / hbm, 4), "traffic": tr["bytes"] if tr else None,
             "traffic_source": tr, "alg_bytes_per_launch": alg[dom], "avg_launch_ms": round(avg_ms, 5),
@@ -571,7 +573,7 @@ def run_largest(args):
     alg = algorithmic_bytes(dict(cfg, tile_batch=tuning["tile_batch"]), counts, cfg["vel_bits"])
     e2e = None
     if not args.no_e2e:
-        e2e = e2e_packed(pm, a, b, torch, max(1, min(args.steps, 3)), world, dist, n_total)
+        e2e = e2e_packed(pm, a, b, torch, max(1, min(args.steps, 5)), world, dist, n_total)
     result = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
@@ -581,7 +583,7 @@ def run_largest(args):
                    "vel_bits": 16, "vmax_mode": args.vmax_mode, "global_batch": n_total * world,
                    "parallelism": f"replicas{world}", "l2": "inputs larger than L2: 49 GB of codes, 58 GB of meshes"},
         "e2e": e2e, "gpu_launches": int(launches),
-        "roofline": kernel_roofline(stages, alg, "largest1536", n_total),
+        "roofline": kernel_roofline(stages, alg, "largest1536", n_total, cfg["vel_bits"]),
         "step_roofline": step_roofline(step_model_bytes(cfg, counts, cfg["vel_bits"]), step_ms),
         "tuning": tuning,
         "stages_ms": {k: round(v[0], 4) for k, v in stages.items()},
@@ -707,7 +709,7 @@ def run_workload(args, workload, adjoint=True, cpu=True):
                    "l2": "working set > L2 (126 MB): codes + meshes > 400 MB per step"},
         "e2e": e2e,
         "gpu_launches": int(launches),
-        "roofline": kernel_roofline(stages, alg, workload, n_total),
+        "roofline": kernel_roofline(stages, alg, workload, n_total, w.vel_bits),
         "step_roofline": step_roofline(step_model_bytes(cfg, counts, w.vel_bits), step_ms),
         "tuning": tuning,
         "launch_forms": {"graph_ms_per_step": round(step_ms, 5),

@@ -56,6 +56,11 @@ extern "C" {
 typedef struct pm_handle pm_handle_t;
 
 /* Problem statement (Sec. 2.1): meshes, tiles, species and the split.
+ * Lengths are fine-mesh cells throughout, so the box is n_fine cells on a
+ * side and there is no separate box length: a caller with a box of side L
+ * passes positions x n_fine / L, velocities v n_fine / L (per unit of the
+ * time variable of c_kick and c_drift) and G (n_fine / L)^3 (mass units
+ * unchanged), and scales the results back.
  *  n_fine        fine-mesh cells per side; positions live on [0, n_fine).
  *  coarse_ratio  fine cells per coarse cell (the paper uses 4: the short-
  *                range mesh is 4x finer than the long-range one).  1 selects

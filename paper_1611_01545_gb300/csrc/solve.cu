@@ -642,7 +642,7 @@ template <int N> struct PassCT {
 };
 
 #ifndef PM_SOLVE_C_MINB
-#define PM_SOLVE_C_MINB 1
+#define PM_SOLVE_C_MINB 3
 #endif
 template <int N>
 __global__ void __launch_bounds__(SolveCfg<N>::threads_c, PM_SOLVE_C_MINB) k_solve_c_tma(SolveArgs a) {
