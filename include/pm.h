@@ -311,15 +311,19 @@ int pm_step_packed(pm_handle_t* h, const pm_host_codes_t in[2], pm_host_codes_t 
  * on a library stream, then unpacked there), the step on `stream`, and the
  * output copies (device -> host on a second library stream), and returns.
  * Consecutive calls overlap: a call's input copies start once the previous
- * step has read its input (after its count pass), and its count pass waits
- * for the previous step's output copies, so one step's output copies run
- * beside the next step's input copies, deposit and solve.  `out` is complete,
+ * step has read its input (after its count pass), and one step's output
+ * copies run beside the next step's input copies, deposit, solve and (when
+ * the device has room for a packed output buffer of its own, 9 or 6 bytes
+ * per particle, with 2 GB to spare) its count pass and scatter; without that
+ * room the packed output shares the step scratch and the next count pass
+ * waits for the copies.  `out` is complete,
  * and `in` may be changed, only after pm_check (which synchronises `stream`
  * and both library streams and reports the status); the host buffers must
  * stay valid until then, and a caller that reuses one `out` for several
  * calls keeps the last step's codes.  Needs device memory for one more
  * packed copy of the input (9 or 6 bytes per particle) beyond
- * pm_step_packed's.  Graph replay does not apply to this call. */
+ * pm_step_packed's, allocated on the first call.  Graph replay does not
+ * apply to this call. */
 int pm_step_packed_async(pm_handle_t* h, const pm_host_codes_t in[2], pm_host_codes_t out[2], double c_kick,
                          double c_drift, void* stream);
 

@@ -71,9 +71,14 @@ struct pm_handle {
   // compute; separate packed input buffers (the output ones sit in the scratch)
   cudaStream_t d2h_stream = nullptr;
   cudaEvent_t as_in_free = nullptr, as_pos_ready = nullptr, as_vel_ready = nullptr, as_packed = nullptr,
-              as_out_done = nullptr;
+              as_meta_done = nullptr, as_out_done = nullptr;
   uint8_t* as_pos[2] = {nullptr, nullptr};
   uint8_t* as_vel[2] = {nullptr, nullptr};
+  // packed output buffers of their own when device memory allows; otherwise
+  // the output shares the step scratch and the next count pass waits for it
+  uint8_t* as_opos[2] = {nullptr, nullptr};
+  uint8_t* as_ovel[2] = {nullptr, nullptr};
+  bool as_sep = false;
   bool as_ready = false;
   cudaEvent_t pre_count_wait2 = nullptr;     // set only while an async packed step is being enqueued
   cudaEvent_t post_count_record = nullptr;   // recorded after the count pass (the staged input is read)
@@ -521,7 +526,8 @@ int pm_destroy(pm_handle_t* h) {
   if (h->pk_fork) cudaEventDestroy(h->pk_fork);
   if (h->pk_vel_ready) cudaEventDestroy(h->pk_vel_ready);
   if (h->d2h_stream) cudaStreamDestroy(h->d2h_stream);
-  for (cudaEvent_t e : {h->as_in_free, h->as_pos_ready, h->as_vel_ready, h->as_packed, h->as_out_done})
+  for (cudaEvent_t e : {h->as_in_free, h->as_pos_ready, h->as_vel_ready, h->as_packed, h->as_meta_done,
+                        h->as_out_done})
     if (e) cudaEventDestroy(e);
   if (h->side_stream) cudaStreamDestroy(h->side_stream);
   if (h->fork_ev) cudaEventDestroy(h->fork_ev);
@@ -1299,13 +1305,28 @@ int pm_step_packed_async(pm_handle_t* h, const pm_host_codes_t in[2], pm_host_co
       CK(h, dalloc(h, &h->as_pos[s], 3 * n + 16));
       CK(h, dalloc(h, &h->as_vel[s], vbytes * n + 16));
     }
+    // separate packed output buffers when they fit with 2 GB to spare
+    // (otherwise the output shares the step scratch)
+    size_t need = 0, free_b = 0, total_b = 0;
+    for (int s = 0; s < 2; ++s) need += (3 + vbytes) * (size_t)h->stage_in[s].n + 512;
+    CK(h, cudaMemGetInfo(&free_b, &total_b));
+    h->as_sep = free_b > need + ((size_t)2 << 30);
+    for (int s = 0; s < 2 && h->as_sep; ++s) {
+      const size_t n = (size_t)h->stage_in[s].n;
+      CK(h, dalloc(h, &h->as_opos[s], 3 * n + 16));
+      CK(h, dalloc(h, &h->as_ovel[s], vbytes * n + 16));
+    }
     CK(h, cudaStreamCreateWithFlags(&h->d2h_stream, cudaStreamNonBlocking));
-    for (cudaEvent_t* e : {&h->as_in_free, &h->as_pos_ready, &h->as_vel_ready, &h->as_packed, &h->as_out_done})
+    for (cudaEvent_t* e : {&h->as_in_free, &h->as_pos_ready, &h->as_vel_ready, &h->as_packed, &h->as_meta_done,
+                           &h->as_out_done})
       CK(h, cudaEventCreateWithFlags(e, cudaEventDisableTiming));
     CK(h, cudaEventRecord(h->as_in_free, st));
+    CK(h, cudaEventRecord(h->as_meta_done, h->d2h_stream));
     CK(h, cudaEventRecord(h->as_out_done, h->d2h_stream));
     h->as_ready = true;
   }
+  uint8_t* const* opos = h->as_sep ? h->as_opos : h->pk_pos[1];
+  uint8_t* const* ovel = h->as_sep ? h->as_ovel : h->pk_vel[1];
   // input copies and unpacking, once the previous step's count pass has read its input
   CK(h, cudaStreamWaitEvent(h->copy_stream, h->as_in_free, 0));
   for (int s = 0; s < 2; ++s) {
@@ -1323,27 +1344,32 @@ int pm_step_packed_async(pm_handle_t* h, const pm_host_codes_t in[2], pm_host_co
     CK(h, launch_unpack(nullptr, h->as_vel[s], vel16, n, nullptr, h->stage_in[s].vel, h->copy_stream));
   }
   CK(h, cudaEventRecord(h->as_vel_ready, h->copy_stream));
-  // the step: positions first; velocities and the previous step's output copies before the count pass
+  // the step: positions first; velocities, and the previous step's output
+  // copies out of what this step overwrites, before the count pass (its
+  // counts and v_max always; its packed records too when they share the
+  // step scratch)
   CK(h, cudaStreamWaitEvent(st, h->as_pos_ready, 0));
   h->pre_count_wait = h->as_vel_ready;
-  h->pre_count_wait2 = h->as_out_done;
+  h->pre_count_wait2 = h->as_sep ? h->as_meta_done : h->as_out_done;
   h->post_count_record = h->as_in_free;
   const int r = step_launch(h, h->stage_in, h->stage_out, c_kick, c_drift, st);
   h->pre_count_wait = h->pre_count_wait2 = h->post_count_record = nullptr;
   if (r != PM_OK) return r;
+  if (h->as_sep) CK(h, cudaStreamWaitEvent(st, h->as_out_done, 0));   // previous packed output copied out
   for (int s = 0; s < 2; ++s)
     CK(h, launch_pack(reinterpret_cast<const uint32_t*>(h->stage_out[s].pos), h->stage_out[s].vel, vel16,
-                      in[s].n, h->pk_pos[1][s], h->pk_vel[1][s], st));
+                      in[s].n, opos[s], ovel[s], st));
   CK(h, cudaEventRecord(h->as_packed, st));
-  // output copies
+  // output copies: counts, escapes and v_max first (the next step rewrites them)
   CK(h, cudaStreamWaitEvent(h->d2h_stream, h->as_packed, 0));
+  for (int s = 0; s < 2; ++s)
+    if (int r2 = copy_meta(h, out[s], h->stage_out[s], ncell, cudaMemcpyDeviceToHost, h->d2h_stream)) return r2;
+  CK(h, cudaEventRecord(h->as_meta_done, h->d2h_stream));
   for (int s = 0; s < 2; ++s) {
     const int64_t n = in[s].n;
-    if (int r2 = copy_meta(h, out[s], h->stage_out[s], ncell, cudaMemcpyDeviceToHost, h->d2h_stream)) return r2;
     if (n > 0) {
-      CK(h, cudaMemcpyAsync(out[s].pos, h->pk_pos[1][s], (size_t)n * 3, cudaMemcpyDeviceToHost, h->d2h_stream));
-      CK(h, cudaMemcpyAsync(out[s].vel, h->pk_vel[1][s], (size_t)n * vbytes, cudaMemcpyDeviceToHost,
-                            h->d2h_stream));
+      CK(h, cudaMemcpyAsync(out[s].pos, opos[s], (size_t)n * 3, cudaMemcpyDeviceToHost, h->d2h_stream));
+      CK(h, cudaMemcpyAsync(out[s].vel, ovel[s], (size_t)n * vbytes, cudaMemcpyDeviceToHost, h->d2h_stream));
     }
   }
   CK(h, cudaEventRecord(h->as_out_done, h->d2h_stream));

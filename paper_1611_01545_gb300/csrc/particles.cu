@@ -1089,6 +1089,26 @@ __device__ __forceinline__ int window_slot_xyz(const Win& w, int n, int cx, int 
 // cell lies in the block's window, else the new cell index itself.
 constexpr uint32_t kInWindow = 0x80000000u;
 
+// Per-particle scratch record of the two recompress passes (stream index t
+// of ntot particles, both species).  Exact v_max' mode: one 16-byte record
+// {new position word, v'_x, v'_y, v'_z as float bits}.  Bound mode (codes
+// final in the count pass): 8-bit codes as one 8-byte record {position
+// word, velocity word}; 16-bit codes as a 4-byte position word and, in a
+// second array after the first (16-byte aligned), an 8-byte velocity word.
+__device__ __forceinline__ unsigned long long* coded_vel16(uint4* tpv, int64_t ntot) {
+  return reinterpret_cast<unsigned long long*>(reinterpret_cast<unsigned char*>(tpv) + ((4 * ntot + 15) & ~15ll));
+}
+__device__ __forceinline__ uint4 load_record(const uint4* tpv, int64_t t, int coded, bool vel16, int64_t ntot) {
+  if (!coded) return tpv[t];
+  if (!vel16) {
+    const uint2 r = reinterpret_cast<const uint2*>(tpv)[t];
+    return make_uint4(r.x, r.y, 0u, 0u);
+  }
+  const uint32_t pw = reinterpret_cast<const uint32_t*>(tpv)[t];
+  const unsigned long long v = coded_vel16(const_cast<uint4*>(tpv), ntot)[t];
+  return make_uint4(pw, (uint32_t)v, (uint32_t)(v >> 32), 0u);
+}
+
 // Cell index of window row r = lz wy + ly at x = 0 (add window_x for the column).
 __device__ __forceinline__ uint32_t window_row(const Geo& g, const Win& w, int r) {
   const int n = g.ncmp;
@@ -1268,8 +1288,14 @@ __global__ void __launch_bounds__(PM_IKD_THREADS, PM_IKD_MIN_BLOCKS) k_ikd_count
             int c3[3];
 #pragma unroll
             for (int d = 0; d < 3; ++d) c3[d] = encode_vel(v[d], qs, half, qzero);
-            tpv[t] = in.vel16 ? make_uint4(pw, (uint32_t)c3[0] | ((uint32_t)c3[1] << 16), (uint32_t)c3[2], 0u)
-                              : make_uint4(pw, (uint32_t)c3[0] | ((uint32_t)c3[1] << 8) | ((uint32_t)c3[2] << 16), 0u, 0u);
+            if (in.vel16) {
+              reinterpret_cast<uint32_t*>(tpv)[t] = pw;
+              coded_vel16(tpv, c0.n + c1.n)[t] = (unsigned long long)((uint32_t)c3[0] | ((uint32_t)c3[1] << 16)) |
+                                                 ((unsigned long long)c3[2] << 32);
+            } else {
+              reinterpret_cast<uint2*>(tpv)[t] =
+                  make_uint2(pw, (uint32_t)c3[0] | ((uint32_t)c3[1] << 8) | ((uint32_t)c3[2] << 16));
+            }
           } else {
             tpv[t] = make_uint4(pw, __float_as_uint(v[0]), __float_as_uint(v[1]), __float_as_uint(v[2]));
             local_max = fmaxf(local_max, fmaxf(fabsf(v[0]), fmaxf(fabsf(v[1]), fabsf(v[2]))));
@@ -1399,7 +1425,7 @@ __global__ void __launch_bounds__(PM_SCATTER_THREADS, PM_SCATTER_MIN_BLOCKS) k_i
             pp[u] = p + u * (int64_t)blockDim.x;
             if (pp[u] < p1) {
               tk[u] = tkey[toff + pp[u]];
-              pv[u] = tpv[toff + pp[u]];
+              pv[u] = load_record(tpv, toff + pp[u], coded, o.vel16, n0 + n1);
             }
           }
 #pragma unroll
@@ -1407,11 +1433,9 @@ __global__ void __launch_bounds__(PM_SCATTER_THREADS, PM_SCATTER_MIN_BLOCKS) k_i
             if (pp[u] >= p1) continue;
             int64_t dst;
             if (tk[u] & kInWindow) {
-              {
               // rank within the block's range of the cell: count its histogram entry down
               const uint32_t sl = s * W + (tk[u] & ~kInWindow);
               dst = (int64_t)base[sl] + (int64_t)atomicSub(hist + sl, 1u) - 1;
-            }
             } else {
               const uint32_t top = atomicSub(counts + tk[u], 1u);
               dst = newoff[tk[u]] + (int64_t)top - 1;

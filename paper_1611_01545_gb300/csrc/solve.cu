@@ -343,31 +343,60 @@ __device__ __forceinline__ void solve_c_body(const SolveArgs& a, float2* tw, flo
   const int pb = blockIdx.z;
   fft_inv<N, NH, 1, NP>(P, tw);
   const int half_rows = a.t / 2;
-  PM_ROWS(j, half_rows) {
-    const float2* Pa = P + (a.b + 2 * j) * NP;
-    const float2* Pb = Pa + NP;
-    float2* Wj = W + j * N;
-    PM_COLS(k, N) {
-      float2 A, B;
-      if (k <= N / 2) {
-        A = Pa[k];
-        B = Pb[k];
-      } else {
-        A = conjf2(Pa[N - k]);
-        B = conjf2(Pb[N - k]);
+  // Inverse x transforms of the output rows, two real rows (b + 2j, b + 2j + 1)
+  // packed as one complex row A + i B (A, B their half spectra, extended by
+  // conjugate symmetry).  Step 1 forms its inputs from P directly: slot
+  // N2 k1 + k2 holds frequency k = k1 + N1 k2.
+  {
+    constexpr int N1 = Factor<N>::N1, N2 = Factor<N>::N2;
+    for (int w = threadIdx.x; w < half_rows * N1; w += blockDim.x) {
+      const int j = w / N1, k1 = w - j * N1;
+      const float2* Pa = P + (a.b + 2 * j) * NP;
+      const float2* Pb = Pa + NP;
+      float2 v[N2];
+#pragma unroll
+      for (int k2 = 0; k2 < N2; ++k2) {
+        const int k = k1 + N1 * k2;
+        float2 A, B;
+        if (k <= N / 2) {
+          A = Pa[k];
+          B = Pb[k];
+        } else {
+          A = conjf2(Pa[N - k]);
+          B = conjf2(Pb[N - k]);
+        }
+        v[k2] = make_float2(A.x - B.y, A.y + B.x);   // A + i B
       }
-      Wj[slot_of<N>(k)] = make_float2(A.x - B.y, A.y + B.x);   // A + i B
+      Dft<N2, 1>::run(v);
+#pragma unroll
+      for (int j2 = 1; j2 < N2; ++j2) v[j2] = cmul(v[j2], conjf2(tw[j2 * k1]));
+      float2* base = W + j * N;
+#pragma unroll
+      for (int j2 = 0; j2 < N2; ++j2) base[N2 * k1 + j2] = v[j2];
     }
+    __syncthreads();
+    for (int w = threadIdx.x; w < half_rows * N2; w += blockDim.x) {
+      const int q = w / N2, j2 = w - q * N2;
+      float2* base = W + q * N;
+      float2 v[N1];
+#pragma unroll
+      for (int k1 = 0; k1 < N1; ++k1) v[k1] = base[N2 * k1 + j2];
+      Dft<N1, 1>::run(v);
+#pragma unroll
+      for (int j1 = 0; j1 < N1; ++j1) base[N2 * j1 + j2] = v[j1];
+    }
+    __syncthreads();
   }
-  __syncthreads();
-  fft_inv_rows<N, N>(W, half_rows, tw);
   int ox, oy, oz;
   problem_origin(a, a.p0 + pb, ox, oy, oz);
   const int n = a.src_n;
   // Prolongation of the coarse force onto this output plane: the coarse values
-  // around the tile interior, interpolated in z, staged in P (free by now).
+  // around the tile interior, interpolated in z, staged in P (free by now),
+  // then along x onto the output columns (R), so an output cell needs one
+  // interpolation in y.
   float* Q = reinterpret_cast<float*>(P);
   const int nq = a.pc ? a.t / a.prc + 1 : 0;
+  float* R = Q + nq * nq;   // [nq][t]
   int lr = 0;
   float inv_r = 0.f;
   if (a.pc) {
@@ -390,6 +419,15 @@ __device__ __forceinline__ void solve_c_body(const SolveArgs& a, float2* tw, flo
       }
     }
     __syncthreads();
+    PM_ROWS(qy, nq) {
+      const float* q = Q + qy * nq;
+      PM_COLS(xl, a.t) {
+        const int qx = xl >> lr;
+        const float fx = (float)(xl & (a.prc - 1)) * inv_r;
+        R[qy * a.t + xl] = fmaf(fx, q[qx + 1] - q[qx], q[qx]);
+      }
+    }
+    __syncthreads();
   }
   // Output cells are interior cells: origin + b + local lies inside [0, n) without wrap.
   const int gz = oz + a.b + zo;
@@ -402,10 +440,9 @@ __device__ __forceinline__ void solve_c_body(const SolveArgs& a, float2* tw, flo
       float val = w[2 * xl];
       m = fmaxf(m, fabsf(val));
       if (a.pc) {
-        const int qy = yl >> lr, qx = xl >> lr;
-        const float fy = (float)(yl & (a.prc - 1)) * inv_r, fx = (float)(xl & (a.prc - 1)) * inv_r;
-        const float* q = Q + qy * nq + qx;
-        const float lo = fmaf(fx, q[1] - q[0], q[0]), hi = fmaf(fx, q[nq + 1] - q[nq], q[nq]);
+        const int qy = yl >> lr;
+        const float fy = (float)(yl & (a.prc - 1)) * inv_r;
+        const float lo = R[qy * a.t + xl], hi = R[(qy + 1) * a.t + xl];
         val += fmaf(fy, hi - lo, lo);
       }
       drow[xl] = val;
