@@ -1327,22 +1327,29 @@ int pm_step_packed_async(pm_handle_t* h, const pm_host_codes_t in[2], pm_host_co
   }
   uint8_t* const* opos = h->as_sep ? h->as_opos : h->pk_pos[1];
   uint8_t* const* ovel = h->as_sep ? h->as_ovel : h->pk_vel[1];
-  // input copies and unpacking, once the previous step's count pass has read its input
-  CK(h, cudaStreamWaitEvent(h->copy_stream, h->as_in_free, 0));
+  // input record copies into the packed staging, which the previous call's
+  // unpacking (earlier on the same stream) has finished reading: they run
+  // beside the whole previous step
   for (int s = 0; s < 2; ++s) {
     const int64_t n = in[s].n;
-    if (int r = copy_meta(h, h->stage_in[s], in[s], ncell, cudaMemcpyHostToDevice, h->copy_stream)) return r;
     if (n > 0) CK(h, cudaMemcpyAsync(h->as_pos[s], in[s].pos, (size_t)n * 3, cudaMemcpyHostToDevice, h->copy_stream));
-    CK(h, launch_unpack(h->as_pos[s], nullptr, vel16, n, reinterpret_cast<uint32_t*>(h->stage_in[s].pos), nullptr,
-                        h->copy_stream));
   }
-  CK(h, cudaEventRecord(h->as_pos_ready, h->copy_stream));
   for (int s = 0; s < 2; ++s) {
     const int64_t n = in[s].n;
     if (n > 0)
       CK(h, cudaMemcpyAsync(h->as_vel[s], in[s].vel, (size_t)n * vbytes, cudaMemcpyHostToDevice, h->copy_stream));
-    CK(h, launch_unpack(nullptr, h->as_vel[s], vel16, n, nullptr, h->stage_in[s].vel, h->copy_stream));
   }
+  // counts, escapes, v_max and the unpacked codes, once the previous step's
+  // count pass has read its input (they run beside its scatter)
+  CK(h, cudaStreamWaitEvent(h->copy_stream, h->as_in_free, 0));
+  for (int s = 0; s < 2; ++s) {
+    if (int r = copy_meta(h, h->stage_in[s], in[s], ncell, cudaMemcpyHostToDevice, h->copy_stream)) return r;
+    CK(h, launch_unpack(h->as_pos[s], nullptr, vel16, in[s].n, reinterpret_cast<uint32_t*>(h->stage_in[s].pos),
+                        nullptr, h->copy_stream));
+  }
+  CK(h, cudaEventRecord(h->as_pos_ready, h->copy_stream));
+  for (int s = 0; s < 2; ++s)
+    CK(h, launch_unpack(nullptr, h->as_vel[s], vel16, in[s].n, nullptr, h->stage_in[s].vel, h->copy_stream));
   CK(h, cudaEventRecord(h->as_vel_ready, h->copy_stream));
   // the step: positions first; velocities, and the previous step's output
   // copies out of what this step overwrites, before the count pass (its
