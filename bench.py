@@ -573,7 +573,7 @@ def run_largest(args):
     alg = algorithmic_bytes(dict(cfg, tile_batch=tuning["tile_batch"]), counts, cfg["vel_bits"])
     e2e = None
     if not args.no_e2e:
-        e2e = e2e_packed(pm, a, b, torch, max(1, min(args.steps, 5)), world, dist, n_total)
+        e2e = e2e_packed(pm, a, b, torch, max(1, min(args.steps, 20)), world, dist, n_total)
     result = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
@@ -739,7 +739,7 @@ def small_e2e(pm, a, b, torch, steps, world, dist, n_total, vel_bits):
     """End to end on a workload whose host copies fit beside the device state:
     packed record bytes (pm_step_packed_async) and the padded in-memory words
     (pm_step_host), pinned host buffers, copies inside the timed region."""
-    k_e2e = max(1, min(steps, 10))
+    k_e2e = max(1, min(steps, 50))
 
     def e2e_run(fn, hin, hout):
         fn(hin, hout, 1.0, 1.0)           # first call allocates the library's staging buffers

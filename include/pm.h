@@ -76,7 +76,10 @@ typedef struct pm_handle pm_handle_t;
  *                bins on the coarse mesh: 4); a power of two.  In two-level
  *                mode it must equal coarse_ratio.
  *  vel_bits      16 (the paper's 2-byte velocities) or 8 (reduced precision).
- *  deposit_mode  0: float32 CIC with atomics; 1: int64 fixed point (mass in
+ *  deposit_mode  0: float32 CIC with atomics (the fused step bins each cell
+ *                block in 32-bit fixed point, scaled per block so that no
+ *                cell overflows, and adds the block to the float32 mesh);
+ *                1: int64 fixed point (mass in
  *                units of 2^-32, conservative integer split) -- bit-exact and
  *                independent of particle order.
  *  G             gravitational constant in these units.

@@ -605,6 +605,20 @@ __device__ __forceinline__ uint32_t take_rank(uint32_t* counts, uint32_t key) {
   return old - (unsigned)__popc(peers) + below;
 }
 
+// Block maximum of values m >= 0, returned to every thread.  Every thread of
+// the block must call it.
+__device__ __forceinline__ float block_max_all(float m) {
+  __shared__ float red[32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  __syncthreads();   // red may still be read by a previous call
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  float r = 0.f;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) r = fmaxf(r, red[w]);
+  return r;
+}
+
 // Block maximum of m into *vmax_bits (float bits of a value >= 0): one atomic
 // per block, and none when the block's maximum does not exceed the current
 // value.  Every thread of the block must call it.
@@ -854,8 +868,9 @@ __device__ __forceinline__ void corner_masses(float, long long M, const float w1
 }
 
 // Decode + deposit of both species for one cell block, binned in shared memory
-// (float32, or int64 in units of 2^-32 mass for the fixed-point mode) and
-// flushed once per cell.  smem: row offsets (2 species), fine region
+// (32-bit fixed point with a per-block power-of-two scale, converted to
+// float32 before the flush; or int64 in units of 2^-32 mass for the
+// fixed-point mode) and flushed once per cell.  smem: row offsets (2 species), fine region
 // (RX r + 1)(RY r + 1)(RZ r + 1), coarse region (RX + 1)(RY + 1)(RZ + 1).
 // Threads per CTA of the deposit.
 #ifndef PM_DEPOSIT_THREADS
@@ -901,6 +916,32 @@ __global__ void PM_DEPOSIT_BOUNDS k_deposit_codes(PCodes c0, PCodes c1, const in
     load_row_offsets(off0, g, bk, cb, roff);
     load_row_offsets(off1, g, bk, cb, roff + nrow * (bk.RX + 1));
     __syncthreads();
+    // Float mode: the block bins its corner masses in 32-bit fixed point
+    // (integer shared-memory atomics, several times the rate of float ones,
+    // and independent of the order of the adds) with a power-of-two scale S.
+    // A fine node receives mass only from particles of the (at most 8)
+    // compression cells around it, so 8 x the block's heaviest compression
+    // cell bounds every node's total; S = 2^floor(log2(2^31 / bound)) keeps
+    // the scaled total below 2^31, and the corner roundings below 2^31 more.
+    float S = 1.f;
+    if constexpr (sizeof(Acc) == 4) {
+      float cm = 0.f;
+      const int nrx = bk.RX + 1, ncells = nrow * bk.RX;
+      for (int i = threadIdx.x; i < ncells; i += blockDim.x) {
+        const int row = i / bk.RX, k = i - row * bk.RX;
+        const int64_t* r0 = roff + row * nrx + k;
+        const int64_t* r1 = r0 + nrow * nrx;
+        const int64_t a0 = r0[0] < c0.n ? r0[0] : c0.n, b0 = r0[1] < c0.n ? r0[1] : c0.n;
+        const int64_t a1 = r1[0] < c1.n ? r1[0] : c1.n, b1 = r1[1] < c1.n ? r1[1] : c1.n;
+        const float w = __fadd_ru(__fmul_ru((float)(b0 - a0), m0), __fmul_ru((float)(b1 - a1), m1));
+        cm = fmaxf(cm, w);
+      }
+      cm = block_max_all(cm);
+      if (cm > 0.f) {
+        const float x = fminf(__fdiv_rd(268435456.0f, cm), 1.329228e36f);   // 2^31 / (8 cm), at most 2^120
+        S = __uint_as_float(__float_as_uint(x) & 0xff800000u);
+      }
+    }
     const float pscale = (float)r / 256.0f;
     const int bxf = cb.ix0 * r, byf = cb.iy0 * r, bzf = cb.iz0 * r;
     for (int s = 0; s < 2; ++s) {
@@ -937,7 +978,11 @@ __global__ void PM_DEPOSIT_BOUNDS k_deposit_codes(PCodes c0, PCodes c1, const in
 #pragma unroll
             for (int c = 0; c < 8; ++c) {
               int dx = c & 1, dy = (c >> 1) & 1, dz = c >> 2;
-              smem_acc(&sf[((lz + dz) * fy + (ly + dy)) * fx + (lx + dx)], t8[c]);
+              const int idx = ((lz + dz) * fy + (ly + dy)) * fx + (lx + dx);
+              if constexpr (sizeof(Acc) == 4)
+                atomicAdd(reinterpret_cast<unsigned int*>(sf) + idx, __float2uint_rn(__fmul_rn((float)t8[c], S)));
+              else
+                smem_acc(&sf[idx], t8[c]);
             }
           }
           if (dep_coarse) {
@@ -968,6 +1013,13 @@ __global__ void PM_DEPOSIT_BOUNDS k_deposit_codes(PCodes c0, PCodes c1, const in
       }
     }
     __syncthreads();
+    if constexpr (sizeof(Acc) == 4) {
+      // fixed point -> float32 (S is a power of two: the scaling is exact)
+      const float inv_s = 1.0f / S;
+      const unsigned int* si = reinterpret_cast<const unsigned int*>(sf);
+      for (int i = threadIdx.x; i < nsf; i += blockDim.x) sf[i] = __fmul_rn(__uint2float_rn(si[i]), inv_s);
+      __syncthreads();
+    }
     const int nf = g.nf;
     // flush: one warp per region row (z, y), lanes along x
     for (int line = threadIdx.x >> 5; line < fy * fz; line += blockDim.x >> 5) {
