@@ -454,11 +454,11 @@ def e2e_packed(pm, codes, spare, torch, steps, world, dist, n_total):
     torch.cuda.empty_cache()
     hout = [empty_pinned_packed(pm, n, cap, torch) for n, cap in ncodes]
     setup_s = time.perf_counter() - t0
-    el, form = packed_steps(pm, hin, hout, steps, world, dist)
+    el, form, gaps = packed_steps(pm, hin, hout, steps, world, dist)
     value, worst = job_rate(el, n_total * steps, world, "cuda", dist)
     nbytes = sum(codes_bytes(c, pm.vel_bits, packed=True) for c in hin)
     return {"value": value, "unit": UNIT, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
-            "steps": steps, "ms_per_step": round(worst / steps * 1e3, 3),
+            "steps": steps, "ms_per_step": round(worst / steps * 1e3, 3), **gap_summary(gaps),
             "host_form": f"packed record bytes in pinned host memory ({form})",
             "setup_s": round(setup_s, 1)}
 
@@ -484,16 +484,30 @@ def packed_steps(pm, hin, hout, steps, world, dist):
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
+    st = torch.cuda.current_stream()
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
     t0 = time.perf_counter()
-    for _ in range(steps):
+    ends[0].record(st)
+    for i in range(steps):
         if form == "pm_step_packed_async":
             pm.step_packed_async(hin, hout, 1.0, 1.0)
         else:
             pm.step_packed(hin, hout, 1.0, 1.0)   # ends with pm_check
+        ends[i + 1].record(st)
     pm.check()
     el = time.perf_counter() - t0
     pm.set_graphs(False)
-    return el, form
+    # time between the ends of consecutive steps' kernels on the step stream:
+    # the first includes the pipeline fill (its whole input copy)
+    gaps = [ends[i].elapsed_time(ends[i + 1]) for i in range(steps)]
+    return el, form, gaps
+
+
+def gap_summary(gaps):
+    """First-step and steady-state (median of the rest) step intervals, ms."""
+    rest = sorted(gaps[1:])
+    return {"first_step_ms": round(gaps[0], 2),
+            "steady_ms_per_step": round(rest[len(rest) // 2], 2) if rest else None}
 
 
 def run_largest(args):
@@ -753,7 +767,7 @@ def small_e2e(pm, a, b, torch, steps, world, dist, n_total, vel_bits):
 
     pk_in = [to_pinned(pm.pack(c), torch) for c in a]
     pk_out = [to_pinned(pm.pack(c), torch) for c in b]
-    e2e_s, e2e_form = packed_steps(pm, pk_in, pk_out, k_e2e, world, dist)
+    e2e_s, e2e_form, _ = packed_steps(pm, pk_in, pk_out, k_e2e, world, dist)
     pm.set_graphs(True)
     pad_s = e2e_run(pm.step_host, [to_pinned(c, torch) for c in a], [to_pinned(c, torch) for c in b])
     pm.set_graphs(False)
