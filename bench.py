@@ -193,7 +193,7 @@ def recorded_traffic(kind, workload, particles, vel_bits):
     for e in rec.get("entries", []):
         if e.get("kind") != kind or e.get("csrc") != digest:
             continue
-        if e.get("workload") == workload:
+        if e.get("workload") == workload and e.get("vel_bits") == vel_bits:
             return {"bytes": int(e["bytes_per_launch"]), "captured_on": workload, "scaled": False}
         if e.get("scale") == "particles" and e.get("particles") and e.get("vel_bits") == vel_bits:
             best = {"bytes": int(round(e["bytes_per_launch"] * particles / e["particles"])),
@@ -635,6 +635,8 @@ def run_workload(args, workload, adjoint=True, cpu=True):
     cfg = w.config()
     cfg["tile_batch"] = args.tile_batch
     cfg["vmax_mode"] = args.vmax_mode
+    vel_bits = args.vel_bits or w.vel_bits
+    cfg["vel_bits"] = vel_bits
     if args.pp:
         # Eq. 4 softening: 0.05 of the mean CDM inter-particle spacing, L / (20 n_p)
         n_p = round(w.counts[0] ** (1.0 / 3.0))
@@ -706,9 +708,9 @@ def run_workload(args, workload, adjoint=True, cpu=True):
     # in-memory form (pm_step_host)
     e2e = None
     if not args.no_e2e:
-        e2e = small_e2e(pm, a, b, torch, args.steps, world, dist, n_total, w.vel_bits)
+        e2e = small_e2e(pm, a, b, torch, args.steps, world, dist, n_total, vel_bits)
 
-    alg = algorithmic_bytes(dict(cfg, tile_batch=tuning["tile_batch"]), counts, w.vel_bits)
+    alg = algorithmic_bytes(dict(cfg, tile_batch=tuning["tile_batch"]), counts, vel_bits)
 
     step_ms = ms_max / args.steps
     result = {
@@ -718,13 +720,13 @@ def run_workload(args, workload, adjoint=True, cpu=True):
         "config": {"workload": workload, "n_fine": w.n_fine, "coarse_ratio": w.coarse_ratio,
                    "tile": w.tile, "buffer": w.buffer, "tile_batch": args.tile_batch,
                    "vmax_mode": args.vmax_mode, "pp": int(args.pp),
-                   "particles": {"cdm": counts[0], "nu": counts[1]}, "vel_bits": w.vel_bits,
+                   "particles": {"cdm": counts[0], "nu": counts[1]}, "vel_bits": vel_bits,
                    "global_batch": n_total * world, "parallelism": f"replicas{world}",
                    "l2": "working set > L2 (126 MB): codes + meshes > 400 MB per step"},
         "e2e": e2e,
         "gpu_launches": int(launches),
-        "roofline": kernel_roofline(stages, alg, workload, n_total, w.vel_bits),
-        "step_roofline": step_roofline(step_model_bytes(cfg, counts, w.vel_bits), step_ms),
+        "roofline": kernel_roofline(stages, alg, workload, n_total, vel_bits),
+        "step_roofline": step_roofline(step_model_bytes(cfg, counts, vel_bits), step_ms),
         "tuning": tuning,
         "launch_forms": {"graph_ms_per_step": round(step_ms, 5),
                          "direct_ms_per_step": round(direct_ms, 5),
@@ -1087,6 +1089,8 @@ def main():
     p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     p.add_argument("--workload", default="largest1536")
     p.add_argument("--tile-batch", type=int, default=0)
+    p.add_argument("--vel-bits", type=int, default=0, choices=[0, 8, 16],
+                   help="velocity code width (0: the workload's own); not for the largest workload")
     p.add_argument("--vmax-mode", type=int, default=0, choices=[0, 1],
                    help="0: exact v_max' (the paper's definition); 1: bound from the force meshes")
     p.add_argument("--no-cpu-baseline", action="store_true")
