@@ -162,13 +162,24 @@ def step_model_bytes(cfg, counts, vel_bits):
     return sum(counts) * per_particle + 40 * cells + kernels
 
 
-def csrc_digest():
-    """Digest of the CUDA sources; ncu traffic figures apply only to the sources they were taken on."""
+# CUDA sources that define each kernel kind (its code and its launcher)
+_PARTICLE_SOURCES = ("particles.cu", "particles.cuh", "pm_common.cuh")
+_SOLVE_SOURCES = ("solve.cu", "fft.cuh", "tma.cuh", "pm_common.cuh")
+KIND_SOURCES = {"deposit": _PARTICLE_SOURCES, "ikd_count": _PARTICLE_SOURCES, "ikd_scatter": _PARTICLE_SOURCES,
+                "fft_a_tiles": _SOLVE_SOURCES, "fft_b_tiles": _SOLVE_SOURCES, "fft_c_tiles": _SOLVE_SOURCES}
+
+
+def csrc_digest(kind=None):
+    """Digest of the CUDA sources of a kernel kind (all sources for kind None);
+    ncu traffic figures apply only to the sources they were taken on."""
     import glob
     import hashlib
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_1611_01545_gb300", "csrc")
-    for f in sorted(glob.glob(os.path.join(d, "*.cu")) + glob.glob(os.path.join(d, "*.cuh"))):
+    files = sorted(glob.glob(os.path.join(d, "*.cu")) + glob.glob(os.path.join(d, "*.cuh")))
+    if kind in KIND_SOURCES:
+        files = [f for f in files if os.path.basename(f) in KIND_SOURCES[kind]]
+    for f in files:
         h.update(os.path.basename(f).encode())
         with open(f, "rb") as fh:
             h.update(fh.read())
@@ -188,7 +199,7 @@ def recorded_traffic(kind, workload, particles, vel_bits):
         rec = json.load(open(path))
     except (OSError, ValueError):
         return None
-    digest = csrc_digest()
+    digest = csrc_digest(kind)
     best = None
     for e in rec.get("entries", []):
         if e.get("kind") != kind or e.get("csrc") != digest:

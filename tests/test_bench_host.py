@@ -15,7 +15,7 @@ def _record(tmp_path, entries):
 
 def test_recorded_traffic_lookup(tmp_path, monkeypatch):
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
-    monkeypatch.setattr(bench, "csrc_digest", lambda: "d1")
+    monkeypatch.setattr(bench, "csrc_digest", lambda kind=None: "d1")
     _record(tmp_path, [
         {"kind": "ikd_count", "workload": "w256", "vel_bits": 8, "particles": 100, "scale": "particles",
          "bytes_per_launch": 1000, "csrc": "d1"},
@@ -42,3 +42,12 @@ def test_gap_summary():
     s = bench.gap_summary([600.0, 380.0, 390.0, 370.0, 400.0])
     assert s == {"first_step_ms": 600.0, "steady_ms_per_step": 390.0}
     assert bench.gap_summary([5.0]) == {"first_step_ms": 5.0, "steady_ms_per_step": None}
+
+
+def test_kind_digests_cover_their_sources():
+    # every kernel kind of the traffic record has its own digest, and kinds
+    # built from the same sources share it
+    assert bench.csrc_digest("ikd_count") == bench.csrc_digest("deposit")
+    assert bench.csrc_digest("fft_a_tiles") == bench.csrc_digest("fft_c_tiles")
+    assert bench.csrc_digest("ikd_count") != bench.csrc_digest("fft_a_tiles")
+    assert bench.csrc_digest() not in (bench.csrc_digest("ikd_count"), bench.csrc_digest("fft_a_tiles"))
