@@ -1374,6 +1374,29 @@ __global__ void __launch_bounds__(PM_IKD_THREADS, PM_IKD_MIN_BLOCKS) k_ikd_count
   });
 }
 
+// Slot countdown of the in-window particles of a warp.  Consecutive lanes
+// with the same slot form a run (the particle stream is cell ordered and most
+// particles stay in their cell, so a warp's particles fall in one or two
+// runs); the run's first lane takes the run's slots with one atomic and
+// hands them out, since a shared-memory atomic whose lanes share an address
+// and return their values is serialised lane by lane.  All 32 lanes must
+// call it; lanes without a slot pass has = false and a slot of their own
+// (~0u - lane).  Returns what atomicSub(hist + slot, 1) would have returned.
+__device__ __forceinline__ uint32_t run_countdown(uint32_t* hist, uint32_t slot, bool has) {
+  const int lane = (int)(threadIdx.x & 31);
+  const uint32_t prev = __shfl_up_sync(0xffffffffu, slot, 1);
+  const bool head = lane == 0 || prev != slot;
+  const uint32_t heads = __ballot_sync(0xffffffffu, head);
+  const uint32_t upto = 0xffffffffu >> (31 - lane);   // lanes 0 .. lane
+  const int first = 31 - __clz(heads & upto);         // head of this lane's run
+  const uint32_t later = heads & ~upto;
+  const int end = later ? __ffs(later) - 1 : 32;       // head of the next run
+  uint32_t old = 0;
+  if (head && has) old = atomicSub(hist + slot, (uint32_t)(end - lane));
+  old = __shfl_sync(0xffffffffu, old, first);
+  return old - (uint32_t)(lane - first);
+}
+
 // Pass 2: place every particle of a cell block in its new cell.  Phase 1
 // histograms the block's new cells over its window; phase 2 reserves one
 // contiguous range per window cell from the cell's global cursor (counts,
@@ -1468,13 +1491,17 @@ __global__ void __launch_bounds__(PM_SCATTER_THREADS, PM_SCATTER_MIN_BLOCKS) k_i
         const int64_t p0 = ro[0] < n ? ro[0] : n, p1 = ro[bk.RX] < n ? ro[bk.RX] : n;
         // PM_SCATTER_UNROLL particles per thread per iteration, all loaded
         // before any is placed, keep that many independent loads in flight.
-        for (int64_t p = p0 + threadIdx.x; p < p1; p += PM_SCATTER_UNROLL * (int64_t)blockDim.x) {
+        // The trip count is the same for every thread (whole warps take part
+        // in the slot countdown).
+        for (int64_t pb = p0; pb < p1; pb += PM_SCATTER_UNROLL * (int64_t)blockDim.x) {
+          const int64_t p = pb + threadIdx.x;
           int64_t pp[PM_SCATTER_UNROLL];
           uint32_t tk[PM_SCATTER_UNROLL];
           uint4 pv[PM_SCATTER_UNROLL];
 #pragma unroll
           for (int u = 0; u < PM_SCATTER_UNROLL; ++u) {
             pp[u] = p + u * (int64_t)blockDim.x;
+            tk[u] = 0u;
             if (pp[u] < p1) {
               tk[u] = tkey[toff + pp[u]];
               pv[u] = load_record(tpv, toff + pp[u], coded, o.vel16, n0 + n1);
@@ -1482,12 +1509,15 @@ __global__ void __launch_bounds__(PM_SCATTER_THREADS, PM_SCATTER_MIN_BLOCKS) k_i
           }
 #pragma unroll
           for (int u = 0; u < PM_SCATTER_UNROLL; ++u) {
-            if (pp[u] >= p1) continue;
+            const bool live = pp[u] < p1;
+            const bool inw = live && (tk[u] & kInWindow);
+            const uint32_t sl = inw ? s * W + (tk[u] & ~kInWindow) : ~0u - (threadIdx.x & 31);
+            // rank within the block's range of the cell: count its histogram entry down
+            const uint32_t rank = run_countdown(hist, sl, inw);
+            if (!live) continue;
             int64_t dst;
-            if (tk[u] & kInWindow) {
-              // rank within the block's range of the cell: count its histogram entry down
-              const uint32_t sl = s * W + (tk[u] & ~kInWindow);
-              dst = (int64_t)base[sl] + (int64_t)atomicSub(hist + sl, 1u) - 1;
+            if (inw) {
+              dst = (int64_t)base[sl] + (int64_t)rank - 1;
             } else {
               const uint32_t top = atomicSub(counts + tk[u], 1u);
               dst = newoff[tk[u]] + (int64_t)top - 1;
