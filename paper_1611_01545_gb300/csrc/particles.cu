@@ -541,6 +541,45 @@ __device__ __forceinline__ void gather_idx(const float* S, int fx, int fy, int f
   a[2] = s2;
 }
 
+// Strides of a staged force region (fx x fy x fz nodes, 3 components) in
+// shared memory: rows padded to 4 and planes to 16 banks modulo 32, so that
+// the nodes around the particles of one compression cell, which the lanes of
+// a warp gather at the same time, fall in different banks.
+struct RegionStrides {
+  int row, plane, comp;
+};
+#ifndef PM_IKD_PAD
+#define PM_IKD_PAD 1
+#endif
+__host__ __device__ __forceinline__ RegionStrides region_strides(int fx, int fy, int fz) {
+  RegionStrides st;
+  st.row = PM_IKD_PAD ? fx + ((4 - fx) & 31) : fx;
+  const int p0 = st.row * fy;
+  st.plane = PM_IKD_PAD ? p0 + ((16 - p0) & 31) : p0;
+  st.comp = st.plane * fz;
+  return st;
+}
+
+// gather_idx on a region with the strides above; same weights and order.
+__device__ __forceinline__ void gather_strided(const float* S, RegionStrides st, int lx, int ly, int lz,
+                                               const float w1[3], float a[3]) {
+  const float w0[3] = {__fsub_rn(1.0f, w1[0]), __fsub_rn(1.0f, w1[1]), __fsub_rn(1.0f, w1[2])};
+  const float* base = S + lz * st.plane + ly * st.row + lx;
+  float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const int dx = c & 1, dy = (c >> 1) & 1, dz = c >> 2;
+    const float w = __fmul_rn(__fmul_rn(dx ? w1[0] : w0[0], dy ? w1[1] : w0[1]), dz ? w1[2] : w0[2]);
+    const float* q = base + dz * st.plane + dy * st.row + dx;
+    s0 = __fmaf_rn(w, q[0], s0);
+    s1 = __fmaf_rn(w, q[st.comp], s1);
+    s2 = __fmaf_rn(w, q[2 * st.comp], s2);
+  }
+  a[0] = s0;
+  a[1] = s1;
+  a[2] = s2;
+}
+
 __device__ __forceinline__ float wrap_pos(float x, float nf) {
   if (x < 0.f) x = __fadd_rn(x, nf);
   if (x >= nf) x = __fsub_rn(x, nf);
@@ -1226,7 +1265,8 @@ __global__ void __launch_bounds__(PM_IKD_THREADS, PM_IKD_MIN_BLOCKS) k_ikd_count
     int64_t* roff = reinterpret_cast<int64_t*>(smraw);
     uint32_t* hist = reinterpret_cast<uint32_t*>(roff + 2 * nrow * (bk.RX + 1));
     float* sf = reinterpret_cast<float*>(hist + 2 * W);
-    float* sc = sf + 3 * fx * fy * fz;
+    const RegionStrides fst = region_strides(fx, fy, fz);
+    float* sc = sf + 3 * fst.comp;
     load_row_offsets(off0, g, bk, cb, roff);
     load_row_offsets(off1, g, bk, cb, roff + nrow * (bk.RX + 1));
     for (int i = threadIdx.x; i < 2 * W; i += blockDim.x) hist[i] = 0;
@@ -1242,7 +1282,7 @@ __global__ void __launch_bounds__(PM_IKD_THREADS, PM_IKD_MIN_BLOCKS) k_ikd_count
         if (gz >= nf) gz -= nf;
         if (gy >= nf) gy -= nf;
         const float* src = acc_f + comp * nf3 + ((int64_t)gz * nf + gy) * nf;
-        float* dst = sf + (int64_t)li * fx;
+        float* dst = sf + comp * fst.comp + lz * fst.plane + ly * fst.row;
         for (int lx = threadIdx.x & 31; lx < fx; lx += 32) {
           int gx = bxf + lx;
           if (gx >= nf) gx -= nf;
@@ -1310,7 +1350,7 @@ __global__ void __launch_bounds__(PM_IKD_THREADS, PM_IKD_MIN_BLOCKS) k_ikd_count
             num[d] = (2 * q[d] + 1) * r;
             w1[d] = __fmul_rn(__int2float_rn(num[d] & 511), 1.0f / 512.0f);
           }
-          gather_idx(sf, fx, fy, fz, ixl * r + (num[0] >> 9), ky * r + (num[1] >> 9), kz * r + (num[2] >> 9), w1, a);
+          gather_strided(sf, fst, ixl * r + (num[0] >> 9), ky * r + (num[1] >> 9), kz * r + (num[2] >> 9), w1, a);
           if (two_c) {
             // coarse cell == compression cell: corner (ixl, ky, kz), weight (2q + 1) / 512
             float b[3], u1[3];
@@ -1630,10 +1670,10 @@ cudaError_t launch_compress(const float* x, const float* v, int64_t n, const Geo
 
 size_t ikd_count_smem(const Geo& g, const Blk& bk) {
   size_t nrow = (size_t)bk.RY * bk.RZ;
-  size_t fine = (size_t)(bk.RX * g.rcmp + 1) * (bk.RY * g.rcmp + 1) * (bk.RZ * g.rcmp + 1);
   size_t coarse = g.two ? (size_t)(bk.RX + 1) * (bk.RY + 1) * (bk.RZ + 1) : 0;
+  const RegionStrides st = region_strides(bk.RX * g.rcmp + 1, bk.RY * g.rcmp + 1, bk.RZ * g.rcmp + 1);
   return 2 * nrow * (bk.RX + 1) * sizeof(int64_t) + 2 * (size_t)window_cells(g, bk) * 4 +
-         3 * (fine + coarse) * sizeof(float);
+         3 * ((size_t)st.comp + coarse) * sizeof(float);
 }
 
 size_t ikd_scatter_smem(const Geo& g, const Blk& bk) {
