@@ -313,10 +313,11 @@ int pm_step_packed(pm_handle_t* h, const pm_host_codes_t in[2], pm_host_codes_t 
 /* pm_step_packed without waiting: queues the input copies (host -> device
  * on a library stream, then unpacked there), the step on `stream`, and the
  * output copies (device -> host on a second library stream), and returns.
- * Consecutive calls overlap: a call's input copies into the library's packed
- * staging start once the previous call has unpacked its own (so they run
- * beside the whole previous step), its unpacking runs once the previous step
- * has read its input (after its count pass), and one step's output
+ * Consecutive calls overlap: a call's position records go into the library's
+ * packed staging once the previous call has unpacked its own (beside the
+ * previous step), are unpacked once the previous step has read its input
+ * (after its count pass), and its velocity records follow (beside the
+ * previous scatter and this call's deposit and solve); one step's output
  * copies run beside the next step's input copies, deposit, solve and (when
  * the device has room for a packed output buffer of its own, 9 or 6 bytes
  * per particle, with 2 GB to spare) its count pass and scatter; without that

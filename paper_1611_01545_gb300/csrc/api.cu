@@ -1327,20 +1327,16 @@ int pm_step_packed_async(pm_handle_t* h, const pm_host_codes_t in[2], pm_host_co
   }
   uint8_t* const* opos = h->as_sep ? h->as_opos : h->pk_pos[1];
   uint8_t* const* ovel = h->as_sep ? h->as_ovel : h->pk_vel[1];
-  // input record copies into the packed staging, which the previous call's
-  // unpacking (earlier on the same stream) has finished reading: they run
-  // beside the whole previous step
+  // Position records into the packed staging, which the previous call's
+  // unpacking (earlier on the same stream) has finished reading, so they run
+  // beside the previous step; then, once that step's count pass has read its
+  // input, counts, escapes, v_max and the unpacked positions (the deposit
+  // needs no more); then the velocity records, which only the count pass
+  // needs (they run beside the previous scatter and this deposit and solve).
   for (int s = 0; s < 2; ++s) {
     const int64_t n = in[s].n;
     if (n > 0) CK(h, cudaMemcpyAsync(h->as_pos[s], in[s].pos, (size_t)n * 3, cudaMemcpyHostToDevice, h->copy_stream));
   }
-  for (int s = 0; s < 2; ++s) {
-    const int64_t n = in[s].n;
-    if (n > 0)
-      CK(h, cudaMemcpyAsync(h->as_vel[s], in[s].vel, (size_t)n * vbytes, cudaMemcpyHostToDevice, h->copy_stream));
-  }
-  // counts, escapes, v_max and the unpacked codes, once the previous step's
-  // count pass has read its input (they run beside its scatter)
   CK(h, cudaStreamWaitEvent(h->copy_stream, h->as_in_free, 0));
   for (int s = 0; s < 2; ++s) {
     if (int r = copy_meta(h, h->stage_in[s], in[s], ncell, cudaMemcpyHostToDevice, h->copy_stream)) return r;
@@ -1348,8 +1344,12 @@ int pm_step_packed_async(pm_handle_t* h, const pm_host_codes_t in[2], pm_host_co
                         nullptr, h->copy_stream));
   }
   CK(h, cudaEventRecord(h->as_pos_ready, h->copy_stream));
-  for (int s = 0; s < 2; ++s)
-    CK(h, launch_unpack(nullptr, h->as_vel[s], vel16, in[s].n, nullptr, h->stage_in[s].vel, h->copy_stream));
+  for (int s = 0; s < 2; ++s) {
+    const int64_t n = in[s].n;
+    if (n > 0)
+      CK(h, cudaMemcpyAsync(h->as_vel[s], in[s].vel, (size_t)n * vbytes, cudaMemcpyHostToDevice, h->copy_stream));
+    CK(h, launch_unpack(nullptr, h->as_vel[s], vel16, n, nullptr, h->stage_in[s].vel, h->copy_stream));
+  }
   CK(h, cudaEventRecord(h->as_vel_ready, h->copy_stream));
   // the step: positions first; velocities, and the previous step's output
   // copies out of what this step overwrites, before the count pass (its
