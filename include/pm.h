@@ -373,6 +373,16 @@ int pm_step_adjoint_acc(pm_handle_t* h, const pm_particles_t state[2], pm_partic
  * (PM_OK, PM_ERR_CORRUPT, PM_ERR_OVERFLOW, PM_ERR_RANGE, PM_ERR_TIMEOUT). */
 int pm_check(pm_handle_t* h, void* stream);
 
+/* Diagnostic of the bounded device waits (the mbarrier waits of the
+ * TMA-staged tile solve, which give up after about a second and record a
+ * timeout instead of hanging): launches on `stream` one block that waits on
+ * an mbarrier phase no copy ever completes, gives up after limit_cycles SM
+ * clock cycles (1e3 .. 2e9, else PM_ERR_ARG) and records the timeout in the
+ * handle's status word, so the next pm_check returns PM_ERR_TIMEOUT (and
+ * clears the word).  No copy is in flight when the block exits, and the
+ * handle stays usable. */
+int pm_wait_probe(pm_handle_t* h, int64_t limit_cycles, void* stream);
+
 /* Copies the last error message (NUL-terminated, truncated to n). */
 int pm_last_error(const pm_handle_t* h, char* buf, size_t n);
 

@@ -57,7 +57,7 @@ EXPORTED = ["pm_init", "pm_destroy", "pm_geometry", "pm_decompress", "pm_compres
             "pm_step_packed", "pm_step_packed_async", "pm_restrict",
             "pm_stage_times", "pm_serialize", "pm_deserialize", "pm_error_string", "pm_launch_count",
             "pm_decompress_noalloc", "pm_deposit_adjoint", "pm_solve_adjoint", "pm_interpolate_adjoint",
-            "pm_step_adjoint", "pm_step_adjoint_acc"]
+            "pm_step_adjoint", "pm_step_adjoint_acc", "pm_wait_probe"]
 
 _P = ctypes.c_void_p
 _I64 = ctypes.c_int64
@@ -81,6 +81,7 @@ _PROTOS = {
     "pm_step": (ctypes.c_int, [_P, ctypes.POINTER(pm_codes_t), ctypes.POINTER(pm_codes_t), _D, _D, _P]),
     "pm_step_host": (ctypes.c_int, [_P, ctypes.POINTER(pm_codes_t), ctypes.POINTER(pm_codes_t), _D, _D, _P]),
     "pm_check": (ctypes.c_int, [_P, _P]),
+    "pm_wait_probe": (ctypes.c_int, [_P, _I64, _P]),
     "pm_last_error": (ctypes.c_int, [_P, ctypes.c_char_p, ctypes.c_size_t]),
     "pm_set_timing": (ctypes.c_int, [_P, ctypes.c_int]),
     "pm_set_graphs": (ctypes.c_int, [_P, ctypes.c_int]),

@@ -354,6 +354,10 @@ void Timer::clear() {
 }  // namespace pm
 
 // ------------------------------------------------------------ entry points --
+namespace pm {
+cudaError_t launch_wait_probe(int* status, long long limit, cudaStream_t st);   // probe.cu
+}
+
 extern "C" {
 
 int64_t pm_launch_count(void) { return (int64_t)pm::g_launch_count.load(); }
@@ -1488,6 +1492,14 @@ int pm_check(pm_handle_t* h, void* stream) {
   if (s & ST_OVERFLOW) return fail(h, PM_ERR_OVERFLOW, "device validation: escape list capacity exceeded");
   if (s & ST_CORRUPT) return fail(h, PM_ERR_CORRUPT, "device validation: corrupt compressed stream");
   if (s & ST_TIMEOUT) return fail(h, PM_ERR_TIMEOUT, "device wait timed out");
+  return PM_OK;
+}
+
+int pm_wait_probe(pm_handle_t* h, int64_t limit_cycles, void* stream) {
+  if (!h) return PM_ERR_ARG;
+  if (limit_cycles < 1000 || limit_cycles > 2000000000LL) return fail(h, PM_ERR_ARG, "limit_cycles outside [1e3, 2e9]");
+  CK(h, launch_wait_probe(h->status, (long long)limit_cycles, (cudaStream_t)stream));
+  note_launches(1);
   return PM_OK;
 }
 

@@ -157,6 +157,10 @@ class PM:
     def check(self, stream=None):
         self._err(self.lib.pm_check(self.h, _stream(stream)))
 
+    def wait_probe(self, limit_cycles: int, stream=None):
+        """pm_wait_probe: a device wait that runs out; the next check() raises PM_ERR_TIMEOUT."""
+        self._err(self.lib.pm_wait_probe(self.h, int(limit_cycles), _stream(stream)))
+
     def empty_codes(self, n: int, esc_cap: Optional[int] = None) -> Codes:
         return Codes.empty(n, self.n_cmp, self.vel_bits, esc_cap)
 
