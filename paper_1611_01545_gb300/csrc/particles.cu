@@ -985,7 +985,9 @@ __global__ void PM_DEPOSIT_BOUNDS k_deposit_codes(PCodes c0, PCodes c1, const in
     const int bxf = cb.ix0 * r, byf = cb.iy0 * r, bzf = cb.iz0 * r;
     for (int s = 0; s < 2; ++s) {
       const PCodes& cs = s ? c1 : c0;
-      const float m = s ? m1 : m0;
+      // float mode: the species mass times the block's power-of-two scale
+      // (exact), so a corner's fixed-point value is rint(m S w)
+      const float m = sizeof(Acc) == 4 ? __fmul_rn(s ? m1 : m0, S) : (s ? m1 : m0);
       const long long M = s ? M1 : M0;
       const int64_t* ro_s = roff + s * nrow * (bk.RX + 1);
       for (int row = 0; row < nrow; ++row) {
@@ -1005,13 +1007,23 @@ __global__ void PM_DEPOSIT_BOUNDS k_deposit_codes(PCodes c0, PCodes c1, const in
             ixl = row_cell(ro, bk.RX, p);
             int q[3];
             unpack_pos(cs.pos[p], q);
-            px = decode_pos(cb.ix0 + ixl, q[0], pscale);
-            py = decode_pos(iy, q[1], pscale);
-            pz = decode_pos(iz, q[2], pscale);
-            // fine CIC in local region coordinates (no wrap inside the block)
-            float flx = floorf(px), fly = floorf(py), flz = floorf(pz);
-            int lx = (int)flx - bxf, ly = (int)fly - byf, lz = (int)flz - bzf;
-            float w1[3] = {__fsub_rn(px, flx), __fsub_rn(py, fly), __fsub_rn(pz, flz)};
+            if (dep_coarse) {
+              px = decode_pos(cb.ix0 + ixl, q[0], pscale);
+              py = decode_pos(iy, q[1], pscale);
+              pz = decode_pos(iz, q[2], pscale);
+            }
+            // fine CIC in local region coordinates (no wrap inside the block).
+            // Decoded positions are exact dyadics, x = c r + (2q + 1) r / 512,
+            // so the fine cell and the weight come from the codes in integer
+            // arithmetic (the same values as floor(x) and x - floor(x)).
+            int num[3];
+#pragma unroll
+            for (int d = 0; d < 3; ++d) num[d] = (2 * q[d] + 1) * r;
+            const int lx = ixl * r + (num[0] >> 9), ly = (iy - cb.iy0) * r + (num[1] >> 9),
+                      lz = (iz - cb.iz0) * r + (num[2] >> 9);
+            float w1[3];
+#pragma unroll
+            for (int d = 0; d < 3; ++d) w1[d] = __fmul_rn(__int2float_rn(num[d] & 511), 1.0f / 512.0f);
             Acc t8[8];
             corner_masses(m, M, w1, t8);
 #pragma unroll
@@ -1019,7 +1031,7 @@ __global__ void PM_DEPOSIT_BOUNDS k_deposit_codes(PCodes c0, PCodes c1, const in
               int dx = c & 1, dy = (c >> 1) & 1, dz = c >> 2;
               const int idx = ((lz + dz) * fy + (ly + dy)) * fx + (lx + dx);
               if constexpr (sizeof(Acc) == 4)
-                atomicAdd(reinterpret_cast<unsigned int*>(sf) + idx, __float2uint_rn(__fmul_rn((float)t8[c], S)));
+                atomicAdd(reinterpret_cast<unsigned int*>(sf) + idx, __float2uint_rn((float)t8[c]));
               else
                 smem_acc(&sf[idx], t8[c]);
             }
