@@ -71,6 +71,36 @@ def test_clustered_tuned_persistent_graph_step_matches_oracle(small):
     assert sum(int(c.esc_cell.size) for c in ref) > 0
 
 
+def test_clustered_bound_mode_step_matches_oracle(small):
+    """vmax_mode 1 on the clustered set: v_max' is the oracle's rounded-up
+    bound (float32 meshes: relative 1e-4), it covers every kicked velocity,
+    and the codes, escapes included, are the oracle codec's with that v_max
+    (the scatter copies the 12-byte coded records of 16-bit codes), in the
+    one-CTA-per-block and the persistent launch forms."""
+    w, _, codes, _ = small
+    cfg = cfg_of(w, vmax_mode=1)
+    ref, states = step.step(codes, cfg, 1.0, 1.0, vmax_mode=1)
+    pm = _pm(cfg)
+    cap = [max(64, c.n // 255 + 1) for c in codes]
+    din = [lib_codes_from_oracle(c, esc_cap=k) for c, k in zip(codes, cap)]
+    dout = [pm.empty_codes(c.n, esc_cap=k) for c, k in zip(codes, cap)]
+    n, nc = w.n_fine, w.n_fine // 4
+    base = pm.get_tuning()
+    for form in (dict(base, kick_persistent=0), dict(base, deposit_persistent=1, kick_persistent=1)):
+        pm.set_tuning(form)
+        pm.step(din, dout, 1.0, 1.0)
+        pm.check()
+        for s in range(2):
+            g = oracle_codes_from_lib(dout[s], nc, w.vel_bits)
+            assert abs(float(g.vmax) - float(ref[s].vmax)) <= 1e-4 * float(ref[s].vmax)
+            x1, v1 = states[s]
+            assert float(g.vmax) >= np.max(np.abs(v1)) * (1 - 1e-5)
+            mine = codec.compress(step.to_f32_positions(x1, n), v1.astype(np.float32), n, nc, w.vel_bits,
+                                  vmax=g.vmax)
+            assert (g.esc_cell.size > 0) == (mine.esc_cell.size > 0)
+            assert_codes_match(g, mine, f"clustered64 bound mode {form} species {s}")
+
+
 def test_clustered_interpolated_acceleration_matches_oracle(small):
     w, cfg, codes, ref = small
     pm = _pm(cfg)
