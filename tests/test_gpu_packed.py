@@ -72,13 +72,17 @@ def test_step_packed_equals_step():
     pm.set_graphs(False)
 
 
-@pytest.mark.parametrize("vel_bits", [8, 16])
-def test_step_packed_async_overlapping_calls_equal_step(vel_bits):
+@pytest.mark.parametrize("vel_bits,shared_output", [(8, False), (16, False), (16, True)])
+def test_step_packed_async_overlapping_calls_equal_step(vel_bits, shared_output):
     """pm_step_packed_async: three calls queued back to back from one packed
     host input into three host outputs (each call's copies overlapping the
     neighbouring calls' compute), then one pm_check: every output is the
     step pm_step gives (fixed-point deposits, so bit for bit up to the order
-    within a cell), and a following synchronous pm_step_packed agrees too."""
+    within a cell), and a following synchronous pm_step_packed agrees too.
+    shared_output: the device is filled until the library has no room for a
+    packed output buffer of its own, so the packed output shares the step
+    scratch and each count pass waits for the previous output copies (the
+    path the 1536^3 workload takes)."""
     from paper_1611_01545_gb300 import PM
     w = make_workload("two_level64", n_cdm=16, n_nu=40)
     cfg = cfg_of(w, deposit_mode=1, vel_bits=vel_bits)
@@ -96,9 +100,16 @@ def test_step_packed_async_overlapping_calls_equal_step(vel_bits):
         for c in h:
             c.pos.zero_()
             c.vel.zero_()
+    filler = None
+    if shared_output:
+        torch.cuda.synchronize()
+        free, _ = torch.cuda.mem_get_info()
+        filler = torch.empty(free - (1 << 30), dtype=torch.uint8, device="cuda")   # 1 GiB left free
     for h in houts:
         pm.step_packed_async(hin, h, 1.0, 1.0)
     pm.check()
+    del filler
+    torch.cuda.empty_cache()
     sync_out = [pm.pack(c).to("cpu", pin=True) for c in dout]
     pm.step_packed(hin, sync_out, 1.0, 1.0)
     for h in houts + [sync_out]:
