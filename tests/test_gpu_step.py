@@ -201,3 +201,33 @@ def test_fused_step_vmax_bound_mode(name, n_cdm, n_nu):
         assert float(g.vmax) >= np.max(np.abs(v1)) * (1 - 1e-5)
         mine = codec.compress(step.to_f32_positions(x1, n), v1.astype(np.float32), n, nc, w.vel_bits, vmax=g.vmax)
         assert_codes_match(g, mine, f"{name} bound mode species {s}")
+
+
+@pytest.mark.parametrize("case", ["empty_cdm", "zero_step"])
+def test_fused_step_degenerate_cases(case):
+    """The fused step's degenerate cases against the oracle: a species with no
+    particles (the CDM; every pass must skip it and still scan, place and
+    count the neutrinos), and a step with c_kick = c_drift = 0 (nothing moves,
+    the velocities are re-quantised with the new, smaller v_max')."""
+    w = make_workload("two_level64", n_cdm=16, n_nu=40)
+    nc = w.n_fine // 4
+    if case == "empty_cdm":
+        w.x[0] = np.zeros((0, 3), np.float32)
+        w.v[0] = np.zeros((0, 3), np.float32)
+        ck = cd = 1.0
+    else:
+        ck = cd = 0.0
+    cfg = cfg_of(w)
+    codes = [codec.compress(w.x[s], w.v[s], w.n_fine, nc, w.vel_bits) for s in range(2)]
+    pm = _pm(cfg)
+    din = [lib_codes_from_oracle(c) for c in codes]
+    dout = [pm.empty_codes(c.n, esc_cap=64) for c in codes]
+    pm.step(din, dout, ck, cd)
+    pm.check()
+    ref, _ = step.step(codes, cfg, ck, cd)
+    for s in range(2):
+        g = oracle_codes_from_lib(dout[s], nc, w.vel_bits)
+        assert g.n == ref[s].n
+        assert g.counts().sum() == ref[s].n
+        assert abs(float(g.vmax) - float(ref[s].vmax)) <= 1e-5 * float(ref[s].vmax)
+        assert_codes_match(g, ref[s], f"{case} species {s}")
